@@ -1,0 +1,546 @@
+// CPU oracle for the explicit finite-volume Euler residual and Runge-Kutta
+// stage of a multi-block structured-grid solver (Xue, Jackson, Roy,
+// arXiv 2012.02925).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+// restatement of the method that the CUDA library is checked against.  Only
+// the tests, the package's smoke check and the benchmark's CPU-baseline leg
+// may load it.  It shares no code with the CUDA path.
+//
+// Every routine is a direct loop over cells or faces in the order the method
+// states it; it is templated on the scalar type so that the same arithmetic
+// runs in double, in forward-mode dual numbers (for Jacobian-vector products)
+// and in an operation-counting type.  Build with -ffp-contract=off so that no
+// multiply-add is fused.
+//
+// Citations (paper sections and equations):
+//   * governing weak form, conserved Q and inviscid normal flux: Section 2,
+//     Eq. (governing) and the Q / F_{i,n} definitions;
+//   * primitive-variable MUSCL reconstruction: Section 2 and Section 7.2 (V4),
+//     Eq. (flux), with limiter values Psi^{+/-};
+//   * Roe's approximate Riemann flux: Section 2 (flux-difference splitting);
+//   * ghost cells for connected boundaries: Section 2 and Section 4;
+//   * explicit M-step Runge-Kutta time marching: Section 2.
+// Points the paper leaves open are fixed as follows:
+//   limiter: van Leer Psi(r) = (r+|r|)/(1+|r|) with r = a/b, b guarded to
+//     copysign(max(|b|,1e-30), b) (sign(0)=+1); van Albada in the smooth
+//     product form Psi(a/b) b = b (a^2 + a b) / (a^2 + b^2 + delta^2);
+//     "none" means Psi = 1;
+//   entropy fix: Harten's |l| <- (l^2 + d^2)/(2d) when |l| < d, d = harten*c~,
+//     on the acoustic eigenvalues (and on V_n as well when fix_all);
+//   metrics: face vector S = 1/2 (x_c - x_a) x (x_d - x_b) for the face's
+//     nodes a,b,c,d in order; volume = 1/3 sum_faces xbar_f . S_f (outward);
+//   residual summation order: xi pair, eta pair, zeta pair, then the source;
+//   RK: Q^(m) = Q^(0) - alpha_m dt / Omega R(Q^(m-1)).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// scalar types
+// ---------------------------------------------------------------------------
+
+struct Dual {           // value + one tangent direction
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double x) : v(x), d(0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual sqrt_(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual abs_(Dual a) { return a.v < 0 ? -a : a; }
+inline double val(Dual a) { return a.v; }
+
+inline double sqrt_(double a) { return std::sqrt(a); }
+inline double abs_(double a) { return std::fabs(a); }
+inline double val(double a) { return a; }
+
+// Operation-counting scalar: every arithmetic operation bumps a counter.
+struct OpCount { long add, mul, div, sqrt, abs_, cmp; };
+OpCount g_ops;
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double x) : v(x) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_ops.add; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_ops.add; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_ops.mul; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_ops.div; return Cnt(a.v / b.v); }
+inline Cnt sqrt_(Cnt a) { ++g_ops.sqrt; return Cnt(std::sqrt(a.v)); }
+inline Cnt abs_(Cnt a) { ++g_ops.abs_; return Cnt(std::fabs(a.v)); }
+inline double val(Cnt a) { ++g_ops.cmp; return a.v; }
+
+struct Params {
+  double gamma, eps, kappa;
+  int limiter;        // 0 none (Psi = 1), 1 van Leer, 2 van Albada
+  double harten;      // entropy-fix width as a fraction of c~ (0 = off)
+  int fix_all;        // also fix |V_n|
+  double va_delta2;   // van Albada smoothing delta^2
+  int dim;            // 2 or 3
+};
+
+Params unpack(const double* p) {
+  Params q;
+  q.gamma = p[0]; q.eps = p[1]; q.kappa = p[2]; q.limiter = (int)p[3];
+  q.harten = p[4]; q.fix_all = (int)p[5]; q.va_delta2 = p[6]; q.dim = (int)p[7];
+  return q;
+}
+
+constexpr int G = 2;  // ghost layers
+
+// ---------------------------------------------------------------------------
+// Section 2: primitive variables from the conserved vector
+// Q = (rho, rho u, rho v, rho w, rho e_t), p = (gamma-1)(rho e_t - rho|u|^2/2)
+// ---------------------------------------------------------------------------
+template <class T>
+void cons_to_prim(const T q[5], double gamma, T V[5]) {
+  T rho = q[0];
+  T u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
+  V[0] = rho; V[1] = u; V[2] = v; V[3] = w;
+  V[4] = T(gamma - 1.0) * (q[4] - T(0.5) * rho * (u * u + v * v + w * w));
+}
+
+// ---------------------------------------------------------------------------
+// Limited difference Psi(a/b) * b.  In Eq. (flux) every limiter value
+// multiplies the difference that forms the denominator of its ratio, so each
+// of the four limited terms is Psi(a/b) b for a pair of neighbouring
+// differences (a, b).
+// ---------------------------------------------------------------------------
+template <class T>
+T limited(const Params& P, T a, T b) {
+  if (P.limiter == 0) return b;
+  if (P.limiter == 1) {
+    T den = b;
+    double bv = val(b);
+    if (std::fabs(bv) < 1e-30) den = T(bv < 0 ? -1e-30 : 1e-30);
+    T r = a / den;
+    T ar = abs_(r);
+    T psi = (r + ar) / (T(1.0) + ar);
+    return psi * b;
+  }
+  return b * (a * a + a * b) / (a * a + b * b + T(P.va_delta2));
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (flux): MUSCL extrapolation of one primitive component to face i+1/2
+// from V_{i-1}, V_i, V_{i+1}, V_{i+2}.
+//   Psi^+_{i-1/2} = Psi(D_{i+1/2}/D_{i-1/2}),  Psi^-_{i+1/2} = Psi(D_{i-1/2}/D_{i+1/2}),
+//   Psi^+_{i+1/2} = Psi(D_{i+3/2}/D_{i+1/2}),  Psi^-_{i+3/2} = Psi(D_{i+1/2}/D_{i+3/2}).
+// ---------------------------------------------------------------------------
+template <class T>
+void muscl(const Params& P, T vm1, T v0, T vp1, T vp2, T& L, T& R) {
+  T d_m = v0 - vm1;    // D_{i-1/2}
+  T d_0 = vp1 - v0;    // D_{i+1/2}
+  T d_p = vp2 - vp1;   // D_{i+3/2}
+  T e4 = T(P.eps / 4.0);
+  T km = T(1.0 - P.kappa), kp = T(1.0 + P.kappa);
+  L = v0 + e4 * (km * limited(P, d_0, d_m) + kp * limited(P, d_m, d_0));
+  R = vp1 - e4 * (kp * limited(P, d_p, d_0) + km * limited(P, d_0, d_p));
+}
+
+template <class T>
+T entropy_fix(T lam_abs, T delta) {
+  if (val(lam_abs) < val(delta)) return (lam_abs * lam_abs + delta * delta) / (T(2.0) * delta);
+  return lam_abs;
+}
+
+// ---------------------------------------------------------------------------
+// Roe flux-difference splitting (Section 2): F^ = 1/2 (F(V_L).n + F(V_R).n)
+// - 1/2 (|dF1| + |dF234| + |dF5|), returned multiplied by the face area |S|.
+// F.n is the inviscid normal flux of Section 2: (rho V_n, rho u V_n + n_x p,
+// rho v V_n + n_y p, rho w V_n + n_z p, rho h_t V_n).
+// ---------------------------------------------------------------------------
+template <class T>
+void roe_flux(const Params& P, const T VL[5], const T VR[5], const double S[3], T out[5]) {
+  const double g = P.gamma;
+  double area = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  double nx = S[0] / area, ny = S[1] / area, nz = S[2] / area;
+
+  T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
+  T rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
+  T VnL = T(nx) * uL + T(ny) * vL + T(nz) * wL;
+  T VnR = T(nx) * uR + T(ny) * vR + T(nz) * wR;
+  T hL = T(g / (g - 1.0)) * pL / rL + T(0.5) * (uL * uL + vL * vL + wL * wL);
+  T hR = T(g / (g - 1.0)) * pR / rR + T(0.5) * (uR * uR + vR * vR + wR * wR);
+
+  T FL[5], FR[5];
+  FL[0] = rL * VnL;
+  FL[1] = rL * uL * VnL + T(nx) * pL;
+  FL[2] = rL * vL * VnL + T(ny) * pL;
+  FL[3] = rL * wL * VnL + T(nz) * pL;
+  FL[4] = rL * hL * VnL;
+  FR[0] = rR * VnR;
+  FR[1] = rR * uR * VnR + T(nx) * pR;
+  FR[2] = rR * vR * VnR + T(ny) * pR;
+  FR[3] = rR * wR * VnR + T(nz) * pR;
+  FR[4] = rR * hR * VnR;
+
+  // Roe averages
+  T Rt = sqrt_(rR / rL);
+  T rt = sqrt_(rL * rR);
+  T ut = (uL + Rt * uR) / (T(1.0) + Rt);
+  T vt = (vL + Rt * vR) / (T(1.0) + Rt);
+  T wt = (wL + Rt * wR) / (T(1.0) + Rt);
+  T ht = (hL + Rt * hR) / (T(1.0) + Rt);
+  T q2t = ut * ut + vt * vt + wt * wt;
+  T ct = sqrt_(T(g - 1.0) * (ht - T(0.5) * q2t));
+  T Vnt = T(nx) * ut + T(ny) * vt + T(nz) * wt;
+
+  // jumps
+  T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
+  T dVn = VnR - VnL;
+
+  // eigenvalue magnitudes with Harten's entropy fix
+  T delta = T(P.harten) * ct;
+  T l1 = abs_(Vnt - ct), l2 = abs_(Vnt), l5 = abs_(Vnt + ct);
+  if (P.harten > 0.0) {
+    l1 = entropy_fix(l1, delta);
+    l5 = entropy_fix(l5, delta);
+    if (P.fix_all) l2 = entropy_fix(l2, delta);
+  }
+
+  T c2 = ct * ct;
+  T a1 = l1 * (dp - rt * ct * dVn) / (T(2.0) * c2);   // |dF1| strength
+  T a5 = l5 * (dp + rt * ct * dVn) / (T(2.0) * c2);   // |dF5| strength
+  T a2 = l2 * (dr - dp / c2);                          // entropy wave
+  T a3 = l2 * rt;                                      // shear waves
+
+  T dF1[5], dF234[5], dF5[5];
+  dF1[0] = a1;
+  dF1[1] = a1 * (ut - T(nx) * ct);
+  dF1[2] = a1 * (vt - T(ny) * ct);
+  dF1[3] = a1 * (wt - T(nz) * ct);
+  dF1[4] = a1 * (ht - Vnt * ct);
+  dF5[0] = a5;
+  dF5[1] = a5 * (ut + T(nx) * ct);
+  dF5[2] = a5 * (vt + T(ny) * ct);
+  dF5[3] = a5 * (wt + T(nz) * ct);
+  dF5[4] = a5 * (ht + Vnt * ct);
+  dF234[0] = a2;
+  dF234[1] = a2 * ut + a3 * (du - T(nx) * dVn);
+  dF234[2] = a2 * vt + a3 * (dv - T(ny) * dVn);
+  dF234[3] = a2 * wt + a3 * (dw - T(nz) * dVn);
+  dF234[4] = a2 * (T(0.5) * q2t) + a3 * (ut * du + vt * dv + wt * dw - Vnt * dVn);
+
+  for (int n = 0; n < 5; ++n) {
+    T Fh = T(0.5) * (FL[n] + FR[n]) - T(0.5) * (dF1[n] + dF234[n] + dF5[n]);
+    out[n] = Fh * T(area);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block geometry helpers
+// ---------------------------------------------------------------------------
+struct Blk {
+  int ni, nj, nk;
+  long sx, sy, sz;     // ghosted strides (i, j, k)
+  long plane;          // ghosted cells per variable
+  Blk(int a, int b, int c) : ni(a), nj(b), nk(c) {
+    sx = 1; sy = a + 2 * G; sz = (long)(a + 2 * G) * (b + 2 * G);
+    plane = sz * (c + 2 * G);
+  }
+  long at(int i, int j, int k) const { return (long)(k + G) * sz + (long)(j + G) * sy + (i + G); }
+};
+
+inline void cross_half(const double* xa, const double* xb, const double* xc, const double* xd, double* S) {
+  double d1[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
+  double d2[3] = {xd[0] - xb[0], xd[1] - xb[1], xd[2] - xb[2]};
+  S[0] = 0.5 * (d1[1] * d2[2] - d1[2] * d2[1]);
+  S[1] = 0.5 * (d1[2] * d2[0] - d1[0] * d2[2]);
+  S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
+}
+
+template <class T>
+void residual_block(const Params& P, const Blk& B, const double* Sxi, const double* Seta,
+                    const double* Szeta, const double* vol, const T* q, const double* src, T* R) {
+  const int ni = B.ni, nj = B.nj, nk = B.nk;
+  // primitives of every cell, ghosts included
+  std::vector<T> V(5 * B.plane);
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < B.plane; ++c) {
+    T qc[5], vc[5];
+    for (int n = 0; n < 5; ++n) qc[n] = q[n * B.plane + c];
+    // cells that hold no data (edges/corners of the ghost frame) may be zero
+    if (val(qc[0]) == 0.0) { for (int n = 0; n < 5; ++n) V[n * B.plane + c] = T(0.0); continue; }
+    cons_to_prim(qc, P.gamma, vc);
+    for (int n = 0; n < 5; ++n) V[n * B.plane + c] = vc[n];
+  }
+  const long nfx = (long)(ni + 1), nfy = (long)(nj + 1);
+  const long n_xi = (long)nk * nj * nfx, n_eta = (long)nk * nfy * ni, n_zeta = (long)(nk + 1) * nj * ni;
+  std::vector<T> Fx(5 * n_xi), Fy(5 * n_eta), Fz(P.dim == 3 ? 5 * n_zeta : 0);
+
+  // face fluxes in one direction: face f between cells f-1 and f along the axis
+  auto face = [&](long cm2, long stride, const double* Sarr, long nfaces, long fidx, T* F) {
+    T VL[5], VR[5], out[5];
+    for (int n = 0; n < 5; ++n) {
+      const T* Vn = &V[n * B.plane];
+      muscl(P, Vn[cm2], Vn[cm2 + stride], Vn[cm2 + 2 * stride], Vn[cm2 + 3 * stride], VL[n], VR[n]);
+    }
+    double S[3] = {Sarr[fidx], Sarr[nfaces + fidx], Sarr[2 * nfaces + fidx]};
+    roe_flux(P, VL, VR, S, out);
+    for (int n = 0; n < 5; ++n) F[n * nfaces + fidx] = out[n];
+  };
+
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i <= ni; ++i) {
+        long f = ((long)k * nj + j) * nfx + i;
+        face(B.at(i - 2, j, k), B.sx, Sxi, n_xi, f, Fx.data());
+      }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j <= nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        long f = ((long)k * nfy + j) * ni + i;
+        face(B.at(i, j - 2, k), B.sy, Seta, n_eta, f, Fy.data());
+      }
+  if (P.dim == 3) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= nk; ++k)
+      for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+          long f = ((long)k * nj + j) * ni + i;
+          face(B.at(i, j, k - 2), B.sz, Szeta, n_zeta, f, Fz.data());
+        }
+  }
+  // Eq. (governing), discretely: R = sum over faces of F^ |S| (outward) - S Omega
+  const long ncell = (long)ni * nj * nk;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        long c = ((long)k * nj + j) * ni + i;
+        long fx = ((long)k * nj + j) * nfx + i;
+        long fy = ((long)k * nfy + j) * ni + i;
+        long fz = ((long)k * nj + j) * ni + i;
+        for (int n = 0; n < 5; ++n) {
+          T r = (Fx[n * n_xi + fx + 1] - Fx[n * n_xi + fx]) +
+                (Fy[n * n_eta + fy + ni] - Fy[n * n_eta + fy]);
+          if (P.dim == 3) r = r + (Fz[n * n_zeta + fz + (long)ni * nj] - Fz[n * n_zeta + fz]);
+          if (src) r = r - T(src[n * ncell + c] * vol[c]);
+          R[n * ncell + c] = r;
+        }
+      }
+}
+
+// One connection: ghosts of dst face at depth d <- src interior cells at depth d.
+template <class T>
+void exchange_one(const int* dims, const long* offs, T* q, const int* c) {
+  int db = c[0], df = c[1], dlo0 = c[2], dlo1 = c[3], dhi0 = c[4], dhi1 = c[5];
+  int sb = c[6], sf = c[7], slo0 = c[8], slo1 = c[9], t0 = c[10], t1 = c[11];
+  Blk D(dims[3 * db], dims[3 * db + 1], dims[3 * db + 2]);
+  Blk S(dims[3 * sb], dims[3 * sb + 1], dims[3 * sb + 2]);
+  int da = df / 2, sa = sf / 2;
+  int dext[3] = {D.ni, D.nj, D.nk}, sext[3] = {S.ni, S.nj, S.nk};
+  int dtan[2], stan[2], n = 0, m = 0;
+  for (int x = 0; x < 3; ++x) { if (x != da) dtan[n++] = x; if (x != sa) stan[m++] = x; }
+  T* qd = q + offs[db];
+  const T* qs = q + offs[sb];
+  for (int b = 0; b < dhi1 - dlo1; ++b)
+    for (int a = 0; a < dhi0 - dlo0; ++a)
+      for (int d = 1; d <= G; ++d) {
+        int dc[3], sc[3];
+        dc[dtan[0]] = dlo0 + a;
+        dc[dtan[1]] = dlo1 + b;
+        dc[da] = (df % 2 == 0) ? -d : dext[da] - 1 + d;
+        int st[2] = {slo0, slo1};
+        st[std::abs(t0) - 1] += (t0 > 0 ? a : -a);
+        st[std::abs(t1) - 1] += (t1 > 0 ? b : -b);
+        sc[stan[0]] = st[0];
+        sc[stan[1]] = st[1];
+        sc[sa] = (sf % 2 == 0) ? d - 1 : sext[sa] - d;
+        long di = D.at(dc[0], dc[1], dc[2]);
+        long si = S.at(sc[0], sc[1], sc[2]);
+        for (int v = 0; v < 5; ++v) qd[v * D.plane + di] = qs[v * S.plane + si];
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+
+int oracle_max_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Face vectors and volumes (metric setup).  nodes: (nk+1)(nj+1)(ni+1)x3 or NULL
+// for a Cartesian block with spacing h.  Sxi: [3][nk][nj][ni+1] (low face of
+// cell i, pointing to +i), Seta: [3][nk][nj+1][ni], Szeta: [3][nk+1][nj][ni],
+// vol: [nk][nj][ni].
+void oracle_metrics(int ni, int nj, int nk, const double* nodes, const double* h,
+                    double* Sxi, double* Seta, double* Szeta, double* vol) {
+  const long n_xi = (long)nk * nj * (ni + 1), n_eta = (long)nk * (nj + 1) * ni,
+             n_zeta = (long)(nk + 1) * nj * ni;
+  if (!nodes) {
+    for (long f = 0; f < n_xi; ++f) { Sxi[f] = h[1] * h[2]; Sxi[n_xi + f] = 0.0; Sxi[2 * n_xi + f] = 0.0; }
+    for (long f = 0; f < n_eta; ++f) { Seta[f] = 0.0; Seta[n_eta + f] = h[0] * h[2]; Seta[2 * n_eta + f] = 0.0; }
+    for (long f = 0; f < n_zeta; ++f) { Szeta[f] = 0.0; Szeta[n_zeta + f] = 0.0; Szeta[2 * n_zeta + f] = h[0] * h[1]; }
+    for (long c = 0; c < (long)ni * nj * nk; ++c) vol[c] = h[0] * h[1] * h[2];
+    return;
+  }
+  auto X = [&](int i, int j, int k) { return nodes + 3 * (((long)k * (nj + 1) + j) * (ni + 1) + i); };
+  double S[3];
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i <= ni; ++i) {
+        long f = ((long)k * nj + j) * (ni + 1) + i;
+        cross_half(X(i, j, k), X(i, j + 1, k), X(i, j + 1, k + 1), X(i, j, k + 1), S);
+        Sxi[f] = S[0]; Sxi[n_xi + f] = S[1]; Sxi[2 * n_xi + f] = S[2];
+      }
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j <= nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        long f = ((long)k * (nj + 1) + j) * ni + i;
+        cross_half(X(i, j, k), X(i, j, k + 1), X(i + 1, j, k + 1), X(i + 1, j, k), S);
+        Seta[f] = S[0]; Seta[n_eta + f] = S[1]; Seta[2 * n_eta + f] = S[2];
+      }
+  for (int k = 0; k <= nk; ++k)
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        long f = ((long)k * nj + j) * ni + i;
+        cross_half(X(i, j, k), X(i + 1, j, k), X(i + 1, j + 1, k), X(i, j + 1, k), S);
+        Szeta[f] = S[0]; Szeta[n_zeta + f] = S[1]; Szeta[2 * n_zeta + f] = S[2];
+      }
+  // volume = 1/3 sum over the six faces of (face centroid . outward S)
+  auto centroid = [&](const double* a, const double* b, const double* c, const double* d, double* m) {
+    for (int x = 0; x < 3; ++x) m[x] = 0.25 * (a[x] + b[x] + c[x] + d[x]);
+  };
+  for (int k = 0; k < nk; ++k)
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        double m[3], acc = 0.0;
+        long fl = ((long)k * nj + j) * (ni + 1) + i;
+        centroid(X(i, j, k), X(i, j + 1, k), X(i, j + 1, k + 1), X(i, j, k + 1), m);
+        acc -= m[0] * Sxi[fl] + m[1] * Sxi[n_xi + fl] + m[2] * Sxi[2 * n_xi + fl];
+        centroid(X(i + 1, j, k), X(i + 1, j + 1, k), X(i + 1, j + 1, k + 1), X(i + 1, j, k + 1), m);
+        acc += m[0] * Sxi[fl + 1] + m[1] * Sxi[n_xi + fl + 1] + m[2] * Sxi[2 * n_xi + fl + 1];
+        long gl = ((long)k * (nj + 1) + j) * ni + i, gh = gl + ni;
+        centroid(X(i, j, k), X(i, j, k + 1), X(i + 1, j, k + 1), X(i + 1, j, k), m);
+        acc -= m[0] * Seta[gl] + m[1] * Seta[n_eta + gl] + m[2] * Seta[2 * n_eta + gl];
+        centroid(X(i, j + 1, k), X(i, j + 1, k + 1), X(i + 1, j + 1, k + 1), X(i + 1, j + 1, k), m);
+        acc += m[0] * Seta[gh] + m[1] * Seta[n_eta + gh] + m[2] * Seta[2 * n_eta + gh];
+        long zl = ((long)k * nj + j) * ni + i, zh = zl + (long)nj * ni;
+        centroid(X(i, j, k), X(i + 1, j, k), X(i + 1, j + 1, k), X(i, j + 1, k), m);
+        acc -= m[0] * Szeta[zl] + m[1] * Szeta[n_zeta + zl] + m[2] * Szeta[2 * n_zeta + zl];
+        centroid(X(i, j, k + 1), X(i + 1, j, k + 1), X(i + 1, j + 1, k + 1), X(i, j + 1, k + 1), m);
+        acc += m[0] * Szeta[zh] + m[1] * Szeta[n_zeta + zh] + m[2] * Szeta[2 * n_zeta + zh];
+        vol[((long)k * nj + j) * ni + i] = acc / 3.0;
+      }
+}
+
+// Connected-boundary ghost fill for every connection (rows of 12 ints, see
+// the connection table layout), applied in table order.
+void oracle_exchange(int nconn, const int* conns, const int* dims, const long* offs, double* q) {
+  for (int c = 0; c < nconn; ++c) exchange_one<double>(dims, offs, q, conns + 12 * c);
+}
+
+// Residual of one block: R = sum_faces F^ |S| - S Omega (interior cells,
+// [5][nk][nj][ni]).  q: ghosted conserved state [5][nk+4][nj+4][ni+4];
+// src: source per unit volume at cell centroids [5][nk][nj][ni] or NULL.
+void oracle_residual(const double* params, int ni, int nj, int nk, const double* Sxi,
+                     const double* Seta, const double* Szeta, const double* vol,
+                     const double* q, const double* src, double* R) {
+  Params P = unpack(params);
+  Blk B(ni, nj, nk);
+  residual_block<double>(P, B, Sxi, Seta, Szeta, vol, q, src, R);
+}
+
+// Jacobian-vector product of the residual: dR = (dR/dq) dq (forward mode).
+void oracle_residual_jvp(const double* params, int ni, int nj, int nk, const double* Sxi,
+                         const double* Seta, const double* Szeta, const double* vol,
+                         const double* q, const double* dq, const double* src, double* R,
+                         double* dR) {
+  Params P = unpack(params);
+  Blk B(ni, nj, nk);
+  std::vector<Dual> qd(5 * B.plane), Rd(5L * ni * nj * nk);
+  for (long x = 0; x < 5 * B.plane; ++x) qd[x] = Dual(q[x], dq[x]);
+  residual_block<Dual>(P, B, Sxi, Seta, Szeta, vol, qd.data(), src, Rd.data());
+  for (long x = 0; x < 5L * ni * nj * nk; ++x) { R[x] = Rd[x].v; dR[x] = Rd[x].d; }
+}
+
+// Tangent of the ghost exchange (linear: the same copy applied to dq).
+void oracle_exchange_tangent(int nconn, const int* conns, const int* dims, const long* offs, double* dq) {
+  for (int c = 0; c < nconn; ++c) exchange_one<double>(dims, offs, dq, conns + 12 * c);
+}
+
+// RK stage update for one block: Q^(m) = Q^(0) - (alpha dt / Omega) R on the
+// interior; ghost cells of the output take Q^(0)'s ghosts.
+void oracle_rk_update(int ni, int nj, int nk, double alpha_dt, const double* vol,
+                      const double* q0, const double* R, double* qout) {
+  Blk B(ni, nj, nk);
+  std::memcpy(qout, q0, sizeof(double) * 5 * B.plane);
+  const long ncell = (long)ni * nj * nk;
+  for (int n = 0; n < 5; ++n)
+    for (int k = 0; k < nk; ++k)
+      for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+          long c = ((long)k * nj + j) * ni + i;
+          double fac = alpha_dt / vol[c];
+          qout[n * B.plane + B.at(i, j, k)] = q0[n * B.plane + B.at(i, j, k)] - fac * R[n * ncell + c];
+        }
+}
+
+// Pieces exposed for the closed-form checks.
+void oracle_roe_flux(const double* params, const double* VL, const double* VR, const double* S,
+                     double* out) {
+  Params P = unpack(params);
+  roe_flux<double>(P, VL, VR, S, out);
+}
+
+void oracle_muscl(const double* params, const double* v4, double* LR) {
+  Params P = unpack(params);
+  muscl<double>(P, v4[0], v4[1], v4[2], v4[3], LR[0], LR[1]);
+}
+
+double oracle_limited(const double* params, double a, double b) {
+  Params P = unpack(params);
+  return limited<double>(P, a, b);
+}
+
+void oracle_cons_to_prim(double gamma, const double* q, double* V) { cons_to_prim<double>(q, gamma, V); }
+
+// Operation counts of one face evaluation (5 MUSCL components + Roe flux):
+// out = {add, mul, div, sqrt, abs, compare}.
+void oracle_face_opcount(const double* params, const double* V4x5, const double* S, long* out) {
+  Params P = unpack(params);
+  g_ops = OpCount{0, 0, 0, 0, 0, 0};
+  Cnt VL[5], VR[5], F[5];
+  for (int n = 0; n < 5; ++n) {
+    Cnt L, R;
+    muscl<Cnt>(P, Cnt(V4x5[4 * n]), Cnt(V4x5[4 * n + 1]), Cnt(V4x5[4 * n + 2]), Cnt(V4x5[4 * n + 3]), L, R);
+    VL[n] = L; VR[n] = R;
+  }
+  roe_flux<Cnt>(P, VL, VR, S, F);
+  out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt;
+  out[4] = g_ops.abs_; out[5] = g_ops.cmp;
+}
+
+}  // extern "C"
