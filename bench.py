@@ -1,0 +1,432 @@
+"""Throughput of the fused finite-volume residual + RK stage on GB300.
+
+Metric: Gcell-updates/s per RK stage (cells x stages / s) on the 3D
+manufactured-solution block, 128^3 perturbed-curvilinear cells, FP64 state,
+MUSCL + van Leer + Roe, 4-stage RK (the synthetic stand-in for the paper's
+cases; Section 8 cases' grids are not available).  One step = one full RK
+step: per stage the ghost exchange and the fused residual + update kernel.
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the only other place this file runs oracle code) on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cases  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# measured on this GPU pool by a throughput probe (FFMA / DFMA issue rates)
+FP32_OPS_PER_CLK_SM = 128
+FP64_OPS_PER_CLK_SM = 1.6   # measured: DFMA/DADD/DMUL ~505 Gop/s at 152 SMs, ~2.07 GHz
+
+
+def workload(name: str):
+    if name == "mms128":
+        return cases.mms_3d(128, curvilinear=True)
+    if name == "large":
+        return cases.large_periodic(512, 512, 256)
+    if name == "multiblock":
+        return cases.multiblock_batched()
+    if name == "vortex":
+        return cases.vortex_2d(64)
+    if name.startswith("mms"):
+        return cases.mms_3d(int(name[3:]), curvilinear=True)
+    raise SystemExit("unknown workload " + name)
+
+
+def algorithmic_bytes(pb, stage: int, curvilinear: bool) -> float:
+    """Bytes a cell-update must move at least: read Q^(m-1) (40 B), read Q^(0)
+    for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics 80 B
+    (3 face vectors + 1/Omega); a source term 40 B; exchanged ghost cells read
+    and write 80 B each."""
+    n = pb.ncells
+    per = 80.0 + (40.0 if stage > 1 else 0.0)
+    if curvilinear:
+        per += 80.0
+    if pb.source is not None:
+        per += 40.0
+    ghosts = 0
+    for c in pb.conns:
+        ghosts += 2 * (c.dst_hi[0] - c.dst_lo[0]) * (c.dst_hi[1] - c.dst_lo[1])
+    return per * n + 80.0 * ghosts
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0:
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2012_02925_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM traffic per launch from a committed ncu summary, valid only for the
+    kernel sources it was captured from."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except Exception:
+        return {}
+    return t if t.get("kernel_hash") == kernel_hash() else {}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def make_solver(pb, precision, tile=0, kchunk=0):
+    import torch
+    import paper_2012_02925_gb300 as fv
+    s = fv.Solver.from_problem(pb, precision=precision, tile=tile, kchunk=kchunk)
+    s.set_state(torch.from_numpy(pb.q).cuda())
+    if pb.source is not None:
+        s.set_source(torch.from_numpy(np.concatenate([x.ravel() for x in pb.source])).cuda())
+    torch.cuda.synchronize()
+    return s
+
+
+def time_steps(s, pb, steps, warmup, use_graph=True):
+    import torch
+    for _ in range(warmup):
+        s.rk_step(pb.dt, use_graph=use_graph)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        s.rk_step(pb.dt, use_graph=use_graph)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_stage_kernels(s, pb, reps):
+    """Average device time of each RK stage launch (exchange + fused kernel)
+    and of the exchange alone, CUDA events on the launching stream."""
+    import torch
+    st = torch.cuda.current_stream()
+    M = s.n_stages
+    out = []
+    for m in range(1, M + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.rk_stage(m, pb.dt)
+        e0.record(st)
+        for _ in range(reps):
+            s.rk_stage(m, pb.dt)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3 / reps)
+    ex = 0.0
+    if pb.conns:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            s.exchange_ghosts(0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ex = e0.elapsed_time(e1) / 1e3 / reps
+    return out, ex
+
+
+def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, traffic):
+    M = len(stage_times)
+    kt = [max(t - ex_time, 1e-12) for t in stage_times]
+    byts = [algorithmic_bytes(pb, m + 1, curvilinear) - (80.0 * 0 if not pb.conns else 0.0) for m in range(M)]
+    gbs = sum(byts) / sum(kt) / 1e9
+    hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    r = {"kernel": "fv_stage_kernel<%s>" % precision, "bytes_per_launch": sum(byts) / M,
+         "avg_launch_s": sum(kt) / M}
+    if precision == "fp32flux":
+        r.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "peak_source": peak_kind})
+    else:
+        # FP64 and double-float forms are bound by arithmetic issue:
+        # report the HBM fraction too so that the two bounds can be compared.
+        r.update({"bound": "alu", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "peak_source": peak_kind, "note": "HBM fraction of an ALU-bound kernel"})
+    t = traffic.get(precision)
+    r["traffic"] = t
+    return r
+
+
+def run_gpu(args):
+    import torch
+    import paper_2012_02925_gb300 as fv  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pb = workload(args.workload)
+    curv = pb.blocks[0].nodes is not None
+    s = make_solver(pb, args.precision, args.tile, args.kchunk)
+    M = s.n_stages
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            s.rk_step(pb.dt, use_graph=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        elapsed = time_steps(s, pb, args.steps, 0)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    cell_updates = pb.ncells * M * args.steps * world
+    value = cell_updates / elapsed / 1e9
+    pk, peak_kind = peaks()
+    traffic = load_traffic()
+    stage_times, ex_time = time_stage_kernels(s, pb, max(3, args.steps // 2))
+    roof = roofline(pb, args.precision, stage_times, ex_time, curv, pk, peak_kind, traffic)
+    # end to end through the public API with host buffers
+    e2e = run_e2e(s, pb, max(3, args.steps // 4))
+    launches_per_step = M * (2 if pb.conns else 1)
+    result = {
+        "metric": "Gcell-updates/s per RK stage",
+        "value": value,
+        "unit": "Gcell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "df64": "f64 state / f32x2 double-float arithmetic",
+                  "fp32flux": "f64 state / f32 flux / f32x2+f64 accumulate+update"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": pb.name, "cells": pb.ncells, "blocks": len(pb.blocks), "rk_stages": M,
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "l2_flush": "inputs larger than L2 (state+metrics %.0f MB)" % (
+                       (3 * 5 * 8 * pb.ncells + (80 if curv else 0) * pb.ncells) / 1e6)},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "stage_kernel_ms": [t * 1e3 for t in stage_times],
+    }
+    if args.variants and rank == 0 and world == 1:
+        result["variants"] = run_variants(args, pk, peak_kind, traffic)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args.workload)
+    s.close()
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(s, pb, steps):
+    """Same metric through the public API with HOST buffers: per step the
+    state goes host->device (pinned), one RK step runs, and the residual norms
+    (the step's monitored result, 10 doubles) come back to the host."""
+    import torch
+    host = torch.from_numpy(pb.q).pin_memory()
+    s.set_state(host)
+    s.rk_step(pb.dt, use_graph=True)
+    s.residual_norms(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(host)
+        s.rk_step(pb.dt, use_graph=True)
+        s.residual_norms(0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
+            "h2d_bytes_per_step": int(pb.q.nbytes), "d2h_bytes_per_step": 80}
+
+
+def run_variants(args, pk, peak_kind, traffic):
+    out = []
+    specs = [(w, p) for w in args.variant_workloads.split(",") for p in args.variant_precisions.split(",")]
+    for wname, prec in specs:
+        if wname == args.workload and prec == args.precision:
+            continue
+        try:
+            pb = workload(wname)
+            curv = pb.blocks[0].nodes is not None
+            s = make_solver(pb, prec)
+            steps = max(3, args.steps // 2)
+            el = time_steps(s, pb, steps, 3)
+            st, ex = time_stage_kernels(s, pb, 3)
+            out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
+                        "value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
+                        "roofline": roofline(pb, prec, st, ex, curv, pk, peak_kind, traffic)})
+            s.close()
+        except Exception as e:  # report, do not hide
+            out.append({"workload": wname, "precision": prec, "error": str(e)})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------
+
+def oracle_sample(name: str):
+    """Bounded sample of the workload: for the 128^3 block, its first 16
+    k-planes (same nodes, state, ghosts from the neighbouring planes and
+    source) - 262,144 cells."""
+    pb = workload(name)
+    if name != "mms128":
+        return pb, "full workload"
+    b = pb.blocks[0]
+    nk = 16
+    q = cases.unpack_state(pb.blocks, pb.q)[0][:, :nk + 4].copy()
+    nb = cases.BlockDesc(b.ni, b.nj, nk, b.nodes[:nk + 1].copy())
+    src = [pb.source[0][:, :nk].copy()]
+    sp = cases.Problem([nb], [], 3, cases.pack_state([nb], [q]), src, pb.dt, dict(pb.params), pb.name + "_k16")
+    return sp, "first 16 of 128 k-planes of the 128^3 block (262,144 cells), full RK steps"
+
+
+def cpu_baseline(name: str, steps: int = 1):
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    sp, desc = oracle_sample(name)
+    o = oracle.Oracle(sp, threads=cores)
+    q = sp.q.copy()
+    M = len(sp.params["alpha"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q = o.run(q, sp.dt, M)
+    el = time.perf_counter() - t0
+    return {"value": sp.ncells * M * steps / el / 1e9, "unit": "Gcell-updates/s", "cores": cores,
+            "kind": "oracle", "sample": desc + ", %d step(s) of %d stages, %.1f s" % (steps, M, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    sp, desc = oracle_sample(args.workload)
+    o = oracle.Oracle(sp, threads=cores)
+    M = len(sp.params["alpha"])
+    q = sp.q.copy()
+    for _ in range(args.warmup):
+        q = o.run(q, sp.dt, M)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q = o.run(q, sp.dt, M)
+    el = time.perf_counter() - t0
+    v = sp.ncells * M * args.steps / el / 1e9
+    res = {"impl": "reference", "metric": "Gcell-updates/s per RK stage", "value": v, "unit": "Gcell-updates/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": sp.name, "cells": sp.ncells, "rk_stages": M},
+           "cpu_baseline": {"value": v, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fvgb", choices=["fvgb", "reference"])
+    ap.add_argument("--workload", default="mms128")
+    ap.add_argument("--precision", default="df64", choices=["fp64", "df64", "fp32flux"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--kchunk", type=int, default=0)
+    ap.add_argument("--variants", type=int, default=1)
+    ap.add_argument("--variant-workloads", default="mms128,multiblock")
+    ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * fvgb - explicit finite-volume Euler residual and Runge-Kutta stage of a
+ * multi-block structured-grid solver, on one GPU (C ABI).
+ *
+ * The method is the one of Xue, Jackson and Roy, "An improved framework of
+ * GPU computing for CFD applications on structured grids using OpenACC"
+ * (arXiv 2012.02925):
+ *   - cell-centred conserved variables Q = (rho, rho u, rho v, rho w, rho e_t)
+ *     and the weak form of Eq. (governing), Section 2;
+ *   - MUSCL reconstruction of the primitive variables with slope limiter,
+ *     Eq. (flux) of Section 7.2 (V4);
+ *   - Roe's flux-difference splitting as the face flux, Section 2;
+ *   - two ghost layers per block face; connected faces take their ghosts from
+ *     the neighbouring block each sub-step, Section 2 and Section 4;
+ *   - explicit M-step Runge-Kutta time marching, Section 2.
+ *
+ * Conventions used by every call:
+ *   - A block has interior cells i in [0,ni), j in [0,nj), k in [0,nk) and two
+ *     ghost layers on every side.
+ *   - "Packed ghosted state": for each block in order, 5 variable planes of
+ *     (nk+4) x (nj+4) x (ni+4) doubles (i fastest), interior cell (i,j,k) at
+ *     ((k+2)(nj+4) + (j+2))(ni+4) + (i+2) of its plane.  fv_state_size() gives
+ *     the total number of doubles.
+ *   - "Packed interior field": for each block in order, 5 planes of
+ *     nk x nj x ni doubles.  fv_field_size() gives the total.
+ *   - Faces are numbered imin, imax, jmin, jmax, kmin, kmax = 0..5.
+ *   - Pointers named *_dev are device pointers; pointers documented as "host
+ *     or device" may be either (the copy direction is inferred through
+ *     unified addressing).  The caller owns every pointer it passes; the
+ *     library reads or writes it only during the call's stream work.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *     work and return without synchronising unless documented otherwise.
+ *   - Every call returns an fv_status; the message of the last failure on a
+ *     handle is fv_last_error(handle).  No call aborts, traps or throws.
+ */
+#ifndef FVGB_H
+#define FVGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FV_OK = 0,
+  FV_ERR_INVALID_ARG = 1,   /* bad handle, size, range, overlap, stage, ... */
+  FV_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  FV_ERR_OOM = 3,           /* device allocation failed */
+  FV_ERR_NONFINITE = 4,     /* a residual norm found NaN or Inf */
+  FV_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait expired */
+  FV_ERR_UNSUPPORTED = 6    /* option not built (tile shape, precision, ...) */
+} fv_status;
+
+/* Arithmetic of the face computations.  The state in memory is always IEEE
+ * binary64 and the residual sum and RK update keep binary64 accuracy. */
+typedef enum {
+  FV_PREC_FP64 = 0,      /* every operation in IEEE binary64 */
+  FV_PREC_DF64 = 1,      /* face arithmetic in double-float (pairs of binary32,
+                            ~48-bit significand) on the FP32 pipe */
+  FV_PREC_FP32FLUX = 2   /* limiter / reconstruction / Roe flux in binary32;
+                            flux differences, source, RK update in double-float
+                            / binary64 */
+} fv_precision;
+
+typedef enum { FV_LIM_NONE = 0, FV_LIM_VANLEER = 1, FV_LIM_VANALBADA = 2 } fv_limiter;
+
+typedef struct fv_ctx* fv_handle;
+
+/* One block.  nodes: HOST pointer to (nk+1)(nj+1)(ni+1) x 3 doubles
+ * (xyz fastest, then i, j, k) for a curvilinear block, or NULL for a
+ * Cartesian block with origin x0 and spacing h.  Copied during
+ * fv_create_blocks. */
+typedef struct {
+  int ni, nj, nk;
+  const double* nodes;
+  double x0[3];
+  double h[3];
+} fv_block_desc;
+
+/* Ghost layers of dst_face of dst_block are filled from src_block (Section 2:
+ * ghost cells of connected boundaries carry the neighbouring block's data;
+ * Section 5: self-connection is allowed).  The dst patch covers tangential
+ * cell indices [dst_lo[0], dst_hi[0]) x [dst_lo[1], dst_hi[1]) (tangential
+ * axes in i, j, k order without the face normal).  src_lo holds the src
+ * tangential indices of the cell that dst corner dst_lo maps to;
+ * transform[t] = +-1 or +-2 names the src tangential axis (1-based, signed)
+ * along which one step of dst tangential axis t moves.  Ghost depth d = 1, 2
+ * takes the src interior cell at depth d from src_face.  Momentum components
+ * are copied unrotated (one global Cartesian frame). */
+typedef struct {
+  int dst_block, dst_face;
+  int dst_lo[2], dst_hi[2];
+  int src_block, src_face;
+  int src_lo[2];
+  int transform[2];
+} fv_connection;
+
+/* Method parameters.  Readings of points the paper leaves open:
+ *   limiter: van Leer Psi(r) = (r+|r|)/(1+|r|); van Albada in the smooth
+ *     product form Psi(a/b) b = b (a^2+ab)/(a^2+b^2+va_delta2); NONE: Psi = 1.
+ *   eps, kappa: MUSCL parameters of Eq. (flux) (eps=1, kappa=-1 by default).
+ *   harten: Harten entropy-fix width as a fraction of the Roe sound speed, on
+ *     the acoustic eigenvalues (and on V_n too when fix_all); 0 = off.
+ *   dim: 2 (nk must be 1; no zeta fluxes) or 3.
+ *   n_stages, alpha: Q^(m) = Q^(0) - alpha[m-1] dt / Omega R(Q^(m-1)),
+ *     m = 1..n_stages (2..8).
+ *   tile: 0 = automatic; else an index into the compiled tile shapes
+ *     (1: 32x8 cells / 256 threads, 2: 32x4 / 128, 3: 16x8 / 128, 4: 30x8 / 256).
+ *   kchunk: k-planes per tile, 0 = automatic. */
+typedef struct {
+  double gamma, eps, kappa, harten, va_delta2;
+  int limiter, fix_all, dim, n_stages;
+  double alpha[8];
+  int precision;
+  int tile;
+  int kchunk;
+} fv_config;
+
+/* Fill *cfg with the defaults: gamma 1.4, eps 1, kappa -1, van Leer,
+ * harten 0.1, fix_all 0, va_delta2 1e-12, dim 3, 4 stages with
+ * alpha = (1/4, 1/3, 1/2, 1), FV_PREC_FP64, automatic tiles. */
+void fv_config_default(fv_config* cfg);
+
+/* Create the solver state on the current CUDA device: validates blocks and
+ * connections (ranges inside the faces, no ghost cell filled twice), computes
+ * the face vectors S = 1/2 (x_c - x_a) x (x_d - x_b), unit normals, areas and
+ * volumes (1/3 sum of face-centroid . S) on the device, builds the tile and
+ * connection tables and allocates three state buffers (Q^(0) and two stage
+ * buffers).  Blocking.  *out receives the handle (NULL on failure).  The
+ * error text of a failed create is available from fv_last_error(NULL). */
+int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connection* conns, int nconn,
+                     const fv_config* cfg, fv_handle* out);
+
+/* Release every device resource of the handle (synchronises the device). */
+int fv_destroy(fv_handle h);
+
+/* Message of the last failing call on `h` (or of the last failed create when
+ * h is NULL).  Owned by the library; valid until the next call on `h`. */
+const char* fv_last_error(fv_handle h);
+
+/* Sizes (in doubles) of the packed ghosted state and of the packed interior
+ * field; number of interior cells. -1 for a bad handle. */
+int64_t fv_state_size(fv_handle h);
+int64_t fv_field_size(fv_handle h);
+int64_t fv_cell_count(fv_handle h);
+
+/* Set Q^(0) (and both stage buffers, so that fixed ghost values are present
+ * in all of them) from a packed ghosted state (host or device).  Ghost cells
+ * not covered by a connection keep these values for the life of the state
+ * (fixed / Dirichlet ghosts). */
+int fv_set_state(fv_handle h, const double* q, void* stream);
+
+/* Copy buffer `buffer` (0 = Q^(0), the current solution; 1, 2 = stage
+ * buffers) out as a packed ghosted state (host or device destination).  With
+ * a host destination the call synchronises `stream`. */
+int fv_get_state(fv_handle h, int buffer, double* q, void* stream);
+
+/* Source term per unit volume at the cell centroids as a packed interior
+ * field (host or device), S of Eq. (governing); the library stores S * Omega.
+ * NULL removes the source. */
+int fv_set_source(fv_handle h, const double* s, void* stream);
+
+/* Connected-boundary ghost fill of state buffer `buffer`: for every
+ * connection, ghost cells at depth 1 and 2 of the dst patch <- src interior
+ * cells at the same depth (Section 2, Section 4; Section 7.2 V1 packs such
+ * slabs for MPI - on one device the copy is direct).  One kernel launch. */
+int fv_exchange_ghosts(fv_handle h, int buffer, void* stream);
+
+/* Residual R = sum over faces of F^(V_L, V_R) |S| - S Omega of buffer
+ * `buffer` as it stands (no exchange), written to r_dev as a packed interior
+ * field (device pointer, fv_field_size doubles).  Sum order per cell: xi pair,
+ * eta pair, zeta pair, source. */
+int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
+
+/* Runge-Kutta stage m (1..n_stages) with time step dt: exchange the ghosts of
+ * Q^(m-1), evaluate R(Q^(m-1)) and write Q^(m) = Q^(0) - alpha_m dt / Omega R
+ * (stage 1 reads Q^(0); the last stage writes Q^(0)).  Two kernel launches
+ * (exchange, fused residual + update). */
+int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
+
+/* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage
+ * sequence is captured once per (stream, dt) as a CUDA graph and replayed. */
+int fv_rk_step(fv_handle h, double dt, int use_graph, void* stream);
+
+/* Residual norms of buffer `buffer` (after a ghost exchange of it): per
+ * variable L2 = sqrt(mean over all interior cells of R^2) in out_host[0..4]
+ * and Linf = max |R| in out_host[5..9] (host pointer, 10 doubles).
+ * Synchronises `stream`.  Returns FV_ERR_NONFINITE when any R is NaN/Inf. */
+int fv_residual_norms(fv_handle h, int buffer, double* out_host, void* stream);
+
+/* Discrete-adjoint vector-Jacobian product of one RK stage m with step dt.
+ * Stage map: Q^(m) = Q^(0) - alpha_m dt / Omega R(X(Q^(m-1))) with X the
+ * ghost exchange.  Inputs: qin_dev = the stage input Q^(m-1) (packed ghosted
+ * state, device), lam_out_dev = dJ/dQ^(m) (packed interior field).  Outputs:
+ * lam_in_dev (packed interior field) <- (dQ^(m)/dQ^(m-1))^T lam_out,
+ * including the transpose of the exchange (ghost cotangents added into their
+ * donor cells); lam_q0_dev (packed interior field) += lam_out.  qin_dev is
+ * not modified.  Fixed ghost cells are constants. */
+int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
+                   double* lam_in_dev, double* lam_q0_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVGB_H */

@@ -1,0 +1,802 @@
+// Host runtime of the C ABI declared in include/fvgb.h, and the small kernels
+// around the fused stage kernel: metrics, ghost exchange, residual norms,
+// source scaling.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/fvgb.h"
+#include "fv_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct fv_ctx {
+  fv_config cfg;
+  int nblocks = 0, nconn = 0;
+  std::vector<FvBlockDev> hb;
+  std::vector<fv_connection> conns;
+  FvBlockDev* d_blocks = nullptr;
+  FvTile* d_tiles = nullptr;
+  int ntiles = 0;
+  FvLaunch launch{};
+  FvConnDev* d_conns = nullptr;
+  long long conn_items = 0;
+  double* buf[3] = {nullptr, nullptr, nullptr};
+  long long state_elems = 0;        // internal layout, doubles per buffer
+  long long ext_state_elems = 0;    // packed ghosted layout
+  long long ncell = 0;              // interior cells, all blocks
+  void* metric[3] = {nullptr, nullptr, nullptr};
+  long long nfaces[3] = {0, 0, 0};
+  double* invvol = nullptr;
+  double* vol = nullptr;
+  double* srcvol = nullptr;
+  double* scratch_r = nullptr;      // residual (variable-major) for norms
+  double* partials = nullptr;       // per-CTA norm partials
+  double* d_norm = nullptr;         // 11 doubles
+  double* adj_scratch = nullptr;    // adjoint work space (lazily allocated)
+  long long adj_scratch_elems = 0;
+  int device = 0, nsm = 0;
+  std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+namespace {
+
+int fail(fv_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(fv_ctx* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                          \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+inline long long ghosted_cells(int ni, int nj, int nk) {
+  return (long long)(ni + 2 * FV_GHOST) * (nj + 2 * FV_GHOST) * (nk + 2 * FV_GHOST);
+}
+
+int storage_bytes(int precision) {
+  return precision == FV_PREC_FP64 ? 8 : (precision == FV_PREC_DF64 ? 8 : 4);
+}
+
+// ---------------------------------------------------------------------------
+// metrics: face vectors S = 1/2 (x_c - x_a) x (x_d - x_b), unit normals,
+// areas, volumes = 1/3 sum of (face centroid . outward S)
+// ---------------------------------------------------------------------------
+struct NodeView {
+  const double* x;
+  int ni, nj;
+  __device__ const double* at(int i, int j, int k) const {
+    return x + 3 * (((long long)k * (nj + 1) + j) * (ni + 1) + i);
+  }
+};
+
+__device__ void cross_half(const double* a, const double* b, const double* c, const double* d, double* S) {
+  double d1[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double d2[3] = {d[0] - b[0], d[1] - b[1], d[2] - b[2]};
+  S[0] = 0.5 * (d1[1] * d2[2] - d1[2] * d2[1]);
+  S[1] = 0.5 * (d1[2] * d2[0] - d1[0] * d2[2]);
+  S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
+}
+
+// face (dir, i, j, k): the low face of cell (i,j,k) normal to `dir`, nodes in order a b c d
+__device__ void face_nodes(const NodeView& N, int dir, int i, int j, int k, const double* p[4]) {
+  if (dir == 0) { p[0] = N.at(i, j, k); p[1] = N.at(i, j + 1, k); p[2] = N.at(i, j + 1, k + 1); p[3] = N.at(i, j, k + 1); }
+  else if (dir == 1) { p[0] = N.at(i, j, k); p[1] = N.at(i, j, k + 1); p[2] = N.at(i + 1, j, k + 1); p[3] = N.at(i + 1, j, k); }
+  else { p[0] = N.at(i, j, k); p[1] = N.at(i + 1, j, k); p[2] = N.at(i + 1, j + 1, k); p[3] = N.at(i, j + 1, k); }
+}
+
+__device__ __forceinline__ void store_metric(double* m, long long idx, double v) { m[idx] = v; }
+__device__ __forceinline__ void store_metric(float2* m, long long idx, double v) {
+  float h = (float)v;
+  m[idx] = make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ void store_metric(float* m, long long idx, double v) { m[idx] = (float)v; }
+
+template <class MT>
+__global__ void metrics_faces_kernel(const double* nodes, int ni, int nj, int nk, int dir, MT* out,
+                                     long long off, long long mstride) {
+  const int ei = ni + (dir == 0), ej = nj + (dir == 1), ek = nk + (dir == 2);
+  const long long n = (long long)ei * ej * ek;
+  NodeView N{nodes, ni, nj};
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n; f += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(f % ei);
+    const int j = (int)((f / ei) % ej);
+    const int k = (int)(f / ((long long)ei * ej));
+    const double* p[4];
+    face_nodes(N, dir, i, j, k, p);
+    double S[3];
+    cross_half(p[0], p[1], p[2], p[3], S);
+    const double A = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    store_metric(out, off + f, S[0] / A);
+    store_metric(out, off + f + mstride, S[1] / A);
+    store_metric(out, off + f + 2 * mstride, S[2] / A);
+    store_metric(out, off + f + 3 * mstride, A);
+  }
+}
+
+__global__ void volume_kernel(const double* nodes, int ni, int nj, int nk, double* vol, double* invvol) {
+  const long long n = (long long)ni * nj * nk;
+  NodeView N{nodes, ni, nj};
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % ni), j = (int)((c / ni) % nj), k = (int)(c / ((long long)ni * nj));
+    double acc = 0.0;
+    for (int dir = 0; dir < 3; ++dir)
+      for (int side = 0; side < 2; ++side) {
+        const double* p[4];
+        face_nodes(N, dir, i + (dir == 0 ? side : 0), j + (dir == 1 ? side : 0), k + (dir == 2 ? side : 0), p);
+        double S[3];
+        cross_half(p[0], p[1], p[2], p[3], S);
+        double m[3];
+        for (int x = 0; x < 3; ++x) m[x] = 0.25 * (p[0][x] + p[1][x] + p[2][x] + p[3][x]);
+        const double dot = m[0] * S[0] + m[1] * S[1] + m[2] * S[2];
+        acc += side ? dot : -dot;
+      }
+    const double v = acc / 3.0;
+    vol[c] = v;
+    invvol[c] = 1.0 / v;
+  }
+}
+
+__global__ void fill_kernel(double* p, long long n, double v) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) p[x] = v;
+}
+
+// S * Omega from S per unit volume (interior field layout)
+__global__ void source_scale_kernel(const double* s, const double* vol, double* out, long long off5, long long ncell_b,
+                                    long long cell_off) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < 5 * ncell_b; x += (long long)gridDim.x * blockDim.x) {
+    const long long c = x % ncell_b;
+    out[off5 + x] = s[off5 + x] * vol[cell_off + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ghost exchange: work item = (connection, tangential a, b, depth d)
+// ---------------------------------------------------------------------------
+__global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvConnDev* __restrict__ conns, int nconn,
+                                long long nitems, double* q) {
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
+       it += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nconn - 1;
+    while (lo < hi) {               // last connection with item_off <= it
+      const int mid = (lo + hi + 1) >> 1;
+      if (conns[mid].item_off <= it) lo = mid; else hi = mid - 1;
+    }
+    const FvConnDev c = conns[lo];
+    long long local = it - c.item_off;
+    const int a = (int)(local % c.L0);
+    local /= c.L0;
+    const int b = (int)(local % c.L1);
+    const int d = (int)(local / c.L1) + 1;
+    const FvBlockDev& D = blocks[c.dst_block];
+    const FvBlockDev& S = blocks[c.src_block];
+    const int da = c.dst_face >> 1, sa = c.src_face >> 1;
+    const int dext[3] = {D.ni, D.nj, D.nk}, sext[3] = {S.ni, S.nj, S.nk};
+    int dc[3], sc[3];
+    const int dt0 = da == 0 ? 1 : 0, dt1 = da == 2 ? 1 : 2;
+    const int st0 = sa == 0 ? 1 : 0, st1 = sa == 2 ? 1 : 2;
+    dc[dt0] = c.dlo0 + a;
+    dc[dt1] = c.dlo1 + b;
+    dc[da] = (c.dst_face & 1) ? dext[da] - 1 + d : -d;
+    int st[2] = {c.slo0, c.slo1};
+    const int u0 = (c.t0 < 0 ? -c.t0 : c.t0) - 1, u1 = (c.t1 < 0 ? -c.t1 : c.t1) - 1;
+    st[u0] += c.t0 > 0 ? a : -a;
+    st[u1] += c.t1 > 0 ? b : -b;
+    sc[st0] = st[0];
+    sc[st1] = st[1];
+    sc[sa] = (c.src_face & 1) ? sext[sa] - d : d - 1;
+    const long long di = D.qoff + (long long)(dc[2] + 2) * D.kstride + (long long)(dc[1] + 2) * D.jstride + (dc[0] + 2);
+    const long long si = S.qoff + (long long)(sc[2] + 2) * S.kstride + (long long)(sc[1] + 2) * S.jstride + (sc[0] + 2);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[di + v * D.plane] = q[si + v * S.plane];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// residual norms (deterministic two-level reduction)
+// ---------------------------------------------------------------------------
+constexpr int NORM_THREADS = 256;
+
+__global__ void norm_partial_kernel(const double* __restrict__ r, long long n_per_var, double* partials) {
+  __shared__ double ssum[NORM_THREADS / 32], smax[NORM_THREADS / 32];
+  __shared__ int sbad[NORM_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = 0; v < 5; ++v) {
+    double s = 0.0, m = 0.0;
+    int bad = 0;
+    const double* rv = r + v * n_per_var;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n_per_var; x += (long long)gridDim.x * blockDim.x) {
+      const double y = rv[x];
+      if (!isfinite(y)) bad = 1;
+      s += y * y;
+      m = fmax(m, fabs(y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+      bad |= __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) { ssum[warp] = s; smax[warp] = m; sbad[warp] = bad; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ts = 0.0, tm = 0.0;
+      int tb = 0;
+      for (int w = 0; w < NORM_THREADS / 32; ++w) { ts += ssum[w]; tm = fmax(tm, smax[w]); tb |= sbad[w]; }
+      partials[(v * 3 + 0) * gridDim.x + blockIdx.x] = ts;
+      partials[(v * 3 + 1) * gridDim.x + blockIdx.x] = tm;
+      partials[(v * 3 + 2) * gridDim.x + blockIdx.x] = tb;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void norm_final_kernel(const double* partials, int nparts, long long n_per_var, double* out) {
+  const int v = threadIdx.x;
+  if (v < 5) {
+    double s = 0.0, m = 0.0, b = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      s += partials[(v * 3 + 0) * nparts + p];
+      m = fmax(m, partials[(v * 3 + 1) * nparts + p]);
+      b += partials[(v * 3 + 2) * nparts + p];
+    }
+    out[v] = sqrt(s / (double)n_per_var);
+    out[5 + v] = m;
+    out[10 + v] = b;
+  }
+}
+
+int grid_for(long long n, int threads, int nsm) {
+  long long g = (n + threads - 1) / threads;
+  return (int)std::max<long long>(1, std::min<long long>(g, (long long)nsm * 16));
+}
+
+fv_ctx* H(fv_handle h) { return reinterpret_cast<fv_ctx*>(h); }
+
+int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
+  int rc;
+  switch (h->cfg.precision) {
+    case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, h->launch, s); break;
+    case FV_PREC_DF64: rc = fv_launch_stage_df64(a, h->launch, s); break;
+    default: rc = fv_launch_stage_fp32(a, h->launch, s); break;
+  }
+  if (rc == -2) return fail(h, FV_ERR_UNSUPPORTED, "tile shape not compiled");
+  if (rc != 0) return cuda_fail(h, cudaGetLastError(), "stage kernel launch");
+  return FV_OK;
+}
+
+FvStageArgs base_args(fv_ctx* h) {
+  FvStageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.blocks = h->d_blocks;
+  a.tiles = h->d_tiles;
+  a.ntiles = h->ntiles;
+  for (int d = 0; d < 3; ++d) { a.metric[d] = h->metric[d]; a.mstride[d] = h->nfaces[d]; }
+  a.invvol = h->invvol;
+  a.srcvol = h->srcvol;
+  a.ncell_total = h->ncell;
+  a.fp.gamma = h->cfg.gamma;
+  a.fp.eps = h->cfg.eps;
+  a.fp.kappa = h->cfg.kappa;
+  a.fp.harten = h->cfg.harten;
+  a.fp.va_delta2 = h->cfg.va_delta2;
+  a.fp.limiter = h->cfg.limiter;
+  a.fp.fix_all = h->cfg.fix_all;
+  return a;
+}
+
+int stage_in(const fv_ctx* h, int m) {
+  if (m == 1) return 0;
+  const int M = h->cfg.n_stages;
+  const int prev = m - 1;
+  return prev == M ? 0 : ((prev & 1) ? 1 : 2);
+}
+int stage_out(const fv_ctx* h, int m) {
+  return m == h->cfg.n_stages ? 0 : ((m & 1) ? 1 : 2);
+}
+
+int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
+  if (h->conn_items == 0) return FV_OK;
+  const int threads = 256;
+  exchange_kernel<<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(h->d_blocks, h->d_conns, h->nconn,
+                                                                            h->conn_items, q);
+  CK(h, cudaGetLastError());
+  return FV_OK;
+}
+
+int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
+  const int bi = stage_in(h, m), bo = stage_out(h, m);
+  int rc = do_exchange(h, h->buf[bi], s);
+  if (rc) return rc;
+  FvStageArgs a = base_args(h);
+  a.mode = FV_MODE_RK;
+  a.qin = h->buf[bi];
+  a.q0 = h->buf[0];
+  a.qout = h->buf[bo];
+  a.alpha_dt = h->cfg.alpha[m - 1] * dt;
+  return launch_stage(h, a, s);
+}
+
+// copy between the packed ghosted layout and the internal layout (identical
+// when pitch == ni+4)
+int copy_state(fv_ctx* h, const double* src, double* dst, bool to_internal, cudaStream_t s) {
+  long long ext = 0;
+  for (const FvBlockDev& b : h->hb) {
+    const long long cells = ghosted_cells(b.ni, b.nj, b.nk);
+    const size_t wbytes = sizeof(double) * (b.ni + 4);
+    const size_t rows = (size_t)(b.nj + 4) * (b.nk + 4);
+    for (int v = 0; v < 5; ++v) {
+      const double* e = (to_internal ? src : dst) + ext + v * cells;
+      double* in = (to_internal ? dst : const_cast<double*>(src)) + b.qoff + v * b.plane;
+      if (to_internal)
+        CK(h, cudaMemcpy2DAsync(in, sizeof(double) * b.pitch, e, wbytes, wbytes, rows, cudaMemcpyDefault, s));
+      else
+        CK(h, cudaMemcpy2DAsync(const_cast<double*>(e), wbytes, in, sizeof(double) * b.pitch, wbytes, rows,
+                                cudaMemcpyDefault, s));
+    }
+    ext += 5 * cells;
+  }
+  return FV_OK;
+}
+
+void choose_launch(fv_ctx* h) {
+  const fv_config& c = h->cfg;
+  const bool d3 = c.dim == 3;
+  FvLaunch l{};
+  l.three_d = d3;
+  int shape = c.tile;
+  if (shape <= 0) {
+    // automatic: narrow blocks prefer narrow tiles
+    int maxni = 0;
+    for (auto& b : h->hb) maxni = std::max(maxni, b.ni);
+    shape = maxni >= 24 ? 1 : 3;
+  }
+  static const int shapes[5][3] = {{32, 8, 256}, {32, 8, 256}, {32, 4, 128}, {16, 8, 128}, {30, 8, 256}};
+  shape = std::min(std::max(shape, 1), 4);
+  l.tx = shapes[shape][0];
+  l.ty = shapes[shape][1];
+  l.threads = shapes[shape][2];
+  h->launch = l;
+}
+
+int query_occupancy(fv_ctx* h, size_t* smem) {
+  switch (h->cfg.precision) {
+    case FV_PREC_FP64: return fv_stage_occupancy_fp64(h->launch, smem);
+    case FV_PREC_DF64: return fv_stage_occupancy_df64(h->launch, smem);
+    default: return fv_stage_occupancy_fp32(h->launch, smem);
+  }
+}
+
+int build_tiles(fv_ctx* h) {
+  const FvLaunch& l = h->launch;
+  size_t smem = 0;
+  const int occ = query_occupancy(h, &smem);
+  if (occ <= 0) return fail(h, FV_ERR_UNSUPPORTED, "stage kernel cannot be resident with this tile shape");
+  const long long slots = (long long)h->nsm * occ;
+  long long columns = 0;
+  for (auto& b : h->hb) columns += (long long)((b.ni + l.tx - 1) / l.tx) * ((b.nj + l.ty - 1) / l.ty);
+  std::vector<FvTile> tiles;
+  std::vector<long long> cost;
+  for (int bi = 0; bi < (int)h->hb.size(); ++bi) {
+    const FvBlockDev& b = h->hb[bi];
+    int kc = h->cfg.kchunk;
+    if (h->cfg.dim == 2) kc = 1;
+    else if (kc <= 0) {
+      // split k so that the whole problem fills the resident CTA slots a few times
+      const long long want = std::max<long long>(1, (3 * slots + columns - 1) / std::max<long long>(columns, 1));
+      kc = (int)std::max<long long>(4, (b.nk + want - 1) / want);
+    }
+    kc = std::min(kc, b.nk);
+    for (int k0 = 0; k0 < b.nk; k0 += kc)
+      for (int j0 = 0; j0 < b.nj; j0 += l.ty)
+        for (int i0 = 0; i0 < b.ni; i0 += l.tx) {
+          const int k1 = std::min(b.nk, k0 + kc);
+          FvTile t{bi, i0, j0, k0 | (k1 << 16)};
+          tiles.push_back(t);
+          cost.push_back((long long)std::min(l.tx, b.ni - i0) * std::min(l.ty, b.nj - j0) * (k1 - k0 + 2));
+        }
+  }
+  // largest tiles first (static round-robin assignment then balances better)
+  std::vector<int> order(tiles.size());
+  for (size_t x = 0; x < order.size(); ++x) order[x] = (int)x;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<FvTile> sorted;
+  for (int x : order) sorted.push_back(tiles[x]);
+  h->ntiles = (int)sorted.size();
+  h->launch.grid = (int)std::min<long long>(h->ntiles, slots);
+  CK(h, cudaMalloc(&h->d_tiles, sizeof(FvTile) * sorted.size()));
+  CK(h, cudaMemcpy(h->d_tiles, sorted.data(), sizeof(FvTile) * sorted.size(), cudaMemcpyHostToDevice));
+  return FV_OK;
+}
+
+int validate(const fv_block_desc* blocks, int nblocks, const fv_connection* conns, int nconn, const fv_config* cfg) {
+  if (!blocks || nblocks <= 0) return fail(nullptr, FV_ERR_INVALID_ARG, "no blocks");
+  if (!cfg) return fail(nullptr, FV_ERR_INVALID_ARG, "no config");
+  if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, FV_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (cfg->n_stages < 2 || cfg->n_stages > 8) return fail(nullptr, FV_ERR_INVALID_ARG, "n_stages must be 2..8");
+  if (cfg->precision < 0 || cfg->precision > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown precision");
+  if (cfg->limiter < 0 || cfg->limiter > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown limiter");
+  if (!(cfg->gamma > 1.0)) return fail(nullptr, FV_ERR_INVALID_ARG, "gamma must exceed 1");
+  for (int b = 0; b < nblocks; ++b) {
+    const fv_block_desc& d = blocks[b];
+    if (d.ni < 1 || d.nj < 1 || d.nk < 1 || d.ni > 32000 || d.nj > 32000 || d.nk > 16000)
+      return fail(nullptr, FV_ERR_INVALID_ARG, "block " + std::to_string(b) + ": extents out of range");
+    if (cfg->dim == 2 && d.nk != 1) return fail(nullptr, FV_ERR_INVALID_ARG, "dim 2 needs nk == 1");
+    if (!d.nodes && !(d.h[0] > 0 && d.h[1] > 0 && d.h[2] > 0))
+      return fail(nullptr, FV_ERR_INVALID_ARG, "block " + std::to_string(b) + ": Cartesian spacing must be positive");
+  }
+  // ranges and overlap of dst ghost patches
+  std::vector<std::vector<std::vector<char>>> used(nblocks, std::vector<std::vector<char>>(6));
+  for (int c = 0; c < nconn; ++c) {
+    const fv_connection& x = conns[c];
+    const std::string tag = "connection " + std::to_string(c) + ": ";
+    if (x.dst_block < 0 || x.dst_block >= nblocks || x.src_block < 0 || x.src_block >= nblocks)
+      return fail(nullptr, FV_ERR_INVALID_ARG, tag + "block index out of range");
+    if (x.dst_face < 0 || x.dst_face > 5 || x.src_face < 0 || x.src_face > 5)
+      return fail(nullptr, FV_ERR_INVALID_ARG, tag + "face out of range");
+    if (cfg->dim == 2 && (x.dst_face >= 4 || x.src_face >= 4))
+      return fail(nullptr, FV_ERR_INVALID_ARG, tag + "k faces do not exist in 2D");
+    const fv_block_desc& D = blocks[x.dst_block];
+    const fv_block_desc& S = blocks[x.src_block];
+    const int dext[3] = {D.ni, D.nj, D.nk}, sext[3] = {S.ni, S.nj, S.nk};
+    const int da = x.dst_face / 2, sa = x.src_face / 2;
+    int dt[2], st[2], n = 0, m = 0;
+    for (int a = 0; a < 3; ++a) { if (a != da) dt[n++] = a; if (a != sa) st[m++] = a; }
+    for (int t = 0; t < 2; ++t)
+      if (x.dst_lo[t] < 0 || x.dst_hi[t] > dext[dt[t]] || x.dst_lo[t] >= x.dst_hi[t])
+        return fail(nullptr, FV_ERR_INVALID_ARG, tag + "dst patch outside the face");
+    const int t0 = x.transform[0], t1 = x.transform[1];
+    if (!(std::abs(t0) == 1 || std::abs(t0) == 2) || !(std::abs(t1) == 1 || std::abs(t1) == 2) || std::abs(t0) == std::abs(t1))
+      return fail(nullptr, FV_ERR_INVALID_ARG, tag + "transform must be a signed permutation of (1,2)");
+    if (sext[sa] < FV_GHOST) return fail(nullptr, FV_ERR_INVALID_ARG, tag + "src block thinner than the ghost depth");
+    for (int t = 0; t < 2; ++t) {
+      const int T = t == 0 ? t0 : t1;
+      const int u = std::abs(T) - 1;
+      const int L = x.dst_hi[t] - x.dst_lo[t];
+      const int first = x.src_lo[u], last = x.src_lo[u] + (T > 0 ? L - 1 : -(L - 1));
+      if (std::min(first, last) < 0 || std::max(first, last) >= sext[st[u]])
+        return fail(nullptr, FV_ERR_INVALID_ARG, tag + "src patch outside the src face");
+    }
+    auto& u = used[x.dst_block][x.dst_face];
+    if (u.empty()) u.assign((size_t)dext[dt[0]] * dext[dt[1]], 0);
+    for (int b = x.dst_lo[1]; b < x.dst_hi[1]; ++b)
+      for (int a = x.dst_lo[0]; a < x.dst_hi[0]; ++a) {
+        char& f = u[(size_t)b * dext[dt[0]] + a];
+        if (f) return fail(nullptr, FV_ERR_INVALID_ARG, tag + "dst ghost cells already filled by another connection");
+        f = 1;
+      }
+  }
+  return FV_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fv_config_default(fv_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->gamma = 1.4;
+  c->eps = 1.0;
+  c->kappa = -1.0;
+  c->harten = 0.1;
+  c->va_delta2 = 1e-12;
+  c->limiter = FV_LIM_VANLEER;
+  c->fix_all = 0;
+  c->dim = 3;
+  c->n_stages = 4;
+  c->alpha[0] = 0.25;
+  c->alpha[1] = 1.0 / 3.0;
+  c->alpha[2] = 0.5;
+  c->alpha[3] = 1.0;
+  c->precision = FV_PREC_FP64;
+}
+
+const char* fv_last_error(fv_handle h) {
+  if (!h) return g_create_error.c_str();
+  return H(h)->err.c_str();
+}
+
+int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connection* conns, int nconn,
+                     const fv_config* cfg, fv_handle* out) {
+  if (!out) return fail(nullptr, FV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nconn < 0 || (nconn > 0 && !conns)) return fail(nullptr, FV_ERR_INVALID_ARG, "bad connection list");
+  int rc = validate(blocks, nblocks, conns, nconn, cfg);
+  if (rc) return rc;
+  std::unique_ptr<fv_ctx> h(new fv_ctx());
+  h->cfg = *cfg;
+  h->nblocks = nblocks;
+  h->nconn = nconn;
+  h->conns.assign(conns, conns + nconn);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return fail(nullptr, FV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+  // ---- layout ----
+  long long qoff = 0, cell_off = 0, foff[3] = {0, 0, 0};
+  for (int b = 0; b < nblocks; ++b) {
+    const fv_block_desc& d = blocks[b];
+    FvBlockDev B;
+    std::memset(&B, 0, sizeof(B));
+    B.ni = d.ni; B.nj = d.nj; B.nk = d.nk;
+    B.pitch = d.ni + 2 * FV_GHOST;
+    B.jstride = B.pitch;
+    B.kstride = (long long)B.pitch * (d.nj + 2 * FV_GHOST);
+    B.plane = B.kstride * (d.nk + 2 * FV_GHOST);
+    B.qoff = qoff;
+    qoff += 5 * B.plane;
+    B.cell_off = cell_off;
+    cell_off += (long long)d.ni * d.nj * d.nk;
+    B.cartesian = d.nodes == nullptr;
+    if (B.cartesian) {
+      const double hx = d.h[0], hy = d.h[1], hz = d.h[2];
+      for (int x = 0; x < 3; ++x) for (int y = 0; y < 3; ++y) B.cart_n[x][y] = x == y ? 1.0 : 0.0;
+      B.cart_area[0] = hy * hz; B.cart_area[1] = hx * hz; B.cart_area[2] = hx * hy;
+      B.cart_invvol = 1.0 / (hx * hy * hz);
+    } else {
+      B.face_off[0] = foff[0]; foff[0] += (long long)(d.ni + 1) * d.nj * d.nk;
+      B.face_off[1] = foff[1]; foff[1] += (long long)d.ni * (d.nj + 1) * d.nk;
+      B.face_off[2] = foff[2]; foff[2] += (long long)d.ni * d.nj * (d.nk + 1);
+    }
+    h->hb.push_back(B);
+  }
+  h->state_elems = qoff;
+  h->ext_state_elems = 0;
+  for (auto& B : h->hb) h->ext_state_elems += 5 * ghosted_cells(B.ni, B.nj, B.nk);
+  h->ncell = cell_off;
+  for (int d = 0; d < 3; ++d) h->nfaces[d] = foff[d];
+  fv_ctx* hp = h.get();
+  // ---- allocations ----
+  for (int x = 0; x < 3; ++x) CK(hp, cudaMalloc(&h->buf[x], sizeof(double) * h->state_elems));
+  CK(hp, cudaMalloc(&h->d_blocks, sizeof(FvBlockDev) * nblocks));
+  CK(hp, cudaMalloc(&h->invvol, sizeof(double) * h->ncell));
+  CK(hp, cudaMalloc(&h->vol, sizeof(double) * h->ncell));
+  const int mb = storage_bytes(cfg->precision);
+  for (int d = 0; d < 3; ++d)
+    if (h->nfaces[d]) CK(hp, cudaMalloc(&h->metric[d], (size_t)mb * 4 * h->nfaces[d]));
+  // ---- metrics ----
+  double* d_nodes = nullptr;
+  for (int b = 0; b < nblocks; ++b) {
+    const FvBlockDev& B = h->hb[b];
+    const long long nc = (long long)B.ni * B.nj * B.nk;
+    if (B.cartesian) {
+      fill_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(h->invvol + B.cell_off, nc, B.cart_invvol);
+      fill_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(h->vol + B.cell_off, nc, 1.0 / B.cart_invvol);
+      continue;
+    }
+    const long long nn = 3LL * (B.ni + 1) * (B.nj + 1) * (B.nk + 1);
+    if (d_nodes) cudaFree(d_nodes);
+    CK(hp, cudaMalloc(&d_nodes, sizeof(double) * nn));
+    CK(hp, cudaMemcpy(d_nodes, blocks[b].nodes, sizeof(double) * nn, cudaMemcpyHostToDevice));
+    for (int dir = 0; dir < 3; ++dir) {
+      const long long nf = (long long)(B.ni + (dir == 0)) * (B.nj + (dir == 1)) * (B.nk + (dir == 2));
+      const int g = grid_for(nf, 256, h->nsm);
+      if (cfg->precision == FV_PREC_FP64)
+        metrics_faces_kernel<<<g, 256>>>(d_nodes, B.ni, B.nj, B.nk, dir, (double*)h->metric[dir], B.face_off[dir], h->nfaces[dir]);
+      else if (cfg->precision == FV_PREC_DF64)
+        metrics_faces_kernel<<<g, 256>>>(d_nodes, B.ni, B.nj, B.nk, dir, (float2*)h->metric[dir], B.face_off[dir], h->nfaces[dir]);
+      else
+        metrics_faces_kernel<<<g, 256>>>(d_nodes, B.ni, B.nj, B.nk, dir, (float*)h->metric[dir], B.face_off[dir], h->nfaces[dir]);
+    }
+    volume_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(d_nodes, B.ni, B.nj, B.nk, h->vol + B.cell_off, h->invvol + B.cell_off);
+    CK(hp, cudaDeviceSynchronize());
+  }
+  if (d_nodes) cudaFree(d_nodes);
+  CK(hp, cudaGetLastError());
+  CK(hp, cudaMemcpy(h->d_blocks, h->hb.data(), sizeof(FvBlockDev) * nblocks, cudaMemcpyHostToDevice));
+  // ---- connections ----
+  if (nconn) {
+    std::vector<FvConnDev> cd(nconn);
+    long long items = 0;
+    for (int c = 0; c < nconn; ++c) {
+      const fv_connection& x = conns[c];
+      FvConnDev& y = cd[c];
+      y.dst_block = x.dst_block; y.dst_face = x.dst_face;
+      y.dlo0 = x.dst_lo[0]; y.dlo1 = x.dst_lo[1];
+      y.L0 = x.dst_hi[0] - x.dst_lo[0]; y.L1 = x.dst_hi[1] - x.dst_lo[1];
+      y.src_block = x.src_block; y.src_face = x.src_face;
+      y.slo0 = x.src_lo[0]; y.slo1 = x.src_lo[1];
+      y.t0 = x.transform[0]; y.t1 = x.transform[1];
+      y.item_off = items;
+      items += 2LL * y.L0 * y.L1;
+    }
+    h->conn_items = items;
+    CK(hp, cudaMalloc(&h->d_conns, sizeof(FvConnDev) * nconn));
+    CK(hp, cudaMemcpy(h->d_conns, cd.data(), sizeof(FvConnDev) * nconn, cudaMemcpyHostToDevice));
+  }
+  // ---- tiles ----
+  choose_launch(hp);
+  rc = build_tiles(hp);
+  if (rc) { g_create_error = h->err; fv_destroy(reinterpret_cast<fv_handle>(h.release())); return rc; }
+  CK(hp, cudaDeviceSynchronize());
+  *out = reinterpret_cast<fv_handle>(h.release());
+  return FV_OK;
+}
+
+int fv_destroy(fv_handle hh) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  cudaDeviceSynchronize();
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  for (int x = 0; x < 3; ++x) cudaFree(h->buf[x]);
+  for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
+  cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns);
+  cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol);
+  cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm); cudaFree(h->adj_scratch);
+  delete h;
+  return FV_OK;
+}
+
+int64_t fv_state_size(fv_handle h) { return h ? H(h)->ext_state_elems : -1; }
+int64_t fv_field_size(fv_handle h) { return h ? 5 * H(h)->ncell : -1; }
+int64_t fv_cell_count(fv_handle h) { return h ? H(h)->ncell : -1; }
+
+int fv_set_state(fv_handle hh, const double* q, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!q) return fail(h, FV_ERR_INVALID_ARG, "q is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = copy_state(h, q, h->buf[0], true, s);
+  if (rc) return rc;
+  for (int x = 1; x < 3; ++x)
+    CK(h, cudaMemcpyAsync(h->buf[x], h->buf[0], sizeof(double) * h->state_elems, cudaMemcpyDeviceToDevice, s));
+  return FV_OK;
+}
+
+int fv_get_state(fv_handle hh, int buffer, double* q, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!q) return fail(h, FV_ERR_INVALID_ARG, "q is NULL");
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = copy_state(h, h->buf[buffer], q, false, s);
+  if (rc) return rc;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, q) == cudaSuccess && at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    CK(h, cudaStreamSynchronize(s));
+  return FV_OK;
+}
+
+int fv_set_source(fv_handle hh, const double* src, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  if (!src) {
+    if (h->srcvol) { CK(h, cudaStreamSynchronize(s)); cudaFree(h->srcvol); h->srcvol = nullptr; }
+    return FV_OK;
+  }
+  if (!h->srcvol) CK(h, cudaMalloc(&h->srcvol, sizeof(double) * 5 * h->ncell));
+  CK(h, cudaMemcpyAsync(h->srcvol, src, sizeof(double) * 5 * h->ncell, cudaMemcpyDefault, s));
+  for (auto& B : h->hb) {
+    const long long nc = (long long)B.ni * B.nj * B.nk;
+    source_scale_kernel<<<grid_for(5 * nc, 256, h->nsm), 256, 0, s>>>(h->srcvol, h->vol, h->srcvol, 5 * B.cell_off, nc,
+                                                                    B.cell_off);
+  }
+  CK(h, cudaGetLastError());
+  return FV_OK;
+}
+
+int fv_exchange_ghosts(fv_handle hh, int buffer, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  return do_exchange(h, h->buf[buffer], (cudaStream_t)stream);
+}
+
+int fv_residual(fv_handle hh, int buffer, double* r_dev, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  if (!r_dev) return fail(h, FV_ERR_INVALID_ARG, "r_dev is NULL");
+  FvStageArgs a = base_args(h);
+  a.mode = FV_MODE_RESIDUAL;
+  a.qin = h->buf[buffer];
+  a.rout = r_dev;
+  a.rout_varmajor = 0;
+  return launch_stage(h, a, (cudaStream_t)stream);
+}
+
+int fv_rk_stage(fv_handle hh, int stage, double dt, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (stage < 1 || stage > h->cfg.n_stages) return fail(h, FV_ERR_INVALID_ARG, "stage out of range");
+  return do_stage(h, stage, dt, (cudaStream_t)stream);
+}
+
+int fv_rk_step(fv_handle hh, double dt, int use_graph, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) {
+    for (int m = 1; m <= h->cfg.n_stages; ++m) {
+      int rc = do_stage(h, m, dt, s);
+      if (rc) return rc;
+    }
+    return FV_OK;
+  }
+  auto key = std::make_pair(dt, s);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaStream_t cs;
+    CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(h, e, "cudaStreamBeginCapture"); }
+    int rc = FV_OK;
+    for (int m = 1; m <= h->cfg.n_stages && rc == FV_OK; ++m) rc = do_stage(h, m, dt, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    it = h->graphs.emplace(key, ex).first;
+  }
+  CK(h, cudaGraphLaunch(it->second, s));
+  return FV_OK;
+}
+
+int fv_residual_norms(fv_handle hh, int buffer, double* out_host, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  if (!out_host) return fail(h, FV_ERR_INVALID_ARG, "out_host is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nparts = h->nsm * 2;
+  if (!h->scratch_r) CK(h, cudaMalloc(&h->scratch_r, sizeof(double) * 5 * h->ncell));
+  if (!h->partials) CK(h, cudaMalloc(&h->partials, sizeof(double) * 15 * nparts));
+  if (!h->d_norm) CK(h, cudaMalloc(&h->d_norm, sizeof(double) * 16));
+  int rc = do_exchange(h, h->buf[buffer], s);
+  if (rc) return rc;
+  FvStageArgs a = base_args(h);
+  a.mode = FV_MODE_RESIDUAL;
+  a.qin = h->buf[buffer];
+  a.rout = h->scratch_r;
+  a.rout_varmajor = 1;
+  rc = launch_stage(h, a, s);
+  if (rc) return rc;
+  norm_partial_kernel<<<nparts, NORM_THREADS, 0, s>>>(h->scratch_r, h->ncell, h->partials);
+  norm_final_kernel<<<1, 32, 0, s>>>(h->partials, nparts, h->ncell, h->d_norm);
+  CK(h, cudaGetLastError());
+  double tmp[15];
+  CK(h, cudaMemcpyAsync(tmp, h->d_norm, sizeof(double) * 15, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  std::memcpy(out_host, tmp, sizeof(double) * 10);
+  for (int v = 0; v < 5; ++v)
+    if (tmp[10 + v] != 0.0) return fail(h, FV_ERR_NONFINITE, "residual has non-finite entries");
+  return FV_OK;
+}
+
+int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
+                   double* lam_in_dev, double* lam_q0_dev, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (stage < 1 || stage > h->cfg.n_stages) return fail(h, FV_ERR_INVALID_ARG, "stage out of range");
+  if (!qin_dev || !lam_out_dev || !lam_in_dev || !lam_q0_dev) return fail(h, FV_ERR_INVALID_ARG, "NULL pointer");
+  return fail(h, FV_ERR_UNSUPPORTED, "adjoint not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Scalar arithmetic back-ends of the face kernels.
+//
+// Three arithmetic types carry the same face-flux code:
+//   double : IEEE binary64 on the SM's FP64 unit;
+//   df64   : "double-float", an unevaluated sum hi + lo of two binary32
+//            numbers (about 48 significand bits) computed with error-free
+//            transformations on the FP32 pipe (Dekker 1971; Knuth TAOCP 2;
+//            Hida, Li, Bailey 2001);
+//   float  : IEEE binary32.
+// The state in memory is always IEEE binary64.  Conversions between binary64
+// and binary32 are done with integer operations on the bit patterns so that
+// they do not occupy the FP64 unit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define FV_HD __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// bit-level conversions
+// ---------------------------------------------------------------------------
+
+// binary64 -> binary32, round to nearest even.  Magnitudes below 2^-126 become
+// signed zero, overflow becomes infinity, NaN stays NaN.
+__device__ __forceinline__ float fv_d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned ahi = hi & 0x7fffffffu;
+  const unsigned e = ahi >> 20;
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  f = (e < 897u) ? 0u : f;
+  f = (e > 1150u) ? 0x7f800000u : f;
+  f = (e == 2047u) ? 0x7fc00000u : f;
+  return __int_as_float((int)(f | sign));
+}
+
+// binary32 -> binary64, exact (zero and normal numbers; subnormals flush).
+__device__ __forceinline__ double fv_f2d(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned a = u & 0x7fffffffu;
+  unsigned hi = (((a >> 23) + 896u) << 20) | ((a >> 3) & 0xfffffu);
+  unsigned lo = a << 29;
+  const bool zero = a < 0x00800000u;
+  const bool special = a >= 0x7f800000u;
+  hi = zero ? 0u : (special ? (0x7ff00000u | ((a >> 3) & 0xfffffu)) : hi);
+  lo = zero ? 0u : lo;
+  return __longlong_as_double((long long)(((unsigned long long)(hi | sign) << 32) | lo));
+}
+
+// ---------------------------------------------------------------------------
+// double-float
+// ---------------------------------------------------------------------------
+struct df64 {
+  float hi, lo;
+};
+
+FV_HD df64 mk(float h, float l) { df64 r; r.hi = h; r.lo = l; return r; }
+
+// binary32 operations that the compiler may neither contract into FMAs nor
+// reorder: the error-free transformations below depend on every rounding.
+#define FADD __fadd_rn
+#define FSUB __fsub_rn
+#define FMUL __fmul_rn
+#define FFMA __fmaf_rn
+
+// s + e = a + b exactly (any magnitudes)
+FV_HD df64 two_sum(float a, float b) {
+  float s = FADD(a, b);
+  float bb = FSUB(s, a);
+  float e = FADD(FSUB(a, FSUB(s, bb)), FSUB(b, bb));
+  return mk(s, e);
+}
+// s + e = a + b exactly when |a| >= |b|
+FV_HD df64 quick_two_sum(float a, float b) {
+  float s = FADD(a, b);
+  float e = FSUB(b, FSUB(s, a));
+  return mk(s, e);
+}
+FV_HD df64 two_prod(float a, float b) {
+  float p = FMUL(a, b);
+  float e = FFMA(a, b, -p);
+  return mk(p, e);
+}
+
+FV_HD df64 operator+(df64 a, df64 b) {
+  df64 s = two_sum(a.hi, b.hi);
+  df64 t = two_sum(a.lo, b.lo);
+  float lo = FADD(s.lo, t.hi);
+  s = quick_two_sum(s.hi, lo);
+  lo = FADD(s.lo, t.lo);
+  return quick_two_sum(s.hi, lo);
+}
+FV_HD df64 operator-(df64 a) { return mk(-a.hi, -a.lo); }
+FV_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
+FV_HD df64 operator*(df64 a, df64 b) {
+  df64 p = two_prod(a.hi, b.hi);
+  float e = FFMA(a.hi, b.lo, p.lo);
+  e = FFMA(a.lo, b.hi, e);
+  return quick_two_sum(p.hi, e);
+}
+FV_HD df64 operator*(df64 a, float b) {
+  df64 p = two_prod(a.hi, b);
+  float e = FFMA(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, e);
+}
+FV_HD df64 operator*(float b, df64 a) { return a * b; }
+
+__device__ __forceinline__ float fv_rcp(float x) { return __frcp_rn(x); }
+
+// a / b: a binary32 reciprocal estimate and two correction steps in double-float
+FV_HD df64 operator/(df64 a, df64 b) {
+  float r = fv_rcp(b.hi);
+  float q1 = FMUL(a.hi, r);
+  df64 rem = a - b * q1;
+  float q2 = FMUL(rem.hi, r);
+  df64 q = quick_two_sum(q1, q2);
+  rem = a - b * q;
+  float q3 = FMUL(rem.hi, r);
+  return q + mk(q3, 0.0f);
+}
+FV_HD df64 df_rcp(df64 b) { return mk(1.0f, 0.0f) / b; }
+
+FV_HD df64 df_sqrt(df64 a) {
+  if (!(a.hi > 0.0f)) return mk(a.hi == 0.0f ? 0.0f : __int_as_float(0x7fc00000), 0.0f);
+  float s = __fsqrt_rn(a.hi);
+  df64 e = a - two_prod(s, s);
+  float corr = FMUL(e.hi, FMUL(0.5f, fv_rcp(s)));
+  return quick_two_sum(s, corr);
+}
+FV_HD df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
+FV_HD bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+FV_HD bool operator>(df64 a, df64 b) { return b < a; }
+
+// binary64 -> double-float (hi = RN(x), lo = RN(x - hi)), bit operations only
+__device__ __forceinline__ df64 fv_d2df(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned ahi = hi & 0x7fffffffu;
+  const unsigned e = ahi >> 20;
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  f += up;
+  // remainder x - hi = (rem - up*2^29) * 2^(e-1075), |.| <= 2^28 * 2^(e-1075)
+  const int r = (int)rem - (int)(up << 29);
+  float lof = __int2float_rn(r);
+  // scale by 2^(e-1075): build the binary32 power of two when it is normal
+  const int pe = (int)e - 1075 + 127;
+  const float scale = __int_as_float(pe > 0 ? (pe << 23) : 0);
+  lof = FMUL(lof, scale);
+  if (sign) lof = -lof;
+  f = (e < 897u) ? 0u : f;
+  f = (e > 1150u) ? 0x7f800000u : f;
+  f = (e == 2047u) ? 0x7fc00000u : f;
+  lof = (e < 897u || e > 1150u) ? 0.0f : lof;
+  return mk(__int_as_float((int)(f | sign)), lof);
+}
+
+// double-float -> binary64 (exact conversions of both halves, one FP64 add)
+__device__ __forceinline__ double fv_df2d(df64 a) { return fv_f2d(a.hi) + fv_f2d(a.lo); }
+
+// ---------------------------------------------------------------------------
+// uniform scalar interface used by the face code
+// ---------------------------------------------------------------------------
+template <class T> struct Sc;
+
+template <> struct Sc<double> {
+  static __device__ __forceinline__ double from_d(double x) { return x; }
+  static __device__ __forceinline__ double to_d(double x) { return x; }
+  static __device__ __forceinline__ double c(double x) { return x; }     // constant
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double abs(double x) { return ::fabs(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ float hi(double x) { return (float)x; }
+  static __device__ __forceinline__ bool lt(double a, double b) { return a < b; }
+  static __device__ __forceinline__ bool pos(double a) { return a > 0.0; }
+};
+
+template <> struct Sc<float> {
+  static __device__ __forceinline__ float from_d(double x) { return fv_d2f_rn(x); }
+  static __device__ __forceinline__ double to_d(float x) { return fv_f2d(x); }
+  static __device__ __forceinline__ float c(double x) { return (float)x; }
+  static __device__ __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  static __device__ __forceinline__ float abs(float x) { return ::fabsf(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float hi(float x) { return x; }
+  static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+  static __device__ __forceinline__ bool pos(float a) { return a > 0.0f; }
+};
+
+template <> struct Sc<df64> {
+  static __device__ __forceinline__ df64 from_d(double x) { return fv_d2df(x); }
+  static __device__ __forceinline__ double to_d(df64 x) { return fv_df2d(x); }
+  // compile-time constants: split on the host side of the compiler
+  static __device__ __forceinline__ df64 c(double x) {
+    float h = (float)x;
+    return mk(h, (float)(x - (double)h));
+  }
+  static __device__ __forceinline__ df64 sqrt(df64 x) { return df_sqrt(x); }
+  static __device__ __forceinline__ df64 abs(df64 x) { return df_abs(x); }
+  static __device__ __forceinline__ df64 rcp(df64 x) { return df_rcp(x); }
+  static __device__ __forceinline__ float hi(df64 x) { return x.hi; }
+  static __device__ __forceinline__ bool lt(df64 a, df64 b) { return a < b; }
+  static __device__ __forceinline__ bool pos(df64 a) { return a.hi > 0.0f; }
+};

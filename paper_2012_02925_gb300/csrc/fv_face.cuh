@@ -1,0 +1,180 @@
+// Per-cell primitive recovery and per-face MUSCL reconstruction, slope
+// limiter and Roe flux, written once for every arithmetic type T.
+//
+//  * Section 2 (vector Q, inviscid normal flux F_{i,n}, Roe's flux-difference
+//    splitting, MUSCL on primitive variables);
+//  * Eq. (flux) of Section 7.2 (V4): the kappa-scheme with limiter values
+//    Psi^{+/-}; each limiter value multiplies the difference that is the
+//    denominator of its ratio, so a limited term is Psi(a/b) b.
+#pragma once
+#include "fv_arith.cuh"
+#include "fv_internal.h"
+
+template <class T>
+struct FaceC {
+  T gm1;          // gamma - 1
+  T g_gm1;        // gamma / (gamma - 1)
+  T half, one;
+  T e4km, e4kp;   // eps/4 (1 - kappa), eps/4 (1 + kappa)
+  T harten;       // entropy-fix width / c~
+  T va_d2;        // van Albada delta^2
+  int limiter, fix_all, has_fix;
+  int upwind_only;  // kappa == -1: the (1+kappa) terms of Eq. (flux) vanish
+};
+
+template <class T>
+__device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
+  using S = Sc<T>;
+  FaceC<T> c;
+  c.gm1 = S::from_d(p.gamma - 1.0);
+  c.g_gm1 = S::from_d(p.gamma / (p.gamma - 1.0));
+  c.half = S::from_d(0.5);
+  c.one = S::from_d(1.0);
+  c.e4km = S::from_d(p.eps * 0.25 * (1.0 - p.kappa));
+  c.e4kp = S::from_d(p.eps * 0.25 * (1.0 + p.kappa));
+  c.harten = S::from_d(p.harten);
+  c.va_d2 = S::from_d(p.va_delta2);
+  c.limiter = p.limiter;
+  c.fix_all = p.fix_all;
+  c.has_fix = p.harten > 0.0;
+  c.upwind_only = (p.kappa == -1.0);
+  return c;
+}
+
+// Q = (rho, rho u, rho v, rho w, rho e_t) -> V = (rho, u, v, w, p)
+template <class T>
+__device__ __forceinline__ void prim_from_cons(const FaceC<T>& C, const T q[5], T V[5]) {
+  T rinv = Sc<T>::rcp(q[0]);
+  T u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
+  V[0] = q[0];
+  V[1] = u;
+  V[2] = v;
+  V[3] = w;
+  V[4] = C.gm1 * (q[4] - C.half * q[0] * (u * u + v * v + w * w));
+}
+
+// Psi(a/b) * b
+template <class T>
+__device__ __forceinline__ T limited(const FaceC<T>& C, T a, T b) {
+  using S = Sc<T>;
+  if (C.limiter == 0) return b;
+  if (C.limiter == 1) {
+    // van Leer, Psi(r) = (r + |r|)/(1 + |r|):  Psi(a/b) b = (a|b| + |a| b)/(|a| + |b|)
+    T aa = S::abs(a), ab = S::abs(b);
+    T den = aa + ab;
+    if (!S::pos(den)) return S::c(0.0);
+    return (a * ab + aa * b) * S::rcp(den);
+  }
+  // van Albada in smooth product form: b (a^2 + a b)/(a^2 + b^2 + delta^2)
+  T a2 = a * a;
+  return b * (a2 + a * b) * S::rcp(a2 + b * b + C.va_d2);
+}
+
+// Eq. (flux) for one component from V_{i-1}, V_i, V_{i+1}, V_{i+2}
+template <class T>
+__device__ __forceinline__ void muscl(const FaceC<T>& C, T vm1, T v0, T vp1, T vp2, T& L, T& R) {
+  T dm = v0 - vm1, d0 = vp1 - v0, dp = vp2 - vp1;
+  if (C.upwind_only) {
+    L = v0 + C.e4km * limited(C, d0, dm);
+    R = vp1 - C.e4km * limited(C, d0, dp);
+  } else {
+    L = v0 + (C.e4km * limited(C, d0, dm) + C.e4kp * limited(C, dm, d0));
+    R = vp1 - (C.e4kp * limited(C, dp, d0) + C.e4km * limited(C, d0, dp));
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T entropy_fixed(const FaceC<T>& C, T lam, T delta) {
+  // Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d
+  if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * (C.half * Sc<T>::rcp(delta));
+  return lam;
+}
+
+// Roe flux times face area for reconstructed primitive states VL, VR and the
+// unit normal (nx, ny, nz) with area A.
+template <class T>
+__device__ __forceinline__ void roe_flux(const FaceC<T>& C, const T VL[5], const T VR[5], T nx, T ny,
+                                         T nz, T A, T out[5]) {
+  using S = Sc<T>;
+  const T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
+  const T rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
+  const T VnL = nx * uL + ny * vL + nz * wL;
+  const T VnR = nx * uR + ny * vR + nz * wR;
+  const T riL = S::rcp(rL), riR = S::rcp(rR);
+  const T hL = C.g_gm1 * pL * riL + C.half * (uL * uL + vL * vL + wL * wL);
+  const T hR = C.g_gm1 * pR * riR + C.half * (uR * uR + vR * vR + wR * wR);
+  const T mL = rL * VnL, mR = rR * VnR;
+
+  // Roe averages: R = sqrt(rho_R/rho_L), rho~ = rho_L R
+  const T Rt = S::sqrt(rR * riL);
+  const T rt = rL * Rt;
+  const T w1 = S::rcp(C.one + Rt);
+  const T ut = (uL + Rt * uR) * w1;
+  const T vt = (vL + Rt * vR) * w1;
+  const T wt = (wL + Rt * wR) * w1;
+  const T ht = (hL + Rt * hR) * w1;
+  const T q2h = C.half * (ut * ut + vt * vt + wt * wt);
+  const T c2 = C.gm1 * (ht - q2h);
+  const T ct = S::sqrt(c2);
+  const T ic2 = S::rcp(c2);
+  const T Vnt = nx * ut + ny * vt + nz * wt;
+
+  const T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
+  const T dVn = VnR - VnL;
+
+  T l1 = S::abs(Vnt - ct), l2 = S::abs(Vnt), l5 = S::abs(Vnt + ct);
+  if (C.has_fix) {
+    const T delta = C.harten * ct;
+    l1 = entropy_fixed(C, l1, delta);
+    l5 = entropy_fixed(C, l5, delta);
+    if (C.fix_all) l2 = entropy_fixed(C, l2, delta);
+  }
+  const T rcd = rt * ct * dVn;
+  const T hic2 = C.half * ic2;
+  const T a1 = l1 * (dp - rcd) * hic2;
+  const T a5 = l5 * (dp + rcd) * hic2;
+  const T a2 = l2 * (dr - dp * ic2);
+  const T a3 = l2 * rt;
+  const T a15 = a1 + a5, d51 = (a5 - a1) * ct;
+
+  // dissipation |dF1| + |dF234| + |dF5|
+  T D0 = a15 + a2;
+  T D1 = a15 * ut + d51 * nx + a2 * ut + a3 * (du - nx * dVn);
+  T D2 = a15 * vt + d51 * ny + a2 * vt + a3 * (dv - ny * dVn);
+  T D3 = a15 * wt + d51 * nz + a2 * wt + a3 * (dw - nz * dVn);
+  T D4 = a15 * ht + d51 * Vnt + a2 * q2h + a3 * (ut * du + vt * dv + wt * dw - Vnt * dVn);
+
+  const T hA = C.half * A;
+  out[0] = ((mL + mR) - D0) * hA;
+  out[1] = ((mL * uL + mR * uR + nx * (pL + pR)) - D1) * hA;
+  out[2] = ((mL * vL + mR * vR + ny * (pL + pR)) - D2) * hA;
+  out[3] = ((mL * wL + mR * wR + nz * (pL + pR)) - D3) * hA;
+  out[4] = ((mL * hL + mR * hR) - D4) * hA;
+}
+
+// Full face: reconstruct the 5 primitive components along the stencil
+// c0..c3 (pointers to component 0 of each cell, components `cs` apart) and
+// evaluate the Roe flux times area.
+template <class T>
+__device__ __forceinline__ void face_flux(const FaceC<T>& C, const T* c0, const T* c1, const T* c2,
+                                          const T* c3, int cs, T nx, T ny, T nz, T A, T out[5]) {
+  T VL[5], VR[5];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) muscl(C, c0[n * cs], c1[n * cs], c2[n * cs], c3[n * cs], VL[n], VR[n]);
+  roe_flux(C, VL, VR, nx, ny, nz, A, out);
+}
+
+// The double-float face is large; one out-of-line copy per kernel keeps the
+// code size (and the compile time) in check.  Constants come from shared
+// memory and results go straight to their shared-memory destination so that
+// the call needs no stack frame.
+template <class T>
+__device__ __noinline__ void face_flux_outlined(const FaceC<T>* __restrict__ Cp, const T* c0, const T* c1,
+                                                const T* c2, const T* c3, int cs, T nx, T ny, T nz, T A,
+                                                T* dst, int dstr) {
+  const FaceC<T> C = *Cp;
+  T out[5];
+  face_flux(C, c0, c1, c2, c3, cs, nx, ny, nz, A, out);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
+}

@@ -1,0 +1,77 @@
+// Internal data structures shared by the host runtime and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define FV_GHOST 2
+
+// One structured block as the kernels see it.  State buffers hold, per
+// block, 5 variable planes of (nk+4) x (nj+4) rows of `pitch` doubles
+// (i fastest, ghost cells inline, interior cell (i,j,k) at
+// ((k+2)*(nj+4) + (j+2))*pitch + (i+2)).
+struct FvBlockDev {
+  int ni, nj, nk, pitch;
+  long long jstride, kstride;   // = pitch, pitch*(nj+4)
+  long long plane;              // distance between variable planes (elements)
+  long long qoff;               // block offset inside a state buffer (elements)
+  long long cell_off;           // first interior cell in cell-indexed arrays
+  long long face_off[3];        // first face in the per-direction metric arrays
+  int cartesian;                // metrics are per-block constants
+  int pad_;
+  double cart_n[3][3];          // Cartesian unit normal of each face family
+  double cart_area[3];          // Cartesian face areas
+  double cart_invvol;           // Cartesian 1/volume
+};
+
+// One unit of work of the fused stage kernel: a TX x TY column of cells of a
+// block, marched from k0 to k1-1.
+struct FvTile {
+  int block, i0, j0, kk;        // kk = k0 | (k1 << 16)
+};
+
+struct FvConnDev {
+  int dst_block, dst_face, dlo0, dlo1, L0, L1;
+  int src_block, src_face, slo0, slo1, t0, t1;
+  long long item_off;           // first work item (a, b, depth) of this connection
+};
+
+struct FvFaceParams {
+  double gamma, eps, kappa, harten, va_delta2;
+  int limiter, fix_all;
+};
+
+enum { FV_MODE_RK = 0, FV_MODE_RESIDUAL = 1 };
+
+struct FvStageArgs {
+  const FvBlockDev* blocks;
+  const FvTile* tiles;
+  int ntiles;
+  int mode;
+  const double* qin;            // Q^(m-1)
+  const double* q0;             // Q^(0)
+  double* qout;                 // Q^(m)
+  const void* metric[3];        // per direction: nx, ny, nz, area planes
+  long long mstride[3];         // per direction: faces in all blocks (plane length)
+  const double* invvol;         // 1/Omega per interior cell
+  const double* srcvol;         // S*Omega, [block][5][cells], or null
+  double* rout;                 // residual output or null
+  int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
+  long long ncell_total;
+  double alpha_dt;              // alpha_m * dt
+  FvFaceParams fp;
+};
+
+// Kernel launchers, one translation unit per arithmetic form.
+struct FvLaunch {
+  int tx, ty, threads;          // tile shape
+  int grid;                     // CTAs (persistent)
+  int three_d;
+};
+
+int fv_launch_stage_fp64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_df64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+// occupancy queries: CTAs per SM for a tile shape (0 = shape not compiled)
+int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);

@@ -1,0 +1,298 @@
+// Fused residual + Runge-Kutta stage kernel (one template for every form).
+//
+// One CTA owns a TX x TY column of cells of one block and marches it through
+// k.  Per k-plane it
+//   1. stages the primitive variables of the newest plane (with a two-cell
+//      i/j halo) in shared memory, a ring of four planes for the zeta stencil;
+//   2. evaluates every face the tile needs exactly once - the (TX+1) x TY xi
+//      faces and TX x (TY+1) eta faces of the plane and the TX x TY zeta faces
+//      above it - as one balanced list spread over all threads;
+//   3. sums, per cell, R = (xi pair) + (eta pair) + (zeta pair) - S*Omega in
+//      that order (Section 2, Eq. (governing) discretised) and applies
+//      Q^(m) = Q^(0) - alpha_m dt / Omega * R (explicit M-step RK, Section 2),
+//      or writes R itself.
+// Nothing per face is written to global memory (the V4 design of Section 7.2
+// stored limiter and flux arrays; here they live in registers and shared
+// memory only).  Tiles come from a table, so one launch covers every block of
+// a multi-block problem.
+#pragma once
+#include <type_traits>
+#include "fv_face.cuh"
+
+template <class T> struct MetricStore;
+template <> struct MetricStore<double> {
+  using type = double;
+  static __device__ __forceinline__ double ld(const double* p, long long i) { return __ldg(p + i); }
+};
+template <> struct MetricStore<df64> {
+  using type = float2;
+  static __device__ __forceinline__ df64 ld(const float2* p, long long i) {
+    float2 v = __ldg(p + i);
+    return mk(v.x, v.y);
+  }
+};
+template <> struct MetricStore<float> {
+  using type = float;
+  static __device__ __forceinline__ float ld(const float* p, long long i) { return __ldg(p + i); }
+};
+
+// accumulation type: binary32 face fluxes are summed in double-float
+template <class T> struct Acc {
+  using type = T;
+  static __device__ __forceinline__ T diff(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T from_d(double x) { return Sc<T>::from_d(x); }
+};
+template <> struct Acc<float> {
+  using type = df64;
+  static __device__ __forceinline__ df64 diff(float a, float b) { return two_sum(a, -b); }
+  static __device__ __forceinline__ df64 from_d(double x) { return fv_d2df(x); }
+};
+
+// Q^(0) - fac * R in binary64, with fac = alpha dt / Omega
+__device__ __forceinline__ double rk_apply(double q0, double alpha_dt, double invvol, double R) {
+  return q0 - (alpha_dt * invvol) * R;
+}
+__device__ __forceinline__ double rk_apply(double q0, df64 fac, df64 R) {
+  df64 d = fac * R;
+  return q0 - fv_df2d(d);
+}
+
+template <class T, int TX, int TY>
+struct StageSmem {
+  static constexpr int W = TX + 4, H = TY + 4, PL = W * H;
+  static constexpr int NXI = (TX + 1) * TY, NETA = TX * (TY + 1), NZETA = TX * TY;
+  static constexpr size_t bytes(bool three_d) {
+    return sizeof(T) * (size_t)((three_d ? 4 : 1) * 5 * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0));
+  }
+};
+
+template <class T, int TX, int TY, int NT, bool DIM3>
+__global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
+  using S = Sc<T>;
+  using AT = typename Acc<T>::type;
+  using MT = typename MetricStore<T>::type;
+  using SM = StageSmem<T, TX, TY>;
+  constexpr int W = SM::W, PL = SM::PL;
+  constexpr int NXI = SM::NXI, NETA = SM::NETA, NZETA = SM::NZETA;
+  constexpr int NSLOT = DIM3 ? 4 : 1;
+  constexpr int NFACE = NXI + NETA + (DIM3 ? NZETA : 0);
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);        // [NSLOT][5][H][W]
+  T* Fx = Vs + NSLOT * 5 * PL;                    // [5][TY][TX+1]
+  T* Fy = Fx + 5 * NXI;                           // [5][TY+1][TX]
+  T* Fz = Fy + 5 * NETA;                          // [2][5][TY][TX]
+
+  const int tid = threadIdx.x;
+  const FaceC<T> C = make_face_consts<T>(args.fp);
+  __shared__ FaceC<T> Cs;
+  if (tid == 0) Cs = C;
+  __syncthreads();
+  const MT* mxi = reinterpret_cast<const MT*>(args.metric[0]);
+  const MT* meta = reinterpret_cast<const MT*>(args.metric[1]);
+  const MT* mzeta = reinterpret_cast<const MT*>(args.metric[2]);
+  const long long msx = args.mstride[0], msy = args.mstride[1], msz = args.mstride[2];
+
+  for (int tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
+    const FvTile td = args.tiles[tile];
+    const FvBlockDev& B = args.blocks[td.block];
+    const int ni = B.ni, nj = B.nj, nk = B.nk;
+    const int i0 = td.i0, j0 = td.j0, k0 = td.kk & 0xffff, k1 = td.kk >> 16;
+    const long long js = B.jstride, ks = B.kstride, pl = B.plane;
+    const double* qin = args.qin + B.qoff;
+    const bool cart = B.cartesian != 0;
+
+    // stage plane kk (ghosted index kk + 2 in memory) into ring slot `slot`
+    auto load_plane = [&](int kk, int slot) {
+      T* dst = Vs + slot * 5 * PL;
+      for (int it = tid; it < PL; it += NT) {
+        const int r = it / W, c = it - r * W;
+        const int j = j0 - 2 + r, i = i0 - 2 + c;
+        if (i < ni + 2 && j < nj + 2) {
+          const double* src = qin + (long long)(kk + 2) * ks + (long long)(j + 2) * js + (i + 2);
+          T q[5], V[5];
+#pragma unroll
+          for (int n = 0; n < 5; ++n) q[n] = S::from_d(__ldg(src + n * pl));
+          prim_from_cons(C, q, V);
+#pragma unroll
+          for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
+        }
+      }
+    };
+
+    // Evaluate one face from its stencil cells s0..s3 (ring/plane pointers),
+    // direction `dir` and face index f, storing the 5 fluxes at dst[n * dstr].
+    auto do_face = [&](const T* s0, const T* s1, const T* s2, const T* s3, int dir, long long f, T* dst,
+                       int dstr) {
+      T nx, ny, nz, A;
+      if (cart) {
+        nx = S::from_d(B.cart_n[dir][0]); ny = S::from_d(B.cart_n[dir][1]);
+        nz = S::from_d(B.cart_n[dir][2]); A = S::from_d(B.cart_area[dir]);
+      } else {
+        const MT* m = dir == 0 ? mxi : (dir == 1 ? meta : mzeta);
+        const long long ms = dir == 0 ? msx : (dir == 1 ? msy : msz);
+        nx = MetricStore<T>::ld(m, f); ny = MetricStore<T>::ld(m, f + ms);
+        nz = MetricStore<T>::ld(m, f + 2 * ms); A = MetricStore<T>::ld(m, f + 3 * ms);
+      }
+      if constexpr (std::is_same<T, df64>::value) {
+        face_flux_outlined(&Cs, s0, s1, s2, s3, PL, nx, ny, nz, A, dst, dstr);
+      } else {
+        T out[5];
+        face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
+      }
+    };
+    // zeta face between planes kf-1 and kf (stencil kf-2 .. kf+1) of tile column e = y*TX + x
+    auto zeta_face = [&](int kf, int e, T* dst) {
+      const int y = e / TX, x = e - y * TX;
+      if (i0 + x < ni && j0 + y < nj) {
+        const int c = (y + 2) * W + (x + 2);
+        const long long f = B.face_off[2] + ((long long)kf * nj + (j0 + y)) * ni + (i0 + x);
+        do_face(Vs + ((kf - 2) & 3) * 5 * PL + c, Vs + ((kf - 1) & 3) * 5 * PL + c, Vs + (kf & 3) * 5 * PL + c,
+                Vs + ((kf + 1) & 3) * 5 * PL + c, 2, f, dst, NZETA);
+      }
+    };
+
+    if (DIM3) {
+      for (int s = -2; s <= 1; ++s) load_plane(k0 + s, (k0 + s) & 3);
+      __syncthreads();
+      for (int it = tid; it < NZETA; it += NT) zeta_face(k0, it, Fz + (k0 & 1) * 5 * NZETA + it);
+      __syncthreads();
+    } else {
+      load_plane(0, 0);
+      __syncthreads();
+    }
+
+    for (int k = k0; k < k1; ++k) {
+      const int slot = DIM3 ? (k & 3) : 0;
+      if (DIM3) {
+        load_plane(k + 2, (k + 2) & 3);
+        __syncthreads();
+      }
+      const T* P = Vs + slot * 5 * PL;
+      // ---- every face of this plane (and the zeta faces above it), once ----
+      for (int it = tid; it < NFACE; it += NT) {
+        if (it < NXI) {
+          const int y = it / (TX + 1), x = it - y * (TX + 1);     // face between cells x-1 and x
+          const int i = i0 + x, j = j0 + y;
+          if (i <= ni && j < nj) {
+            const T* c0 = P + (y + 2) * W + x;                   // cell x-2
+            do_face(c0, c0 + 1, c0 + 2, c0 + 3, 0, B.face_off[0] + ((long long)k * nj + j) * (ni + 1) + i,
+                    Fx + it, NXI);
+          }
+        } else if (it < NXI + NETA) {
+          const int e = it - NXI;
+          const int y = e / TX, x = e - y * TX;                   // face between rows y-1 and y
+          const int i = i0 + x, j = j0 + y;
+          if (i < ni && j <= nj) {
+            const T* c0 = P + y * W + (x + 2);                   // row y-2
+            do_face(c0, c0 + W, c0 + 2 * W, c0 + 3 * W, 1,
+                    B.face_off[1] + ((long long)k * (nj + 1) + j) * ni + i, Fy + e, NETA);
+          }
+        } else if (DIM3) {
+          const int e = it - NXI - NETA;
+          zeta_face(k + 1, e, Fz + ((k + 1) & 1) * 5 * NZETA + e);
+        }
+      }
+      __syncthreads();
+      // ---- per cell: flux differences in a fixed order, then the RK update ----
+      if (tid < TX * TY) {
+        const int y = tid / TX, x = tid - y * TX;
+        const int i = i0 + x, j = j0 + y;
+        if (i < ni && j < nj) {
+          const long long cell = ((long long)k * nj + j) * ni + i;
+          const long long q_idx = (long long)(k + 2) * ks + (long long)(j + 2) * js + (i + 2);
+          const long long ncell_b = (long long)ni * nj * nk;
+          AT R[5];
+#pragma unroll
+          for (int n = 0; n < 5; ++n) {
+            AT rx = Acc<T>::diff(Fx[n * NXI + y * (TX + 1) + x + 1], Fx[n * NXI + y * (TX + 1) + x]);
+            AT ry = Acc<T>::diff(Fy[n * NETA + (y + 1) * TX + x], Fy[n * NETA + y * TX + x]);
+            AT r = rx + ry;
+            if (DIM3) {
+              AT rz = Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
+                                   Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
+              r = r + rz;
+            }
+            if (args.srcvol) r = r - Acc<T>::from_d(__ldg(args.srcvol + 5 * (B.cell_off) + n * ncell_b + cell));
+            R[n] = r;
+          }
+          if (args.mode == FV_MODE_RK) {
+            const double iv = cart ? B.cart_invvol : __ldg(args.invvol + B.cell_off + cell);
+            const double* q0 = args.q0 + B.qoff + q_idx;
+            double* qo = args.qout + B.qoff + q_idx;
+            if constexpr (std::is_same<AT, double>::value) {
+#pragma unroll
+              for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], args.alpha_dt, iv, R[n]);
+            } else {
+              const df64 fac = fv_d2df(args.alpha_dt) * fv_d2df(iv);
+#pragma unroll
+              for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], fac, R[n]);
+            }
+          } else {
+            double* ro = args.rout;
+            if (args.rout_varmajor) {
+#pragma unroll
+              for (int n = 0; n < 5; ++n) ro[n * args.ncell_total + B.cell_off + cell] = Sc<AT>::to_d(R[n]);
+            } else {
+#pragma unroll
+              for (int n = 0; n < 5; ++n) ro[5 * B.cell_off + n * ncell_b + cell] = Sc<AT>::to_d(R[n]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();   // smem is reused by the next tile
+  }
+}
+
+// The dynamic shared-memory limit is raised once by occupancy_t (at handle
+// creation), so a launch is a plain enqueue that stream capture accepts.
+template <class T, int TX, int TY, int NT>
+static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
+  const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0);
+  if (l.three_d) {
+    fv_stage_kernel<T, TX, TY, NT, true><<<l.grid, NT, smem, s>>>(a);
+  } else {
+    fv_stage_kernel<T, TX, TY, NT, false><<<l.grid, NT, smem, s>>>(a);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class T, int TX, int TY, int NT>
+static int occupancy_t(bool three_d, size_t* smem_out) {
+  const size_t smem = StageSmem<T, TX, TY>::bytes(three_d);
+  int n = 0;
+  if (three_d) {
+    auto k = fv_stage_kernel<T, TX, TY, NT, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
+  } else {
+    auto k = fv_stage_kernel<T, TX, TY, NT, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
+  }
+  if (smem_out) *smem_out = smem;
+  return n;
+}
+
+// Tile shapes compiled for every form: (TX, TY, threads)
+template <class T>
+int fv_dispatch_launch(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
+  if (l.tx == 32 && l.ty == 8 && l.threads == 256) return launch_stage_t<T, 32, 8, 256>(a, l, s);
+  if (l.tx == 32 && l.ty == 4 && l.threads == 128) return launch_stage_t<T, 32, 4, 128>(a, l, s);
+  if (l.tx == 16 && l.ty == 8 && l.threads == 128) return launch_stage_t<T, 16, 8, 128>(a, l, s);
+  if (l.tx == 30 && l.ty == 8 && l.threads == 256) return launch_stage_t<T, 30, 8, 256>(a, l, s);
+  return -2;
+}
+
+template <class T>
+int fv_dispatch_occupancy(const FvLaunch& l, size_t* smem) {
+  const bool d3 = l.three_d != 0;
+  if (l.tx == 32 && l.ty == 8 && l.threads == 256) return occupancy_t<T, 32, 8, 256>(d3, smem);
+  if (l.tx == 32 && l.ty == 4 && l.threads == 128) return occupancy_t<T, 32, 4, 128>(d3, smem);
+  if (l.tx == 16 && l.ty == 8 && l.threads == 128) return occupancy_t<T, 16, 8, 128>(d3, smem);
+  if (l.tx == 30 && l.ty == 8 && l.threads == 256) return occupancy_t<T, 30, 8, 256>(d3, smem);
+  return 0;
+}

@@ -1,0 +1,262 @@
+"""CUDA library vs CPU oracle, element by element, through the C ABI.
+
+Tolerances (relative L-infinity per variable, normalised by the field's
+maximum magnitude; paper Section 8 compares parallel and serial solutions the
+same way at 1e-12):
+  FP64 and DF64 forms: 1e-12 on one residual, 1e-10 after 100 RK stages;
+  FP32-flux form: 1e-5 on one residual (its drift over stages is reported by
+  the benchmark).
+Sizes span several tiles with ragged tails in i, j and k.
+"""
+import numpy as np
+import pytest
+
+import cases
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_RES = {"fp64": 1e-12, "df64": 1e-12, "fp32flux": 1e-5}
+TOL_RUN = {"fp64": 1e-10, "df64": 1e-10}
+
+
+def solver(pb, precision, **kw):
+    import paper_2012_02925_gb300 as fv
+    s = fv.Solver.from_problem(pb, precision=precision, **kw)
+    s.set_state(torch.from_numpy(pb.q).cuda())
+    if pb.source is not None:
+        s.set_source(torch.from_numpy(np.concatenate([x.ravel() for x in pb.source])).cuda())
+    return s
+
+
+def flux_scale(o, q):
+    """Per-variable magnitude of the terms a residual sums: the largest
+    physical normal flux |F_v(V_c) . e_d| over cells and axis directions times
+    the largest face area.  Rounding in any correct evaluation of R is relative
+    to this, not to R itself, which cancels down to the truncation error for a
+    manufactured solution or to zero for a free stream."""
+    scales = np.zeros(5)
+    smax = max(np.sqrt((m[d] ** 2).sum(0)).max() for m in o.metrics for d in range(3))
+    gm1 = o.params["gamma"] - 1.0
+    for qi in o.interior(q):
+        rho = qi[0]
+        u, v, w = qi[1] / rho, qi[2] / rho, qi[3] / rho
+        p = gm1 * (qi[4] - 0.5 * rho * (u * u + v * v + w * w))
+        H = (qi[4] + p) / rho
+        for d, vel in enumerate((u, v, w)):
+            F = (rho * vel, rho * u * vel + (d == 0) * p, rho * v * vel + (d == 1) * p,
+                 rho * w * vel + (d == 2) * p, rho * H * vel)
+            for x in range(5):
+                scales[x] = max(scales[x], np.abs(F[x]).max())
+    return scales * smax
+
+
+def rel_err_fields(a, b, o, q=None):
+    """max over variables of max|a-b| / max(max|b|, term scale) over all
+    blocks' packed interior fields."""
+    A = np.concatenate([a[o.roffs[n]:o.roffs[n + 1]].reshape(5, -1) for n in range(len(o.blocks))], axis=1)
+    B = np.concatenate([b[o.roffs[n]:o.roffs[n + 1]].reshape(5, -1) for n in range(len(o.blocks))], axis=1)
+    fs = flux_scale(o, q if q is not None else o.pb.q)
+    worst = 0.0
+    for v in range(5):
+        scale = max(np.abs(B[v]).max(), fs[v])
+        if scale == 0:
+            continue
+        worst = max(worst, np.abs(A[v] - B[v]).max() / scale)
+    return worst
+
+
+def rel_err_states(qa, qb, o):
+    ia = np.concatenate([x.reshape(5, -1) for x in o.interior(qa)], axis=1)
+    ib = np.concatenate([x.reshape(5, -1) for x in o.interior(qb)], axis=1)
+    return max(np.abs(ia[v] - ib[v]).max() / np.abs(ib[v]).max() for v in range(5) if np.abs(ib[v]).max() > 0)
+
+
+def residual_pair(pb, precision, exchange=True, **kw):
+    o = oracle.Oracle(pb)
+    q = pb.q.copy()
+    if exchange:
+        o.exchange(q)
+    r_ref = o.residual(q)
+    s = solver(pb, precision, **kw)
+    if exchange:
+        s.exchange_ghosts(0)
+    r = s.residual(0).cpu().numpy()
+    s.close()
+    return r, r_ref, o
+
+
+PRECS = ["fp64", "df64", "fp32flux"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_residual_vortex_2d(prec):
+    r, ref, o = residual_pair(cases.vortex_2d(64), prec)
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims", [(40, 19, 13), (24, 24, 24)])
+def test_residual_mms_curvilinear(prec, dims):
+    r, ref, o = residual_pair(cases.mms_3d(dims, curvilinear=True), prec, exchange=False)
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("opts", [dict(limiter=2, fix_all=1), dict(limiter=0), dict(kappa=1.0 / 3.0),
+                                  dict(eps=0.0), dict(harten=0.0)])
+def test_residual_method_options(prec, opts):
+    r, ref, o = residual_pair(cases.mms_3d((20, 11, 9), curvilinear=True, **opts), prec, exchange=False)
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+def test_residual_every_tile_shape(tile):
+    r, ref, o = residual_pair(cases.mms_3d((37, 21, 11), curvilinear=True), "fp64", exchange=False, tile=tile)
+    assert rel_err_fields(r, ref, o) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_free_stream_preserved(prec):
+    pb = cases.uniform_3d(20, curvilinear=True)
+    o = oracle.Oracle(pb)
+    s = solver(pb, prec)
+    r = s.residual(0).cpu().numpy()
+    s.close()
+    Smax = max(np.sqrt((m[0] ** 2).sum(0)).max() for m in o.metrics)
+    bound = {"fp64": 1e-13, "df64": 1e-13, "fp32flux": 1e-6}[prec]
+    assert np.abs(r).max() <= bound * Smax * 2.0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_residual_multiblock_random_connections(prec):
+    pb = cases.multiblock_batched(nblocks=12, lo=5, hi=21, seed=3)
+    r, ref, o = residual_pair(pb, prec)
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+
+
+def test_exchange_bit_exact():
+    pb = cases.multiblock_batched(nblocks=12, lo=5, hi=21, seed=4)
+    o = oracle.Oracle(pb)
+    rng = np.random.default_rng(0)
+    q = pb.q + rng.normal(size=pb.q.shape) * 1e-3
+    s = solver(pb, "fp64")
+    s.set_state(torch.from_numpy(q).cuda())
+    s.exchange_ghosts(0)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert np.array_equal(got, o.exchange(q.copy()))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_100_stages_vortex(prec):
+    pb = cases.vortex_2d(64)
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 100)
+    s = solver(pb, prec)
+    for st in range(100):
+        s.rk_stage(st % 4 + 1, pb.dt)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert rel_err_states(got, ref, o) <= TOL_RUN[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_100_stages_mms_graph(prec):
+    pb = cases.mms_3d((18, 13, 11), curvilinear=True)
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 100)
+    s = solver(pb, prec)
+    for _ in range(25):
+        s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert rel_err_states(got, ref, o) <= TOL_RUN[prec]
+
+
+def test_fp32flux_one_step_close():
+    pb = cases.mms_3d((18, 13, 11), curvilinear=True)
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 4)
+    s = solver(pb, "fp32flux")
+    s.rk_step(pb.dt, use_graph=False)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    # binary32 face fluxes carry ~1e-6 relative error (unit roundoff 6e-8 grown
+    # over the ~100 operations of a face); one step moves Q by dt R / Omega
+    assert rel_err_states(got, ref, o) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_multiblock_8_stages(prec):
+    pb = cases.multiblock_batched(nblocks=10, lo=5, hi=17, seed=5)
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 8)
+    s = solver(pb, prec)
+    s.rk_step(pb.dt, use_graph=True)
+    s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert rel_err_states(got, ref, o) <= TOL_RUN[prec]
+
+
+def test_rotated_split_gpu_matches_oracle():
+    pb = cases.rotated_split_problem(cases.mms_3d(12, curvilinear=True), 5)
+    r, ref, o = residual_pair(pb, "fp64")
+    assert rel_err_fields(r, ref, o) <= 1e-12
+
+
+def test_residual_norms_match_oracle():
+    pb = cases.vortex_2d(64)
+    o = oracle.Oracle(pb)
+    q = o.exchange(pb.q.copy())
+    l2_ref, linf_ref = o.norms(o.residual(q))
+    s = solver(pb, "fp64")
+    l2, linf = s.residual_norms(0)
+    s.close()
+    assert np.allclose(l2, l2_ref, rtol=1e-12, atol=1e-300)
+    assert np.allclose(linf, linf_ref, rtol=1e-12, atol=1e-300)
+
+
+def test_residual_norms_flag_nonfinite():
+    import paper_2012_02925_gb300 as fv
+    pb = cases.mms_3d(8, curvilinear=True)
+    q = pb.q.copy()
+    q[((3 + 2) * 12 + (3 + 2)) * 12 + (3 + 2)] = np.nan  # density of interior cell (3,3,3)
+    s = solver(pb, "fp64")
+    s.set_state(torch.from_numpy(q).cuda())
+    with pytest.raises(fv.FvError) as e:
+        s.residual_norms(0)
+    assert e.value.code == fv.FV_ERR_NONFINITE
+    s.close()
+
+
+def test_thin_blocks_and_fixed_ghosts():
+    pb = cases.mms_3d((1, 3, 5), curvilinear=True)
+    r, ref, o = residual_pair(pb, "fp64", exchange=False)
+    assert rel_err_fields(r, ref, o) <= 1e-12
+
+
+def test_host_buffers_roundtrip():
+    pb = cases.mms_3d((9, 7, 5), curvilinear=True)
+    import paper_2012_02925_gb300 as fv
+    s = fv.Solver.from_problem(pb, precision="fp64")
+    s.set_state(pb.q)                       # host pointer
+    out = np.zeros_like(pb.q)
+    s.get_state(0, out=out)                 # host destination (synchronous)
+    s.close()
+    assert np.array_equal(out, pb.q)
+
+
+def test_invalid_arguments_are_reported():
+    import paper_2012_02925_gb300 as fv
+    pb = cases.mms_3d(6, curvilinear=True)
+    bad = cases.Connection(0, 1, (0, 0), (7, 6), 0, 0, (0, 0), (1, 2))   # patch wider than the face
+    with pytest.raises(fv.FvError) as e:
+        fv.Solver(pb.blocks, [bad], 3, pb.params)
+    assert e.value.code == fv.FV_ERR_INVALID_ARG
+    s = solver(pb, "fp64")
+    with pytest.raises(fv.FvError):
+        s.rk_stage(9, 0.1)
+    s.close()
