@@ -200,6 +200,36 @@ int fv_residual_norms(fv_handle h, int buffer, double* out_host, void* stream);
 int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
                    double* lam_in_dev, double* lam_q0_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free residual norms.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while they
+ * run - code inside a CUDA-graph capture or a framework's caching allocator
+ * (where cudaMalloc would synchronise the device or fragment the pool),
+ * real-time or embedded hosts that forbid allocation after start-up, and
+ * plugins that only receive memory from their host application.
+ *
+ * field_dev: device pointer to 5 contiguous planes of n doubles (variable v at
+ *   field_dev + v*n), e.g. the packed interior field that fv_residual writes
+ *   for a one-block handle.  n must satisfy 1 <= n <= FV_NOALLOC_MAX_N.
+ * out_dev: device pointer to 11 doubles: per-variable L2 = sqrt(mean of
+ *   squares) in [0..4], Linf in [5..9], and in [10] the number of variables
+ *   that hold NaN or Inf.  Written asynchronously on `stream`.
+ * Partial sums (one slot per FV_NOALLOC_CHUNK elements) live in a fixed
+ * 120 KiB device array inside the library: it is held on every GPU that loads
+ * the library until the process exits, it is shared by every call, and calls
+ * whose kernels overlap on the GPU race on it (serialise them on one stream).
+ * The first call on a device looks up that array's device address, so make
+ * it before any stream capture that includes this call.  Nothing is
+ * allocated or freed.
+ * Returns FV_ERR_INVALID_ARG for NULL pointers or n outside
+ * [1, FV_NOALLOC_MAX_N], FV_ERR_CUDA when the address lookup or a launch
+ * fails, FV_ERR_UNSUPPORTED for device ordinals above 63.
+ * ------------------------------------------------------------------------- */
+#define FV_NOALLOC_CHUNK 65536
+#define FV_NOALLOC_MAX_N (1024LL * FV_NOALLOC_CHUNK)
+
+int fv_field_norms_noalloc(const double* field_dev, int64_t n, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
