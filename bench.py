@@ -151,13 +151,15 @@ def load_traffic():
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_solver(pb, precision, tile=0, kchunk=0):
+def make_solver(pb, precision, tile=0, kchunk=0, tune=True):
     import torch
     import paper_2012_02925_gb300 as fv
     s = fv.Solver.from_problem(pb, precision=precision, tile=tile, kchunk=kchunk)
     s.set_state(torch.from_numpy(pb.q).cuda())
     if pb.source is not None:
         s.set_source(torch.from_numpy(np.concatenate([x.ravel() for x in pb.source])).cuda())
+    if tune and tile == 0:
+        s.autotune(pb.dt)
     torch.cuda.synchronize()
     return s
 
@@ -287,6 +289,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "stage_kernel_ms": [t * 1e3 for t in stage_times],
+        "launch": s.launch(),
     }
     if args.variants and rank == 0 and world == 1:
         result["variants"] = run_variants(args, pk, peak_kind, traffic)
@@ -335,6 +338,7 @@ def run_variants(args, pk, peak_kind, traffic):
             st, ex = time_stage_kernels(s, pb, 3)
             out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
                         "value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
+                        "launch": s.launch(),
                         "roofline": roofline(pb, prec, st, ex, curv, pk, peak_kind, traffic)})
             s.close()
         except Exception as e:  # report, do not hide

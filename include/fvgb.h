@@ -189,6 +189,18 @@ int fv_rk_step(fv_handle h, double dt, int use_graph, void* stream);
  * Synchronises `stream`.  Returns FV_ERR_NONFINITE when any R is NaN/Inf. */
 int fv_residual_norms(fv_handle h, int buffer, double* out_host, void* stream);
 
+/* Autotuner of the batched launch (not in the paper): times `reps` launches
+ * of RK stage 1 with step dt for every compiled tile shape and a set of
+ * k-chunk lengths (planes per tile; automatic = enough tiles to fill the
+ * resident CTA slots about three times), keeps the fastest and discards
+ * cached step graphs.  Reads Q^(0), overwrites stage buffer 1: call it between
+ * steps.  Synchronises `stream`. */
+int fv_autotune(fv_handle h, double dt, int reps, void* stream);
+
+/* Current launch configuration: out4 = {tile shape (0 = automatic), k-chunk
+ * (0 = automatic), number of tiles, persistent CTAs}. */
+int fv_get_launch(fv_handle h, int* out4);
+
 /* Discrete-adjoint vector-Jacobian product of one RK stage m with step dt.
  * Stage map: Q^(m) = Q^(0) - alpha_m dt / Omega R(X(Q^(m-1))) with X the
  * ghost exchange.  Inputs: qin_dev = the stage input Q^(m-1) (packed ghosted

@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": PREC_FP64, "df64": PREC_DF64, "fp32flux": PREC_FP32FLUX}
 EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error", "fv_state_size",
            "fv_field_size", "fv_cell_count", "fv_set_state", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-           "fv_adjoint_vjp")
+           "fv_adjoint_vjp", "fv_autotune", "fv_get_launch")
 
 
 class FvError(RuntimeError):
@@ -85,9 +85,11 @@ def load_library(path: Optional[str] = None):
     L.fv_rk_step.argtypes = [vp, dbl, i32, vp]
     L.fv_residual_norms.argtypes = [vp, i32, vp, vp]
     L.fv_adjoint_vjp.argtypes = [vp, i32, dbl, vp, vp, vp, vp, vp]
+    L.fv_autotune.argtypes = [vp, dbl, i32, vp]
+    L.fv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-              "fv_adjoint_vjp"):
+              "fv_adjoint_vjp", "fv_autotune", "fv_get_launch"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -237,6 +239,15 @@ class Solver:
             raise FvError(rc, self._L.fv_last_error(self._h).decode())
         self._check(rc)
         return out[:5].copy(), out[5:].copy()
+
+    def autotune(self, dt: float, reps: int = 3, stream=None):
+        self._check(self._L.fv_autotune(self._h, float(dt), int(reps), _stream(stream)))
+        return self.launch()
+
+    def launch(self):
+        out = (ctypes.c_int * 4)()
+        self._check(self._L.fv_get_launch(self._h, out))
+        return {"tile": out[0], "kchunk": out[1], "tiles": out[2], "ctas": out[3]}
 
     def adjoint_vjp(self, stage: int, dt: float, qin, lam_out, lam_in, lam_q0, stream=None):
         self._check(self._L.fv_adjoint_vjp(self._h, int(stage), float(dt), _ptr(qin), _ptr(lam_out),

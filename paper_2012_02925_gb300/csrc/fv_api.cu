@@ -420,6 +420,7 @@ int build_tiles(fv_ctx* h) {
   for (int x : order) sorted.push_back(tiles[x]);
   h->ntiles = (int)sorted.size();
   h->launch.grid = (int)std::min<long long>(h->ntiles, slots);
+  if (h->d_tiles) { cudaFree(h->d_tiles); h->d_tiles = nullptr; }
   CK(h, cudaMalloc(&h->d_tiles, sizeof(FvTile) * sorted.size()));
   CK(h, cudaMemcpy(h->d_tiles, sorted.data(), sizeof(FvTile) * sorted.size(), cudaMemcpyHostToDevice));
   return FV_OK;
@@ -787,6 +788,59 @@ int fv_residual_norms(fv_handle hh, int buffer, double* out_host, void* stream) 
   std::memcpy(out_host, tmp, sizeof(double) * 10);
   for (int v = 0; v < 5; ++v)
     if (tmp[10 + v] != 0.0) return fail(h, FV_ERR_NONFINITE, "residual has non-finite entries");
+  return FV_OK;
+}
+
+int fv_autotune(fv_handle hh, double dt, int reps, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (reps <= 0) reps = 3;
+  CK(h, cudaStreamSynchronize(s));
+  cudaEvent_t e0, e1;
+  CK(h, cudaEventCreate(&e0));
+  CK(h, cudaEventCreate(&e1));
+  const int kcs[] = {0, 4, 8, 16, 32, 64};
+  float best = 1e30f;
+  int best_tile = 1, best_kc = 0;
+  const fv_config saved = h->cfg;
+  for (int tile = 1; tile <= 4; ++tile) {
+    for (int kc : kcs) {
+      if (h->cfg.dim == 2 && kc != 0) continue;
+      h->cfg.tile = tile;
+      h->cfg.kchunk = kc;
+      choose_launch(h);
+      if (build_tiles(h) != FV_OK) continue;
+      int rc = do_stage(h, 1, dt, s);
+      if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); h->cfg = saved; return rc; }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) do_stage(h, 1, dt, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_tile = tile; best_kc = kc; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cfg.tile = best_tile;
+  h->cfg.kchunk = best_kc;
+  choose_launch(h);
+  int rc = build_tiles(h);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  CK(h, cudaGetLastError());
+  return rc;
+}
+
+int fv_get_launch(fv_handle hh, int* out4) {
+  if (!hh || !out4) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  out4[0] = h->cfg.tile <= 0 ? 0 : h->cfg.tile;
+  out4[1] = h->cfg.kchunk;
+  out4[2] = h->ntiles;
+  out4[3] = h->launch.grid;
   return FV_OK;
 }
 

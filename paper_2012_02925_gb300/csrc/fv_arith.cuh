@@ -86,13 +86,13 @@ FV_HD df64 two_prod(float a, float b) {
   return mk(p, e);
 }
 
+// Sum with one error-free transformation of the high parts ("sloppy" add):
+// the absolute error is below ~2^-47 of the larger operand, which is the
+// accuracy binary64 itself offers relative to its operands.
 FV_HD df64 operator+(df64 a, df64 b) {
   df64 s = two_sum(a.hi, b.hi);
-  df64 t = two_sum(a.lo, b.lo);
-  float lo = FADD(s.lo, t.hi);
-  s = quick_two_sum(s.hi, lo);
-  lo = FADD(s.lo, t.lo);
-  return quick_two_sum(s.hi, lo);
+  float e = FADD(s.lo, FADD(a.lo, b.lo));
+  return quick_two_sum(s.hi, e);
 }
 FV_HD df64 operator-(df64 a) { return mk(-a.hi, -a.lo); }
 FV_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
@@ -111,16 +111,14 @@ FV_HD df64 operator*(float b, df64 a) { return a * b; }
 
 __device__ __forceinline__ float fv_rcp(float x) { return __frcp_rn(x); }
 
-// a / b: a binary32 reciprocal estimate and two correction steps in double-float
+// a / b: correctly rounded binary32 reciprocal of b.hi, quotient estimate and
+// one correction step in double-float (relative error ~2^-47)
 FV_HD df64 operator/(df64 a, df64 b) {
   float r = fv_rcp(b.hi);
   float q1 = FMUL(a.hi, r);
   df64 rem = a - b * q1;
   float q2 = FMUL(rem.hi, r);
-  df64 q = quick_two_sum(q1, q2);
-  rem = a - b * q;
-  float q3 = FMUL(rem.hi, r);
-  return q + mk(q3, 0.0f);
+  return quick_two_sum(q1, q2);
 }
 FV_HD df64 df_rcp(df64 b) { return mk(1.0f, 0.0f) / b; }
 
@@ -128,7 +126,7 @@ FV_HD df64 df_sqrt(df64 a) {
   if (!(a.hi > 0.0f)) return mk(a.hi == 0.0f ? 0.0f : __int_as_float(0x7fc00000), 0.0f);
   float s = __fsqrt_rn(a.hi);
   df64 e = a - two_prod(s, s);
-  float corr = FMUL(e.hi, FMUL(0.5f, fv_rcp(s)));
+  float corr = FMUL(e.hi, FMUL(0.5f, __fdividef(1.0f, s)));
   return quick_two_sum(s, corr);
 }
 FV_HD df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
@@ -185,9 +183,11 @@ template <> struct Sc<float> {
   static __device__ __forceinline__ float from_d(double x) { return fv_d2f_rn(x); }
   static __device__ __forceinline__ double to_d(float x) { return fv_f2d(x); }
   static __device__ __forceinline__ float c(double x) { return (float)x; }
-  static __device__ __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  // approximate (MUFU) reciprocal and square root: the binary32 flux form
+  // already carries ~1e-6 relative error, a few more ulps do not matter
+  static __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(x); }
   static __device__ __forceinline__ float abs(float x) { return ::fabsf(x); }
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float hi(float x) { return x; }
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ bool pos(float a) { return a > 0.0f; }

@@ -117,6 +117,21 @@ def test_residual_every_tile_shape(tile):
     assert rel_err_fields(r, ref, o) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_autotuned_launch_keeps_parity(prec):
+    pb = cases.multiblock_batched(nblocks=8, lo=6, hi=40, seed=6)
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 4)
+    s = solver(pb, prec)
+    cfg = s.autotune(pb.dt, reps=1)
+    s.set_state(torch.from_numpy(pb.q).cuda())
+    s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert cfg["tiles"] > 0
+    assert rel_err_states(got, ref, o) <= TOL_RUN[prec]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_free_stream_preserved(prec):
     pb = cases.uniform_3d(20, curvilinear=True)
