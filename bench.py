@@ -293,6 +293,10 @@ def run_gpu(args):
     }
     if args.variants and rank == 0 and world == 1:
         result["variants"] = run_variants(args, pk, peak_kind, traffic)
+        try:
+            result["adjoint"] = run_adjoint()
+        except Exception as e:  # report, do not hide
+            result["adjoint"] = {"error": str(e)}
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args.workload)
     s.close()
@@ -321,6 +325,53 @@ def run_e2e(s, pb, steps):
     el = time.perf_counter() - t0
     return {"value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
             "h2d_bytes_per_step": int(pb.q.nbytes), "d2h_bytes_per_step": 80}
+
+
+def run_adjoint(n=96, nstages=50):
+    """Discrete adjoint workload: 96^3 curvilinear block, van Albada, Harten
+    fix on every eigenvalue, J = integrated pressure on the k=0 face after 50
+    RK stages; forward with stage checkpoints, then the VJP chain."""
+    import torch
+    import paper_2012_02925_gb300 as fv
+    from paper_2012_02925_gb300.autograd import run_stages
+    pb = cases.mms_3d(n, curvilinear=True, with_source=False, limiter=2, fix_all=1)
+    s = fv.Solver.from_problem(pb, precision="fp64")
+    q0 = torch.from_numpy(pb.q).cuda()
+    s.set_state(q0)
+    b = pb.blocks[0]
+    g = (b.nk + 4, b.nj + 4, b.ni + 4)
+
+    def J(q):
+        Q = q.view(5, *g)[:, 2, 2:-2, 2:-2].reshape(5, -1)
+        return ((0.4 * (Q[4] - 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]))).sum()
+    x = q0.clone().requires_grad_(True)
+    out = run_stages(s, x, pb.dt, nstages)   # warm-up (allocates adjoint scratch)
+    J(out).backward()
+    torch.cuda.synchronize()
+    x = q0.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    out = run_stages(s, x, pb.dt, nstages)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J(out).backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    lam = torch.randn(s.field_size, dtype=torch.float64, device="cuda")
+    li = torch.empty_like(lam)
+    l0 = torch.zeros_like(lam)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(5):
+        s.adjoint_vjp(2, pb.dt, q0, lam, li, l0)
+    e1.record(st)
+    torch.cuda.synchronize()
+    vjp_s = e0.elapsed_time(e1) / 1e3 / 5
+    s.close()
+    return {"workload": pb.name + "_adjoint", "stages": nstages, "cells": pb.ncells,
+            "forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1,
+            "vjp_stage_ms": vjp_s * 1e3, "vjp_value": pb.ncells / vjp_s / 1e9, "unit": "Gcell-updates/s",
+            "precision": "fp64"}
 
 
 def run_variants(args, pk, peak_kind, traffic):

@@ -151,6 +151,11 @@ int64_t fv_cell_count(fv_handle h);
  * (fixed / Dirichlet ghosts). */
 int fv_set_state(fv_handle h, const double* q, void* stream);
 
+/* Overwrite one state buffer (0 = Q^(0), 1, 2 = stage buffers) with a packed
+ * ghosted state (host or device); the other buffers are untouched.  Used to
+ * replay a stage from a checkpoint (the adjoint's forward recomputation). */
+int fv_set_buffer(fv_handle h, int buffer, const double* q, void* stream);
+
 /* Copy buffer `buffer` (0 = Q^(0), the current solution; 1, 2 = stage
  * buffers) out as a packed ghosted state (host or device destination).  With
  * a host destination the call synchronises `stream`. */
@@ -174,9 +179,11 @@ int fv_exchange_ghosts(fv_handle h, int buffer, void* stream);
 int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
 
 /* Runge-Kutta stage m (1..n_stages) with time step dt: exchange the ghosts of
- * Q^(m-1), evaluate R(Q^(m-1)) and write Q^(m) = Q^(0) - alpha_m dt / Omega R
- * (stage 1 reads Q^(0); the last stage writes Q^(0)).  Two kernel launches
- * (exchange, fused residual + update). */
+ * Q^(m-1), evaluate R(Q^(m-1)) and write Q^(m) = Q^(0) - alpha_m dt / Omega R.
+ * Buffers: stage 1 reads Q^(m-1) = Q^(0) from buffer 0; stage m < n_stages
+ * writes buffer 1 when m is odd and buffer 2 when m is even; the last stage
+ * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Two
+ * kernel launches (exchange, fused residual + update). */
 int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
 
 /* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage

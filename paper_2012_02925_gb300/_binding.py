@@ -20,7 +20,7 @@ PREC_FP64, PREC_DF64, PREC_FP32FLUX = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "df64": PREC_DF64, "fp32flux": PREC_FP32FLUX}
 
 EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error", "fv_state_size",
-           "fv_field_size", "fv_cell_count", "fv_set_state", "fv_get_state", "fv_set_source",
+           "fv_field_size", "fv_cell_count", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
            "fv_adjoint_vjp", "fv_autotune", "fv_get_launch")
 
@@ -77,6 +77,7 @@ def load_library(path: Optional[str] = None):
         getattr(L, f).argtypes = [vp]
         getattr(L, f).restype = i64
     L.fv_set_state.argtypes = [vp, vp, vp]
+    L.fv_set_buffer.argtypes = [vp, i32, vp, vp]
     L.fv_get_state.argtypes = [vp, i32, vp, vp]
     L.fv_set_source.argtypes = [vp, vp, vp]
     L.fv_exchange_ghosts.argtypes = [vp, i32, vp]
@@ -87,7 +88,7 @@ def load_library(path: Optional[str] = None):
     L.fv_adjoint_vjp.argtypes = [vp, i32, dbl, vp, vp, vp, vp, vp]
     L.fv_autotune.argtypes = [vp, dbl, i32, vp]
     L.fv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
-    for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_get_state", "fv_set_source",
+    for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
               "fv_adjoint_vjp", "fv_autotune", "fv_get_launch"):
         getattr(L, f).restype = i32
@@ -166,6 +167,7 @@ class Solver:
         cfg.kchunk = int(kchunk)
         self.n_stages = cfg.n_stages
         self.precision = precision
+        self.block_dims = [(int(b.ni), int(b.nj), int(b.nk)) for b in blocks]
         rc = L.fv_create_blocks(descs, len(blocks), cs, len(conns), ctypes.byref(cfg), ctypes.byref(self._h))
         if rc != FV_OK:
             raise FvError(rc, L.fv_last_error(None).decode())
@@ -205,6 +207,16 @@ class Solver:
     # -- C ABI calls ---------------------------------------------------------------
     def set_state(self, q, stream=None):
         self._check(self._L.fv_set_state(self._h, _ptr(q), _stream(stream)))
+
+    def set_buffer(self, buffer: int, q, stream=None):
+        self._check(self._L.fv_set_buffer(self._h, int(buffer), _ptr(q), _stream(stream)))
+
+    def stage_buffers(self, m: int):
+        """(input buffer, output buffer) of RK stage m, as fv_rk_stage defines them."""
+        M = self.n_stages
+        src = 0 if m == 1 else (0 if m - 1 == M else (1 if (m - 1) % 2 == 1 else 2))
+        dst = 0 if m == M else (1 if m % 2 == 1 else 2)
+        return src, dst
 
     def get_state(self, buffer: int = 0, out=None, stream=None):
         import torch

@@ -42,8 +42,10 @@ struct fv_ctx {
   double* scratch_r = nullptr;      // residual (variable-major) for norms
   double* partials = nullptr;       // per-CTA norm partials
   double* d_norm = nullptr;         // 11 doubles
-  double* adj_scratch = nullptr;    // adjoint work space (lazily allocated)
-  long long adj_scratch_elems = 0;
+  double* adj_contrib = nullptr;    // adjoint: per-face input cotangents (20 per face)
+  double* adj_lamg = nullptr;       // adjoint: ghosted cotangent of Q^(m-1)
+  double* adj_qx = nullptr;         // adjoint: X(Q^(m-1)), the exchanged stage input
+  std::vector<FvConnDev> hconns;
   int device = 0, nsm = 0;
   std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
   std::string err;
@@ -621,6 +623,7 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
       items += 2LL * y.L0 * y.L1;
     }
     h->conn_items = items;
+    h->hconns = cd;
     CK(hp, cudaMalloc(&h->d_conns, sizeof(FvConnDev) * nconn));
     CK(hp, cudaMemcpy(h->d_conns, cd.data(), sizeof(FvConnDev) * nconn, cudaMemcpyHostToDevice));
   }
@@ -642,7 +645,8 @@ int fv_destroy(fv_handle hh) {
   for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
   cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns);
   cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol);
-  cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm); cudaFree(h->adj_scratch);
+  cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
+  cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   delete h;
   return FV_OK;
 }
@@ -661,6 +665,14 @@ int fv_set_state(fv_handle hh, const double* q, void* stream) {
   for (int x = 1; x < 3; ++x)
     CK(h, cudaMemcpyAsync(h->buf[x], h->buf[0], sizeof(double) * h->state_elems, cudaMemcpyDeviceToDevice, s));
   return FV_OK;
+}
+
+int fv_set_buffer(fv_handle hh, int buffer, const double* q, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!q) return fail(h, FV_ERR_INVALID_ARG, "q is NULL");
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  return copy_state(h, q, h->buf[buffer], true, (cudaStream_t)stream);
 }
 
 int fv_get_state(fv_handle hh, int buffer, double* q, void* stream) {
@@ -850,7 +862,55 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
   fv_ctx* h = H(hh);
   if (stage < 1 || stage > h->cfg.n_stages) return fail(h, FV_ERR_INVALID_ARG, "stage out of range");
   if (!qin_dev || !lam_out_dev || !lam_in_dev || !lam_q0_dev) return fail(h, FV_ERR_INVALID_ARG, "NULL pointer");
-  return fail(h, FV_ERR_UNSUPPORTED, "adjoint not built yet");
+  if (h->cfg.precision != FV_PREC_FP64)
+    return fail(h, FV_ERR_UNSUPPORTED, "the adjoint runs in binary64: create the handle with FV_PREC_FP64");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nd = h->cfg.dim;
+  // per-direction offsets of each block's faces in the contribution scratch
+  std::vector<long long> coff(3 * h->hb.size());
+  long long tot[3] = {0, 0, 0};
+  for (size_t b = 0; b < h->hb.size(); ++b) {
+    const FvBlockDev& B = h->hb[b];
+    for (int d = 0; d < 3; ++d) {
+      coff[3 * b + d] = tot[d];
+      if (d < nd) tot[d] += (long long)(B.ni + (d == 0)) * (B.nj + (d == 1)) * (B.nk + (d == 2));
+    }
+  }
+  const long long nfaces_all = tot[0] + tot[1] + tot[2];
+  if (!h->adj_contrib) CK(h, cudaMalloc(&h->adj_contrib, sizeof(double) * 20 * nfaces_all));
+  if (!h->adj_lamg) CK(h, cudaMalloc(&h->adj_lamg, sizeof(double) * h->state_elems));
+  double* cdir[3] = {h->adj_contrib, h->adj_contrib + 20 * tot[0], h->adj_contrib + 20 * (tot[0] + tot[1])};
+  // linearise around the state the forward stage saw: X(Q^(m-1)), ghosts exchanged
+  const double* qx = qin_dev;
+  if (h->conn_items) {
+    if (!h->adj_qx) CK(h, cudaMalloc(&h->adj_qx, sizeof(double) * h->state_elems));
+    int rc = copy_state(h, qin_dev, h->adj_qx, true, s);
+    if (rc) return rc;
+    rc = do_exchange(h, h->adj_qx, s);
+    if (rc) return rc;
+    qx = h->adj_qx;
+  }
+  const double alpha_dt = h->cfg.alpha[stage - 1] * dt;
+  const FvStageArgs a = base_args(h);
+  for (size_t b = 0; b < h->hb.size(); ++b) {
+    const FvBlockDev& B = h->hb[b];
+    for (int d = 0; d < nd; ++d)
+      if (fv_adjoint_faces(B, d, qx, lam_out_dev, h->invvol, alpha_dt, (const double*)h->metric[d], h->nfaces[d],
+                           a.fp, cdir[d] + 20 * coff[3 * b + d], s))
+        return cuda_fail(h, cudaGetLastError(), "adjoint face kernel");
+  }
+  for (size_t b = 0; b < h->hb.size(); ++b) {
+    const FvBlockDev& B = h->hb[b];
+    if (fv_adjoint_gather(B, cdir[0] + 20 * coff[3 * b], cdir[1] + 20 * coff[3 * b + 1],
+                          nd == 3 ? cdir[2] + 20 * coff[3 * b + 2] : nullptr, nd == 3, h->adj_lamg, s))
+      return cuda_fail(h, cudaGetLastError(), "adjoint gather kernel");
+  }
+  for (const FvConnDev& c : h->hconns)
+    if (fv_adjoint_transpose(h->d_blocks, c, h->adj_lamg, s)) return cuda_fail(h, cudaGetLastError(), "adjoint transpose");
+  for (const FvBlockDev& B : h->hb)
+    if (fv_adjoint_finish(B, h->adj_lamg, lam_out_dev, lam_in_dev, lam_q0_dev, s))
+      return cuda_fail(h, cudaGetLastError(), "adjoint finish kernel");
+  return FV_OK;
 }
 
 }  // extern "C"

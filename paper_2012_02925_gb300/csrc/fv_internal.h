@@ -75,3 +75,13 @@ int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s
 int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
+
+// Discrete-adjoint kernels (fv_adjoint.cu), binary64 only.
+int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const double* lam_out, const double* invvol,
+                     double alpha_dt, const double* metric, long long mstride, const FvFaceParams& fp,
+                     double* contrib, cudaStream_t s);
+int fv_adjoint_gather(const FvBlockDev& B, const double* cx, const double* cy, const double* cz, int three_d,
+                      double* lamg, cudaStream_t s);
+int fv_adjoint_transpose(const FvBlockDev* d_blocks, const FvConnDev& c, double* lamg, cudaStream_t s);
+int fv_adjoint_finish(const FvBlockDev& B, const double* lamg, const double* lam_out, double* lam_in, double* lam_q0,
+                      cudaStream_t s);
