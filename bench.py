@@ -32,9 +32,34 @@ import cases  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# measured on this GPU pool by a throughput probe (FFMA / DFMA issue rates)
-FP32_OPS_PER_CLK_SM = 128
-FP64_OPS_PER_CLK_SM = 1.6   # measured: DFMA/DADD/DMUL ~505 Gop/s at 152 SMs, ~2.07 GHz
+# Unit counts and clocks of the GB300 (152 SMs, 128 FP32 lanes per SM,
+# 2070 MHz maximum SM clock) and its nominal FP64 rate (1.25 TFLOP/s).
+N_SM, FP32_LANES, SM_HZ = 152, 128, 2.07e9
+FP64_NOMINAL_FLOPS = 1.25e12
+# Algorithmic FP64 operations of one face with the default method (van Leer,
+# kappa = -1, Harten fix), as the oracle's op-counting scalar counts them
+# (add/sub, mul, div, sqrt, abs); tests/test_bench_constants.py checks them.
+FACE_OPS = {"add": 153, "mul": 162, "div": 50, "sqrt": 3, "abs": 23}
+# per interior cell beyond its faces: primitive recovery 12, fixed-order sums
+# with the source 35, RK update 11
+CELL_OPS = 58
+# binary32 instructions of one double-float operation (fv_arith.cuh): sloppy
+# add 11, double-float product 7, quotient 27, square root 25, |x| 2
+DF64_COST = {"add": 11, "mul": 7, "div": 27, "sqrt": 25, "abs": 2}
+
+
+def alu_ops_per_cell(dim: int = 3) -> int:
+    return dim * sum(FACE_OPS.values()) + CELL_OPS
+
+
+def alu_peak(precision: str) -> float:
+    """FP64-operation roofline of the arithmetic forms: the nominal FP64 rate
+    for binary64; for double-float, the FP32 lane rate divided by the mean
+    binary32 cost of one emulated operation over the face's operation mix."""
+    if precision == "fp64":
+        return FP64_NOMINAL_FLOPS
+    mix = sum(FACE_OPS[k] * DF64_COST[k] for k in FACE_OPS) / sum(FACE_OPS.values())
+    return N_SM * FP32_LANES * SM_HZ / mix
 
 
 def workload(name: str):
@@ -215,14 +240,20 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
     hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     r = {"kernel": "fv_stage_kernel<%s>" % precision, "bytes_per_launch": sum(byts) / M,
          "avg_launch_s": sum(kt) / M}
+    r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": peak_kind}
     if precision == "fp32flux":
         r.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                   "peak_source": peak_kind})
     else:
-        # FP64 and double-float forms are bound by arithmetic issue:
-        # report the HBM fraction too so that the two bounds can be compared.
-        r.update({"bound": "alu", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                  "peak_source": peak_kind, "note": "HBM fraction of an ALU-bound kernel"})
+        # FP64-accurate forms are bound by arithmetic: algorithmic FP64
+        # operations per launch / launch time against the derived peak
+        ops = alu_ops_per_cell(pb.dim) * pb.ncells
+        achieved = ops / (sum(kt) / M) / 1e9
+        peak = alu_peak(precision) / 1e9
+        r.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s (FP64 ops)",
+                  "frac": achieved / peak, "ops_per_launch": ops,
+                  "peak_source": "derived: " + ("nominal FP64 1.25 TFLOP/s" if precision == "fp64" else
+                                                "152 SMs x 128 lanes x 2.07 GHz / binary32 cost per op")})
     t = traffic.get(precision)
     r["traffic"] = t
     return r

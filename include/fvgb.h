@@ -106,8 +106,12 @@ typedef struct {
  *   n_stages, alpha: Q^(m) = Q^(0) - alpha[m-1] dt / Omega R(Q^(m-1)),
  *     m = 1..n_stages (2..8).
  *   tile: 0 = automatic; else an index into the compiled tile shapes
- *     (1: 32x8 cells / 256 threads, 2: 32x4 / 128, 3: 16x8 / 128, 4: 30x8 / 256).
- *   kchunk: k-planes per tile, 0 = automatic. */
+ *     (1: 32x8 cells / 256 threads, 2: 32x4 / 128, 3: 16x8 / 128, 4: 30x8 / 256,
+ *     5: 32x8 / 288, 6: 32x8 / 256 and 7: 32x4 / 128 with the next k-plane
+ *     prefetched by cp.async - 6 and 7 for FV_PREC_FP32FLUX only).
+ *   kchunk: k-planes per tile; 0 = automatic (about three tiles per resident
+ *     CTA slot); -w = about w tiles per resident CTA slot.  Tiles are handed
+ *     to persistent CTAs largest first through a device counter. */
 typedef struct {
   double gamma, eps, kappa, harten, va_delta2;
   int limiter, fix_all, dim, n_stages;

@@ -27,6 +27,7 @@ struct fv_ctx {
   FvBlockDev* d_blocks = nullptr;
   FvTile* d_tiles = nullptr;
   int ntiles = 0;
+  int* d_tile_counter = nullptr;    // dynamic tile scheduling of the stage kernel
   FvLaunch launch{};
   FvConnDev* d_conns = nullptr;
   long long conn_items = 0;
@@ -289,6 +290,7 @@ FvStageArgs base_args(fv_ctx* h) {
   a.blocks = h->d_blocks;
   a.tiles = h->d_tiles;
   a.ntiles = h->ntiles;
+  a.tile_counter = h->d_tile_counter;
   for (int d = 0; d < 3; ++d) { a.metric[d] = h->metric[d]; a.mstride[d] = h->nfaces[d]; }
   a.invvol = h->invvol;
   a.srcvol = h->srcvol;
@@ -359,9 +361,8 @@ int copy_state(fv_ctx* h, const double* src, double* dst, bool to_internal, cuda
 
 void choose_launch(fv_ctx* h) {
   const fv_config& c = h->cfg;
-  const bool d3 = c.dim == 3;
   FvLaunch l{};
-  l.three_d = d3;
+  l.three_d = c.dim == 3;
   int shape = c.tile;
   if (shape <= 0) {
     // automatic: narrow blocks prefer narrow tiles
@@ -369,11 +370,11 @@ void choose_launch(fv_ctx* h) {
     for (auto& b : h->hb) maxni = std::max(maxni, b.ni);
     shape = maxni >= 24 ? 1 : 3;
   }
-  static const int shapes[5][3] = {{32, 8, 256}, {32, 8, 256}, {32, 4, 128}, {16, 8, 128}, {30, 8, 256}};
-  shape = std::min(std::max(shape, 1), 4);
-  l.tx = shapes[shape][0];
-  l.ty = shapes[shape][1];
-  l.threads = shapes[shape][2];
+  shape = std::min(std::max(shape, 1), FV_NUM_SHAPES);
+  l.shape = shape;
+  l.tx = FV_SHAPE_TABLE[shape - 1][0];
+  l.ty = FV_SHAPE_TABLE[shape - 1][1];
+  l.threads = FV_SHAPE_TABLE[shape - 1][2];
   h->launch = l;
 }
 
@@ -399,10 +400,14 @@ int build_tiles(fv_ctx* h) {
     const FvBlockDev& b = h->hb[bi];
     int kc = h->cfg.kchunk;
     if (h->cfg.dim == 2) kc = 1;
-    else if (kc <= 0) {
+    else if (kc == 0) {
       // split k so that the whole problem fills the resident CTA slots a few times
       const long long want = std::max<long long>(1, (3 * slots + columns - 1) / std::max<long long>(columns, 1));
       kc = (int)std::max<long long>(4, (b.nk + want - 1) / want);
+    } else if (kc < 0) {
+      // -w: about w tiles per resident CTA slot
+      const long long want = std::max<long long>(1, (-kc * slots) / std::max<long long>(columns, 1));
+      kc = (int)std::max<long long>(2, (b.nk + want - 1) / want);
     }
     kc = std::min(kc, b.nk);
     for (int k0 = 0; k0 < b.nk; k0 += kc)
@@ -571,6 +576,8 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
   // ---- allocations ----
   for (int x = 0; x < 3; ++x) CK(hp, cudaMalloc(&h->buf[x], sizeof(double) * h->state_elems));
   CK(hp, cudaMalloc(&h->d_blocks, sizeof(FvBlockDev) * nblocks));
+  CK(hp, cudaMalloc(&h->d_tile_counter, 2 * sizeof(int)));
+  CK(hp, cudaMemset(h->d_tile_counter, 0, 2 * sizeof(int)));
   CK(hp, cudaMalloc(&h->invvol, sizeof(double) * h->ncell));
   CK(hp, cudaMalloc(&h->vol, sizeof(double) * h->ncell));
   const int mb = storage_bytes(cfg->precision);
@@ -643,7 +650,7 @@ int fv_destroy(fv_handle hh) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
   for (int x = 0; x < 3; ++x) cudaFree(h->buf[x]);
   for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
-  cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns);
+  cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns); cudaFree(h->d_tile_counter);
   cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol);
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
@@ -812,11 +819,11 @@ int fv_autotune(fv_handle hh, double dt, int reps, void* stream) {
   cudaEvent_t e0, e1;
   CK(h, cudaEventCreate(&e0));
   CK(h, cudaEventCreate(&e1));
-  const int kcs[] = {0, 4, 8, 16, 32, 64};
+  const int kcs[] = {0, -1, -2, 4, 8, 16, 32};
   float best = 1e30f;
   int best_tile = 1, best_kc = 0;
   const fv_config saved = h->cfg;
-  for (int tile = 1; tile <= 4; ++tile) {
+  for (int tile = 1; tile <= FV_NUM_SHAPES; ++tile) {
     for (int kc : kcs) {
       if (h->cfg.dim == 2 && kc != 0) continue;
       h->cfg.tile = tile;

@@ -46,6 +46,7 @@ struct FvStageArgs {
   const FvBlockDev* blocks;
   const FvTile* tiles;
   int ntiles;
+  int* tile_counter;            // {next dynamic tile, CTAs finished}; zero between launches
   int mode;
   const double* qin;            // Q^(m-1)
   const double* q0;             // Q^(0)
@@ -63,6 +64,7 @@ struct FvStageArgs {
 
 // Kernel launchers, one translation unit per arithmetic form.
 struct FvLaunch {
+  int shape;                    // compiled tile shape id (1-based)
   int tx, ty, threads;          // tile shape
   int grid;                     // CTAs (persistent)
   int three_d;
@@ -75,6 +77,11 @@ int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s
 int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
+
+// tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
+constexpr int FV_NUM_SHAPES = 7;
+constexpr int FV_SHAPE_TABLE[FV_NUM_SHAPES][4] = {
+    {32, 8, 256, 0}, {32, 4, 128, 0}, {16, 8, 128, 0}, {30, 8, 256, 0}, {32, 8, 288, 0}, {32, 8, 256, 1}, {32, 4, 128, 1}};
 
 // Discrete-adjoint kernels (fv_adjoint.cu), binary64 only.
 int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const double* lam_out, const double* invvol,

@@ -16,6 +16,7 @@
 // memory only).  Tiles come from a table, so one launch covers every block of
 // a multi-block problem.
 #pragma once
+#include <cuda_pipeline.h>
 #include <type_traits>
 #include "fv_face.cuh"
 
@@ -61,12 +62,17 @@ template <class T, int TX, int TY>
 struct StageSmem {
   static constexpr int W = TX + 4, H = TY + 4, PL = W * H;
   static constexpr int NXI = (TX + 1) * TY, NETA = TX * (TY + 1), NZETA = TX * TY;
-  static constexpr size_t bytes(bool three_d) {
+  static constexpr __host__ __device__ size_t typed(bool three_d) {
     return sizeof(T) * (size_t)((three_d ? 4 : 1) * 5 * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0));
+  }
+  // with prefetch: + a binary64 staging plane that cp.async fills while the
+  // faces of the previous plane are computed
+  static constexpr __host__ __device__ size_t bytes(bool three_d, bool prefetch) {
+    return ((typed(three_d) + 15) / 16) * 16 + (prefetch && three_d ? sizeof(double) * 5 * PL : 0);
   }
 };
 
-template <class T, int TX, int TY, int NT, bool DIM3>
+template <class T, int TX, int TY, int NT, bool DIM3, bool PF>
 __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
   using S = Sc<T>;
   using AT = typename Acc<T>::type;
@@ -82,6 +88,7 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
   T* Fx = Vs + NSLOT * 5 * PL;                    // [5][TY][TX+1]
   T* Fy = Fx + 5 * NXI;                           // [5][TY+1][TX]
   T* Fz = Fy + 5 * NETA;                          // [2][5][TY][TX]
+  double* stg = reinterpret_cast<double*>(smem_raw + ((SM::typed(DIM3) + 15) / 16) * 16);  // [5][H][W] (PF)
 
   const int tid = threadIdx.x;
   const FaceC<T> C = make_face_consts<T>(args.fp);
@@ -93,7 +100,11 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
   const MT* mzeta = reinterpret_cast<const MT*>(args.metric[2]);
   const long long msx = args.mstride[0], msy = args.mstride[1], msz = args.mstride[2];
 
-  for (int tile = blockIdx.x; tile < args.ntiles; tile += gridDim.x) {
+  // Tiles 0..gridDim-1 go to the CTAs in order; later ones are handed out
+  // dynamically (largest first, as the table is sorted) through a counter
+  // that the last CTA to finish resets for the next launch.
+  __shared__ int s_next;
+  for (int tile = blockIdx.x; tile < args.ntiles;) {
     const FvTile td = args.tiles[tile];
     const FvBlockDev& B = args.blocks[td.block];
     const int ni = B.ni, nj = B.nj, nk = B.nk;
@@ -113,6 +124,37 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
           T q[5], V[5];
 #pragma unroll
           for (int n = 0; n < 5; ++n) q[n] = S::from_d(__ldg(src + n * pl));
+          prim_from_cons(C, q, V);
+#pragma unroll
+          for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
+        }
+      }
+    };
+
+    // asynchronous copy of plane kk's raw binary64 state into the staging
+    // plane; every thread later converts exactly the cells it copied
+    auto prefetch_plane = [&](int kk) {
+      for (int it = tid; it < PL; it += NT) {
+        const int r = it / W, c = it - r * W;
+        const int j = j0 - 2 + r, i = i0 - 2 + c;
+        if (i < ni + 2 && j < nj + 2) {
+          const double* src = qin + (long long)(kk + 2) * ks + (long long)(j + 2) * js + (i + 2);
+#pragma unroll
+          for (int n = 0; n < 5; ++n) __pipeline_memcpy_async(stg + n * PL + it, src + n * pl, sizeof(double));
+        }
+      }
+      __pipeline_commit();
+    };
+    auto convert_staged = [&](int slot) {
+      __pipeline_wait_prior(0);
+      T* dst = Vs + slot * 5 * PL;
+      for (int it = tid; it < PL; it += NT) {
+        const int r = it / W, c = it - r * W;
+        const int j = j0 - 2 + r, i = i0 - 2 + c;
+        if (i < ni + 2 && j < nj + 2) {
+          T q[5], V[5];
+#pragma unroll
+          for (int n = 0; n < 5; ++n) q[n] = S::from_d(stg[n * PL + it]);
           prim_from_cons(C, q, V);
 #pragma unroll
           for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
@@ -157,6 +199,7 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
     if (DIM3) {
       for (int s = -2; s <= 1; ++s) load_plane(k0 + s, (k0 + s) & 3);
       __syncthreads();
+      if (PF) prefetch_plane(k0 + 2);
       for (int it = tid; it < NZETA; it += NT) zeta_face(k0, it, Fz + (k0 & 1) * 5 * NZETA + it);
       __syncthreads();
     } else {
@@ -167,8 +210,14 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
     for (int k = k0; k < k1; ++k) {
       const int slot = DIM3 ? (k & 3) : 0;
       if (DIM3) {
-        load_plane(k + 2, (k + 2) & 3);
-        __syncthreads();
+        if (PF) {
+          convert_staged((k + 2) & 3);
+          __syncthreads();
+          if (k + 1 < k1) prefetch_plane(k + 3);   // overlaps the faces below
+        } else {
+          load_plane(k + 2, (k + 2) & 3);
+          __syncthreads();
+        }
       }
       const T* P = Vs + slot * 5 * PL;
       // ---- every face of this plane (and the zeta faces above it), once ----
@@ -244,32 +293,43 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
       }
     }
     __syncthreads();   // smem is reused by the next tile
+    if (tid == 0) s_next = (int)gridDim.x + atomicAdd(args.tile_counter, 1);
+    __syncthreads();
+    tile = s_next;
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(args.tile_counter + 1, 1) == (int)gridDim.x - 1) {
+      args.tile_counter[0] = 0;
+      args.tile_counter[1] = 0;
+      __threadfence();
+    }
   }
 }
 
 // The dynamic shared-memory limit is raised once by occupancy_t (at handle
 // creation), so a launch is a plain enqueue that stream capture accepts.
-template <class T, int TX, int TY, int NT>
+template <class T, int TX, int TY, int NT, bool PF>
 static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0);
+  const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0, PF);
   if (l.three_d) {
-    fv_stage_kernel<T, TX, TY, NT, true><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, true, PF><<<l.grid, NT, smem, s>>>(a);
   } else {
-    fv_stage_kernel<T, TX, TY, NT, false><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, false, false><<<l.grid, NT, smem, s>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <class T, int TX, int TY, int NT>
+template <class T, int TX, int TY, int NT, bool PF>
 static int occupancy_t(bool three_d, size_t* smem_out) {
-  const size_t smem = StageSmem<T, TX, TY>::bytes(three_d);
+  const size_t smem = StageSmem<T, TX, TY>::bytes(three_d, PF);
   int n = 0;
   if (three_d) {
-    auto k = fv_stage_kernel<T, TX, TY, NT, true>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, true, PF>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   } else {
-    auto k = fv_stage_kernel<T, TX, TY, NT, false>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, false, false>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   }
@@ -277,22 +337,36 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
   return n;
 }
 
-// Tile shapes compiled for every form: (TX, TY, threads)
+// Compiled tile shapes (TX, TY, threads, prefetch); the shape ids of
+// fv_config.tile are 1-based indices into this list.  The prefetching shapes
+// are built for the binary32-flux form only (their staging plane would cost
+// the wider forms a resident CTA).
+#define FV_SHAPES(X)      \
+  X(1, 32, 8, 256, false) \
+  X(2, 32, 4, 128, false) \
+  X(3, 16, 8, 128, false) \
+  X(4, 30, 8, 256, false) \
+  X(5, 32, 8, 288, false) \
+  X(6, 32, 8, 256, true)  \
+  X(7, 32, 4, 128, true)
+
 template <class T>
 int fv_dispatch_launch(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  if (l.tx == 32 && l.ty == 8 && l.threads == 256) return launch_stage_t<T, 32, 8, 256>(a, l, s);
-  if (l.tx == 32 && l.ty == 4 && l.threads == 128) return launch_stage_t<T, 32, 4, 128>(a, l, s);
-  if (l.tx == 16 && l.ty == 8 && l.threads == 128) return launch_stage_t<T, 16, 8, 128>(a, l, s);
-  if (l.tx == 30 && l.ty == 8 && l.threads == 256) return launch_stage_t<T, 30, 8, 256>(a, l, s);
+  constexpr bool allow_pf = std::is_same<T, float>::value;
+#define FV_LAUNCH_CASE(ID, TX, TY, NT, PF) \
+  if (l.shape == ID) { if (PF && !allow_pf) return -2; return launch_stage_t<T, TX, TY, NT, PF && allow_pf>(a, l, s); }
+  FV_SHAPES(FV_LAUNCH_CASE)
+#undef FV_LAUNCH_CASE
   return -2;
 }
 
 template <class T>
 int fv_dispatch_occupancy(const FvLaunch& l, size_t* smem) {
+  constexpr bool allow_pf = std::is_same<T, float>::value;
   const bool d3 = l.three_d != 0;
-  if (l.tx == 32 && l.ty == 8 && l.threads == 256) return occupancy_t<T, 32, 8, 256>(d3, smem);
-  if (l.tx == 32 && l.ty == 4 && l.threads == 128) return occupancy_t<T, 32, 4, 128>(d3, smem);
-  if (l.tx == 16 && l.ty == 8 && l.threads == 128) return occupancy_t<T, 16, 8, 128>(d3, smem);
-  if (l.tx == 30 && l.ty == 8 && l.threads == 256) return occupancy_t<T, 30, 8, 256>(d3, smem);
+#define FV_OCC_CASE(ID, TX, TY, NT, PF) \
+  if (l.shape == ID) { if (PF && !allow_pf) return 0; return occupancy_t<T, TX, TY, NT, PF && allow_pf>(d3, smem); }
+  FV_SHAPES(FV_OCC_CASE)
+#undef FV_OCC_CASE
   return 0;
 }

@@ -1,0 +1,18 @@
+"""The benchmark's algorithmic operation count per face is the oracle's own
+count (op-counting scalar), so the ALU roofline uses the method's arithmetic,
+not the kernel's."""
+import bench
+import oracle
+from cases.core import default_params
+
+
+def test_face_op_count_matches_oracle():
+    c = oracle.face_opcount(default_params())
+    for k, v in bench.FACE_OPS.items():
+        assert c[k] == v, (k, c[k], v)
+
+
+def test_alu_peaks_are_derived_from_unit_counts():
+    assert bench.alu_peak("fp64") == 1.25e12
+    p = bench.alu_peak("df64")
+    assert 3.0e12 < p < 4.5e12

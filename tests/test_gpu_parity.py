@@ -111,10 +111,20 @@ def test_residual_method_options(prec, opts):
     assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4])
-def test_residual_every_tile_shape(tile):
-    r, ref, o = residual_pair(cases.mms_3d((37, 21, 11), curvilinear=True), "fp64", exchange=False, tile=tile)
-    assert rel_err_fields(r, ref, o) <= 1e-12
+SHAPES = [(p, t) for p in PRECS for t in range(1, 8) if t <= 5 or p == "fp32flux"]
+
+
+@pytest.mark.parametrize("prec,tile", SHAPES)
+def test_every_tile_shape_residual_and_step(prec, tile):
+    pb = cases.mms_3d((37, 21, 11), curvilinear=True)
+    r, ref, o = residual_pair(pb, prec, exchange=False, tile=tile, kchunk=3)
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+    s = solver(pb, prec, tile=tile, kchunk=4)
+    s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    ref_q = o.run(pb.q.copy(), pb.dt, 4)
+    assert rel_err_states(got, ref_q, o) <= (1e-6 if prec == "fp32flux" else 1e-12)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
