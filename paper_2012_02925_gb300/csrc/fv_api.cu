@@ -40,6 +40,7 @@ struct fv_ctx {
   double* invvol = nullptr;
   double* vol = nullptr;
   double* srcvol = nullptr;
+  float2* srcvol2 = nullptr;        // S*Omega as double-float pairs (non-binary64 forms)
   double* scratch_r = nullptr;      // residual (variable-major) for norms
   double* partials = nullptr;       // per-CTA norm partials
   double* d_norm = nullptr;         // 11 doubles
@@ -170,6 +171,15 @@ __global__ void source_scale_kernel(const double* s, const double* vol, double* 
   }
 }
 
+// binary64 -> (hi, lo) binary32 pairs
+__global__ void split_kernel(const double* in, float2* out, long long n) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const double v = in[x];
+    const float h = (float)v;
+    out[x] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // ghost exchange: work item = (connection, tangential a, b, depth d)
 // ---------------------------------------------------------------------------
@@ -294,6 +304,7 @@ FvStageArgs base_args(fv_ctx* h) {
   for (int d = 0; d < 3; ++d) { a.metric[d] = h->metric[d]; a.mstride[d] = h->nfaces[d]; }
   a.invvol = h->invvol;
   a.srcvol = h->srcvol;
+  a.srcvol2 = h->srcvol2;
   a.ncell_total = h->ncell;
   a.fp.gamma = h->cfg.gamma;
   a.fp.eps = h->cfg.eps;
@@ -651,7 +662,7 @@ int fv_destroy(fv_handle hh) {
   for (int x = 0; x < 3; ++x) cudaFree(h->buf[x]);
   for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
   cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns); cudaFree(h->d_tile_counter);
-  cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol);
+  cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol); cudaFree(h->srcvol2);
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   delete h;
@@ -703,7 +714,11 @@ int fv_set_source(fv_handle hh, const double* src, void* stream) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
   h->graphs.clear();
   if (!src) {
-    if (h->srcvol) { CK(h, cudaStreamSynchronize(s)); cudaFree(h->srcvol); h->srcvol = nullptr; }
+    if (h->srcvol || h->srcvol2) {
+      CK(h, cudaStreamSynchronize(s));
+      cudaFree(h->srcvol); h->srcvol = nullptr;
+      cudaFree(h->srcvol2); h->srcvol2 = nullptr;
+    }
     return FV_OK;
   }
   if (!h->srcvol) CK(h, cudaMalloc(&h->srcvol, sizeof(double) * 5 * h->ncell));
@@ -712,6 +727,10 @@ int fv_set_source(fv_handle hh, const double* src, void* stream) {
     const long long nc = (long long)B.ni * B.nj * B.nk;
     source_scale_kernel<<<grid_for(5 * nc, 256, h->nsm), 256, 0, s>>>(h->srcvol, h->vol, h->srcvol, 5 * B.cell_off, nc,
                                                                     B.cell_off);
+  }
+  if (h->cfg.precision != FV_PREC_FP64) {
+    if (!h->srcvol2) CK(h, cudaMalloc(&h->srcvol2, sizeof(float2) * 5 * h->ncell));
+    split_kernel<<<grid_for(5 * h->ncell, 256, h->nsm), 256, 0, s>>>(h->srcvol, h->srcvol2, 5 * h->ncell);
   }
   CK(h, cudaGetLastError());
   return FV_OK;

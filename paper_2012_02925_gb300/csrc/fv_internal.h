@@ -55,6 +55,7 @@ struct FvStageArgs {
   long long mstride[3];         // per direction: faces in all blocks (plane length)
   const double* invvol;         // 1/Omega per interior cell
   const double* srcvol;         // S*Omega, [block][5][cells], or null
+  const float2* srcvol2;        // the same as double-float (hi, lo) pairs, or null
   double* rout;                 // residual output or null
   int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
   long long ncell_total;

@@ -254,18 +254,46 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
           const long long q_idx = (long long)(k + 2) * ks + (long long)(j + 2) * js + (i + 2);
           const long long ncell_b = (long long)ni * nj * nk;
           AT R[5];
+          const long long src_off = 5 * B.cell_off + cell;
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
-            AT rx = Acc<T>::diff(Fx[n * NXI + y * (TX + 1) + x + 1], Fx[n * NXI + y * (TX + 1) + x]);
-            AT ry = Acc<T>::diff(Fy[n * NETA + (y + 1) * TX + x], Fy[n * NETA + y * TX + x]);
-            AT r = rx + ry;
-            if (DIM3) {
-              AT rz = Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
-                                   Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
-              r = r + rz;
+            const T x1 = Fx[n * NXI + y * (TX + 1) + x + 1], x0 = Fx[n * NXI + y * (TX + 1) + x];
+            const T y1 = Fy[n * NETA + (y + 1) * TX + x], y0 = Fy[n * NETA + y * TX + x];
+            if constexpr (std::is_same<T, float>::value) {
+              // exact pair differences, then the high parts summed with
+              // error-free transformations and the low parts in binary32
+              const df64 rx = two_sum(x1, -x0), ry = two_sum(y1, -y0);
+              df64 h = two_sum(rx.hi, ry.hi);
+              float lo = FADD(FADD(rx.lo, ry.lo), h.lo);
+              if (DIM3) {
+                const df64 rz = two_sum(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
+                                        -Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
+                const df64 h2 = two_sum(h.hi, rz.hi);
+                lo = FADD(FADD(lo, rz.lo), h2.lo);
+                h.hi = h2.hi;
+              }
+              if (args.srcvol2) {
+                const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);
+                const df64 t = two_sum(h.hi, -sv.x);
+                lo = FADD(FSUB(lo, sv.y), t.lo);
+                h.hi = t.hi;
+              }
+              R[n] = quick_two_sum(h.hi, lo);
+            } else {
+              AT r = Acc<T>::diff(x1, x0) + Acc<T>::diff(y1, y0);
+              if (DIM3)
+                r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
+                                     Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
+              if constexpr (std::is_same<AT, df64>::value) {
+                if (args.srcvol2) {
+                  const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);
+                  r = r - mk(sv.x, sv.y);
+                }
+              } else {
+                if (args.srcvol) r = r - __ldg(args.srcvol + src_off + n * ncell_b);
+              }
+              R[n] = r;
             }
-            if (args.srcvol) r = r - Acc<T>::from_d(__ldg(args.srcvol + 5 * (B.cell_off) + n * ncell_b + cell));
-            R[n] = r;
           }
           if (args.mode == FV_MODE_RK) {
             const double iv = cart ? B.cart_invvol : __ldg(args.invvol + B.cell_off + cell);
