@@ -259,6 +259,15 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
     return r
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The slowest rank's time: replicas run independently, the job ends
+    when the last one does."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     import paper_2012_02925_gb300 as fv  # noqa: F401
@@ -285,9 +294,7 @@ def run_gpu(args):
             dist.barrier()
         elapsed = time_steps(s, pb, args.steps, 0)
     if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, "cuda")
     cell_updates = pb.ncells * M * args.steps * world
     value = cell_updates / elapsed / 1e9
     pk, peak_kind = peaks()

@@ -177,6 +177,7 @@ template <> struct Sc<double> {
   static __device__ __forceinline__ float hi(double x) { return (float)x; }
   static __device__ __forceinline__ bool lt(double a, double b) { return a < b; }
   static __device__ __forceinline__ bool pos(double a) { return a > 0.0; }
+  static __device__ __forceinline__ bool above(double a, float t) { return a > (double)t; }
 };
 
 template <> struct Sc<float> {
@@ -193,6 +194,7 @@ template <> struct Sc<float> {
   static __device__ __forceinline__ float hi(float x) { return x; }
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ bool pos(float a) { return a > 0.0f; }
+  static __device__ __forceinline__ bool above(float a, float t) { return a > t; }
 };
 
 template <> struct Sc<df64> {
@@ -209,4 +211,5 @@ template <> struct Sc<df64> {
   static __device__ __forceinline__ float hi(df64 x) { return x.hi; }
   static __device__ __forceinline__ bool lt(df64 a, df64 b) { return a < b; }
   static __device__ __forceinline__ bool pos(df64 a) { return a.hi > 0.0f; }
+  static __device__ __forceinline__ bool above(df64 a, float t) { return a.hi > t; }
 };

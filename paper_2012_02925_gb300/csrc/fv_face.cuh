@@ -60,9 +60,13 @@ __device__ __forceinline__ T limited(const FaceC<T>& C, T a, T b) {
   if (C.limiter == 0) return b;
   if (C.limiter == 1) {
     // van Leer, Psi(r) = (r + |r|)/(1 + |r|):  Psi(a/b) b = (a|b| + |a| b)/(|a| + |b|)
+    // Both differences below 1e-30 (rounding noise of a quantity that is
+    // zero, e.g. a transverse velocity): zero slope, as the oracle's guarded
+    // ratio gives to within 2e-30; it also keeps the binary32 reciprocal of a
+    // subnormal sum from overflowing.
     T aa = S::abs(a), ab = S::abs(b);
     T den = aa + ab;
-    if (!S::pos(den)) return S::c(0.0);
+    if (!S::above(den, 1e-30f)) return S::c(0.0);
     return (a * ab + aa * b) * S::rcp(den);
   }
   // van Albada in smooth product form: b (a^2 + a b)/(a^2 + b^2 + delta^2)

@@ -1,0 +1,147 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark uses (autotuned tile shape and k-chunk).
+
+* 128^3 curvilinear manufactured-solution block: every cell of one residual
+  (all three forms) and of one full RK step (FP64-accurate forms).
+* 64 seeded uneven blocks (10.9 M cells) with random connections: every cell
+  of one residual after the exchange and of one RK step.
+* 512 x 512 x 256 periodic block (67 M cells): the residual on seeded
+  windows that the oracle evaluates one by one from the same initial state
+  (interior windows need no exchange; one window on the periodic seam takes
+  its halo from the periodic wrap), plus conservation of the totals of
+  Omega*Q over a full RK step - a property that holds at any size.
+"""
+import numpy as np
+import pytest
+
+import cases
+import oracle
+from test_gpu_parity import TOL_RES, TOL_RUN, rel_err_fields, rel_err_states, solver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mms128():
+    return cases.mms_3d(128, curvilinear=True)
+
+
+@pytest.fixture(scope="module")
+def multiblock():
+    return cases.multiblock_batched()
+
+
+@pytest.fixture(scope="module")
+def large():
+    return cases.large_periodic(512, 512, 256)
+
+
+def tuned(pb, prec, reps=2):
+    s = solver(pb, prec)
+    s.autotune(pb.dt, reps=reps)
+    s.set_state(torch.from_numpy(pb.q).cuda())
+    return s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32flux"])
+def test_mms128_every_cell_residual(mms128, prec):
+    pb = mms128
+    o = oracle.Oracle(pb)
+    ref = o.residual(pb.q.copy())
+    s = tuned(pb, prec)
+    r = s.residual(0).cpu().numpy()
+    s.close()
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_mms128_every_cell_rk_step(mms128, prec):
+    pb = mms128
+    o = oracle.Oracle(pb)
+    ref = o.run(pb.q.copy(), pb.dt, 4)
+    s = tuned(pb, prec)
+    s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert rel_err_states(got, ref, o) <= TOL_RUN[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32flux"])
+def test_multiblock_every_cell(multiblock, prec):
+    pb = multiblock
+    o = oracle.Oracle(pb)
+    ref = o.residual(o.exchange(pb.q.copy()))
+    s = tuned(pb, prec)
+    s.exchange_ghosts(0)
+    r = s.residual(0).cpu().numpy()
+    assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+    if prec != "fp32flux":
+        s.set_state(torch.from_numpy(pb.q).cuda())
+        s.rk_step(pb.dt, use_graph=True)
+        got = s.get_state(0).cpu().numpy()
+        assert rel_err_states(got, o.run(pb.q.copy(), pb.dt, 4), o) <= TOL_RUN[prec]
+    s.close()
+
+
+def _window_problem(pb, qg, lo, n):
+    """A Cartesian block made of the n^3 cells starting at interior index lo
+    of the large block, its ghosts taken from the ghosted array qg."""
+    b = pb.blocks[0]
+    i, j, k = lo
+    sl = qg[:, k:k + n + 4, j:j + n + 4, i:i + n + 4]
+    wb = cases.BlockDesc(n, n, n, None, (b.x0[0] + i * b.h[0], b.x0[1] + j * b.h[1], b.x0[2] + k * b.h[2]),
+                         tuple(b.h))
+    return cases.Problem([wb], [], 3, np.ascontiguousarray(sl).ravel(), None, pb.dt, dict(pb.params))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32flux"])
+def test_large_sampled_windows_and_conservation(large, prec):
+    pb = large
+    b = pb.blocks[0]
+    n = 10
+    rng = np.random.default_rng(12)
+    qg = pb.q.reshape(cases.ghosted_shape(b))
+    # interior windows keep their 2-cell halo inside the interior
+    lows = [(int(rng.integers(2, b.ni - n - 2)), int(rng.integers(2, b.nj - n - 2)), int(rng.integers(2, b.nk - n - 2)))
+            for _ in range(5)]
+    # one window across the periodic seam in every direction
+    seam = (b.ni - n // 2, b.nj - n // 2, b.nk - n // 2)
+    s = solver(pb, prec)
+    if prec == "fp32flux":
+        s.autotune(pb.dt, reps=1)
+        s.set_state(torch.from_numpy(pb.q).cuda())
+    s.exchange_ghosts(0)
+    r = s.residual(0).view(5, b.nk, b.nj, b.ni)
+    checks = [(lo, qg) for lo in lows]
+    # the seam window wraps around the periodic block: its ghosted cells are
+    # interior cells taken modulo the extents (the periodic connection's
+    # closed form, pinned by test_exchange_periodic_closed_form)
+    idx = [np.arange(seam[a] - 2, seam[a] + n + 2) % (b.ni, b.nj, b.nk)[a] + 2 for a in range(3)]
+    seam_q = qg[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+    for lo, src in checks + [((0, 0, 0), None)]:
+        if src is None:
+            wp = cases.Problem([cases.BlockDesc(n, n, n, None, (0, 0, 0), tuple(b.h))], [], 3,
+                               np.ascontiguousarray(seam_q).ravel(), None, pb.dt, dict(pb.params))
+            ii = [np.arange(seam[a], seam[a] + n) % (b.ni, b.nj, b.nk)[a] for a in range(3)]
+            got = r[:, ii[2]][:, :, ii[1]][:, :, :, ii[0]].cpu().numpy()
+        else:
+            wp = _window_problem(pb, src, lo, n)
+            i, j, k = lo
+            got = r[:, k:k + n, j:j + n, i:i + n].cpu().numpy()
+        wo = oracle.Oracle(wp)
+        ref = wo.residual(wp.q.copy())
+        assert rel_err_fields(got.ravel(), ref, wo) <= TOL_RES[prec]
+    # totals of Omega*Q over one RK step (periodic: conserved up to rounding)
+    vol = b.h[0] * b.h[1] * b.h[2]
+    s.set_state(torch.from_numpy(pb.q).cuda())
+
+    def totals():
+        q = s.get_state(0).view(5, b.nk + 4, b.nj + 4, b.ni + 4)[:, 2:-2, 2:-2, 2:-2]
+        return (q.sum(dim=(1, 2, 3)) * vol).cpu().numpy()
+    t0 = totals()
+    s.rk_step(pb.dt, use_graph=True)
+    t1 = totals()
+    s.close()
+    scale = np.abs(t0).max()
+    assert np.abs(t1 - t0).max() <= (1e-12 if prec != "fp32flux" else 1e-9) * scale
