@@ -176,7 +176,7 @@ def load_traffic():
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_solver(pb, precision, tile=0, kchunk=0, tune=True):
+def make_solver(pb, precision, tile=0, kchunk=0, tune=True, reps=3):
     import torch
     import paper_2012_02925_gb300 as fv
     s = fv.Solver.from_problem(pb, precision=precision, tile=tile, kchunk=kchunk)
@@ -184,7 +184,7 @@ def make_solver(pb, precision, tile=0, kchunk=0, tune=True):
     if pb.source is not None:
         s.set_source(torch.from_numpy(np.concatenate([x.ravel() for x in pb.source])).cuda())
     if tune and tile == 0:
-        s.autotune(pb.dt)
+        s.autotune(pb.dt, reps=reps)
     torch.cuda.synchronize()
     return s
 
@@ -415,14 +415,19 @@ def run_adjoint(n=96, nstages=50):
 def run_variants(args, pk, peak_kind, traffic):
     out = []
     specs = [(w, p) for w in args.variant_workloads.split(",") for p in args.variant_precisions.split(",")]
+    cache = {}
     for wname, prec in specs:
         if wname == args.workload and prec == args.precision:
             continue
         try:
-            pb = workload(wname)
+            if wname not in cache:
+                cache.clear()
+                cache[wname] = workload(wname)
+            pb = cache[wname]
             curv = pb.blocks[0].nodes is not None
-            s = make_solver(pb, prec)
-            steps = max(3, args.steps // 2)
+            big = pb.ncells > 3e7
+            s = make_solver(pb, prec, reps=1 if big else 3)
+            steps = 3 if big else max(3, args.steps // 2)
             el = time_steps(s, pb, steps, 3)
             st, ex = time_stage_kernels(s, pb, 3)
             out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
@@ -509,7 +514,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
-    ap.add_argument("--variant-workloads", default="mms128,multiblock")
+    ap.add_argument("--variant-workloads", default="mms128,multiblock,large")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

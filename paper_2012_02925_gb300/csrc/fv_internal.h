@@ -80,9 +80,10 @@ int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
-constexpr int FV_NUM_SHAPES = 7;
-constexpr int FV_SHAPE_TABLE[FV_NUM_SHAPES][4] = {
-    {32, 8, 256, 0}, {32, 4, 128, 0}, {16, 8, 128, 0}, {30, 8, 256, 0}, {32, 8, 288, 0}, {32, 8, 256, 1}, {32, 4, 128, 1}};
+constexpr int FV_NUM_SHAPES = 8;
+constexpr int FV_SHAPE_TABLE[FV_NUM_SHAPES][4] = {{32, 8, 256, 0}, {32, 4, 128, 0}, {16, 8, 128, 0},
+                                                  {30, 8, 256, 0}, {32, 8, 288, 0}, {32, 8, 256, 1},
+                                                  {32, 4, 128, 1}, {32, 7, 256, 0}};
 
 // Discrete-adjoint kernels (fv_adjoint.cu), binary64 only.
 int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const double* lam_out, const double* invvol,

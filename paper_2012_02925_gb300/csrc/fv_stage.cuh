@@ -72,8 +72,15 @@ struct StageSmem {
   }
 };
 
+// resident CTAs per SM the register allocation must allow (shared memory
+// permits this many for the compiled shapes)
+template <class T, int NT>
+constexpr int stage_min_ctas() {
+  return sizeof(T) == 4 ? (NT <= 128 ? 8 : 4) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
+}
+
 template <class T, int TX, int TY, int NT, bool DIM3, bool PF>
-__global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
+__global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel(const FvStageArgs args) {
   using S = Sc<T>;
   using AT = typename Acc<T>::type;
   using MT = typename MetricStore<T>::type;
@@ -113,52 +120,60 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
     const double* qin = args.qin + B.qoff;
     const bool cart = B.cartesian != 0;
 
+    // Per-thread work descriptors, fixed for the whole tile (only the plane
+    // index changes along k): the halo cells this thread stages ...
+    constexpr int LROUNDS = (PL + NT - 1) / NT;
+    int loff[LROUNDS];                // (j+2)*js + (i+2), or -1 outside the ghosted block
+#pragma unroll
+    for (int r = 0; r < LROUNDS; ++r) {
+      const int it = tid + r * NT;
+      const int rr = it / W, c = it - rr * W;
+      const int j = j0 - 2 + rr, i = i0 - 2 + c;
+      loff[r] = (it < PL && i < ni + 2 && j < nj + 2) ? (int)((j + 2) * js + (i + 2)) : -1;
+    }
     // stage plane kk (ghosted index kk + 2 in memory) into ring slot `slot`
     auto load_plane = [&](int kk, int slot) {
       T* dst = Vs + slot * 5 * PL;
-      for (int it = tid; it < PL; it += NT) {
-        const int r = it / W, c = it - r * W;
-        const int j = j0 - 2 + r, i = i0 - 2 + c;
-        if (i < ni + 2 && j < nj + 2) {
-          const double* src = qin + (long long)(kk + 2) * ks + (long long)(j + 2) * js + (i + 2);
-          T q[5], V[5];
+      const double* base = qin + (long long)(kk + 2) * ks;
 #pragma unroll
-          for (int n = 0; n < 5; ++n) q[n] = S::from_d(__ldg(src + n * pl));
-          prim_from_cons(C, q, V);
+      for (int r = 0; r < LROUNDS; ++r) {
+        if (loff[r] < 0) continue;
+        const double* src = base + loff[r];
+        T q[5], V[5];
 #pragma unroll
-          for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
-        }
+        for (int n = 0; n < 5; ++n) q[n] = S::from_d(__ldg(src + n * pl));
+        prim_from_cons(C, q, V);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) dst[n * PL + tid + r * NT] = V[n];
       }
     };
 
     // asynchronous copy of plane kk's raw binary64 state into the staging
     // plane; every thread later converts exactly the cells it copied
     auto prefetch_plane = [&](int kk) {
-      for (int it = tid; it < PL; it += NT) {
-        const int r = it / W, c = it - r * W;
-        const int j = j0 - 2 + r, i = i0 - 2 + c;
-        if (i < ni + 2 && j < nj + 2) {
-          const double* src = qin + (long long)(kk + 2) * ks + (long long)(j + 2) * js + (i + 2);
+      const double* base = qin + (long long)(kk + 2) * ks;
 #pragma unroll
-          for (int n = 0; n < 5; ++n) __pipeline_memcpy_async(stg + n * PL + it, src + n * pl, sizeof(double));
-        }
+      for (int r = 0; r < LROUNDS; ++r) {
+        if (loff[r] < 0) continue;
+#pragma unroll
+        for (int n = 0; n < 5; ++n)
+          __pipeline_memcpy_async(stg + n * PL + tid + r * NT, base + loff[r] + n * pl, sizeof(double));
       }
       __pipeline_commit();
     };
     auto convert_staged = [&](int slot) {
       __pipeline_wait_prior(0);
       T* dst = Vs + slot * 5 * PL;
-      for (int it = tid; it < PL; it += NT) {
-        const int r = it / W, c = it - r * W;
-        const int j = j0 - 2 + r, i = i0 - 2 + c;
-        if (i < ni + 2 && j < nj + 2) {
-          T q[5], V[5];
 #pragma unroll
-          for (int n = 0; n < 5; ++n) q[n] = S::from_d(stg[n * PL + it]);
-          prim_from_cons(C, q, V);
+      for (int r = 0; r < LROUNDS; ++r) {
+        if (loff[r] < 0) continue;
+        const int it = tid + r * NT;
+        T q[5], V[5];
 #pragma unroll
-          for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
-        }
+        for (int n = 0; n < 5; ++n) q[n] = S::from_d(stg[n * PL + it]);
+        prim_from_cons(C, q, V);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
       }
     };
 
@@ -185,22 +200,54 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
         for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
       }
     };
-    // zeta face between planes kf-1 and kf (stencil kf-2 .. kf+1) of tile column e = y*TX + x
-    auto zeta_face = [&](int kf, int e, T* dst) {
-      const int y = e / TX, x = e - y * TX;
-      if (i0 + x < ni && j0 + y < nj) {
-        const int c = (y + 2) * W + (x + 2);
-        const long long f = B.face_off[2] + ((long long)kf * nj + (j0 + y)) * ni + (i0 + x);
-        do_face(Vs + ((kf - 2) & 3) * 5 * PL + c, Vs + ((kf - 1) & 3) * 5 * PL + c, Vs + (kf & 3) * 5 * PL + c,
-                Vs + ((kf + 1) & 3) * 5 * PL + c, 2, f, dst, NZETA);
+    // ... and, for each face item it = tid + r*NT, the face it evaluates:
+    // direction, stencil offset inside a plane (xi, eta) or column offset
+    // (zeta), metric index without its k term and destination slot
+    // (dir < 0: unused or outside).  Decoded on the fly: holding these in
+    // registers for the whole tile costs more occupancy than the decode.
+    auto face_item = [&](int it, int& dir, int& off, int& dst, long long& met) {
+      dir = -1;
+      if (it < NXI) {
+        const int y = it / (TX + 1), x = it - y * (TX + 1);     // face between cells x-1 and x
+        const int i = i0 + x, j = j0 + y;
+        if (i <= ni && j < nj) {
+          dir = 0; off = (y + 2) * W + x; dst = it;
+          met = B.face_off[0] + (long long)j * (ni + 1) + i;
+        }
+      } else if (it < NXI + NETA) {
+        const int e = it - NXI;
+        const int y = e / TX, x = e - y * TX;                   // face between rows y-1 and y
+        const int i = i0 + x, j = j0 + y;
+        if (i < ni && j <= nj) {
+          dir = 1; off = y * W + (x + 2); dst = e;
+          met = B.face_off[1] + (long long)j * ni + i;
+        }
+      } else if (DIM3 && it < NFACE) {
+        const int e = it - NXI - NETA;
+        const int y = e / TX, x = e - y * TX;
+        if (i0 + x < ni && j0 + y < nj) {
+          dir = 2; off = (y + 2) * W + (x + 2); dst = e;
+          met = B.face_off[2] + (long long)(j0 + y) * ni + (i0 + x);
+        }
       }
+    };
+    const long long kfx = (long long)nj * (ni + 1), kfy = (long long)(nj + 1) * ni, kfz = (long long)nj * ni;
+    // zeta face between planes kf-1 and kf (stencil kf-2 .. kf+1) at column offset c
+    auto zeta_face = [&](int kf, int c, long long fm, T* dst) {
+      do_face(Vs + ((kf - 2) & 3) * 5 * PL + c, Vs + ((kf - 1) & 3) * 5 * PL + c, Vs + (kf & 3) * 5 * PL + c,
+              Vs + ((kf + 1) & 3) * 5 * PL + c, 2, fm + kf * kfz, dst, NZETA);
     };
 
     if (DIM3) {
       for (int s = -2; s <= 1; ++s) load_plane(k0 + s, (k0 + s) & 3);
       __syncthreads();
       if (PF) prefetch_plane(k0 + 2);
-      for (int it = tid; it < NZETA; it += NT) zeta_face(k0, it, Fz + (k0 & 1) * 5 * NZETA + it);
+      for (int it = tid; it < NFACE; it += NT) {
+        int d, off, dst;
+        long long met;
+        face_item(it, d, off, dst, met);
+        if (d == 2) zeta_face(k0, off, met, Fz + (k0 & 1) * 5 * NZETA + dst);
+      }
       __syncthreads();
     } else {
       load_plane(0, 0);
@@ -222,26 +269,17 @@ __global__ void __launch_bounds__(NT) fv_stage_kernel(const FvStageArgs args) {
       const T* P = Vs + slot * 5 * PL;
       // ---- every face of this plane (and the zeta faces above it), once ----
       for (int it = tid; it < NFACE; it += NT) {
-        if (it < NXI) {
-          const int y = it / (TX + 1), x = it - y * (TX + 1);     // face between cells x-1 and x
-          const int i = i0 + x, j = j0 + y;
-          if (i <= ni && j < nj) {
-            const T* c0 = P + (y + 2) * W + x;                   // cell x-2
-            do_face(c0, c0 + 1, c0 + 2, c0 + 3, 0, B.face_off[0] + ((long long)k * nj + j) * (ni + 1) + i,
-                    Fx + it, NXI);
-          }
-        } else if (it < NXI + NETA) {
-          const int e = it - NXI;
-          const int y = e / TX, x = e - y * TX;                   // face between rows y-1 and y
-          const int i = i0 + x, j = j0 + y;
-          if (i < ni && j <= nj) {
-            const T* c0 = P + y * W + (x + 2);                   // row y-2
-            do_face(c0, c0 + W, c0 + 2 * W, c0 + 3 * W, 1,
-                    B.face_off[1] + ((long long)k * (nj + 1) + j) * ni + i, Fy + e, NETA);
-          }
-        } else if (DIM3) {
-          const int e = it - NXI - NETA;
-          zeta_face(k + 1, e, Fz + ((k + 1) & 1) * 5 * NZETA + e);
+        int d, off, dst;
+        long long met;
+        face_item(it, d, off, dst, met);
+        if (d == 0) {
+          const T* c0 = P + off;
+          do_face(c0, c0 + 1, c0 + 2, c0 + 3, 0, met + k * kfx, Fx + dst, NXI);
+        } else if (d == 1) {
+          const T* c0 = P + off;
+          do_face(c0, c0 + W, c0 + 2 * W, c0 + 3 * W, 1, met + k * kfy, Fy + dst, NETA);
+        } else if (DIM3 && d == 2) {
+          zeta_face(k + 1, off, met, Fz + ((k + 1) & 1) * 5 * NZETA + dst);
         }
       }
       __syncthreads();
@@ -376,7 +414,8 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
   X(4, 30, 8, 256, false) \
   X(5, 32, 8, 288, false) \
   X(6, 32, 8, 256, true)  \
-  X(7, 32, 4, 128, true)
+  X(7, 32, 4, 128, true)  \
+  X(8, 32, 7, 256, false)
 
 template <class T>
 int fv_dispatch_launch(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
