@@ -178,6 +178,8 @@ template <> struct Sc<double> {
   static __device__ __forceinline__ bool lt(double a, double b) { return a < b; }
   static __device__ __forceinline__ bool pos(double a) { return a > 0.0; }
   static __device__ __forceinline__ bool above(double a, float t) { return a > (double)t; }
+  using mask = bool;
+  static __device__ __forceinline__ double sel(bool m, double a, double b) { return m ? a : b; }
 };
 
 template <> struct Sc<float> {
@@ -195,6 +197,8 @@ template <> struct Sc<float> {
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ bool pos(float a) { return a > 0.0f; }
   static __device__ __forceinline__ bool above(float a, float t) { return a > t; }
+  using mask = bool;
+  static __device__ __forceinline__ float sel(bool m, float a, float b) { return m ? a : b; }
 };
 
 template <> struct Sc<df64> {
@@ -212,4 +216,6 @@ template <> struct Sc<df64> {
   static __device__ __forceinline__ bool lt(df64 a, df64 b) { return a < b; }
   static __device__ __forceinline__ bool pos(df64 a) { return a.hi > 0.0f; }
   static __device__ __forceinline__ bool above(df64 a, float t) { return a.hi > t; }
+  using mask = bool;
+  static __device__ __forceinline__ df64 sel(bool m, df64 a, df64 b) { return m ? a : b; }
 };

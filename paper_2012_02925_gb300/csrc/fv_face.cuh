@@ -26,14 +26,14 @@ template <class T>
 __device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
   using S = Sc<T>;
   FaceC<T> c;
-  c.gm1 = S::from_d(p.gamma - 1.0);
-  c.g_gm1 = S::from_d(p.gamma / (p.gamma - 1.0));
-  c.half = S::from_d(0.5);
-  c.one = S::from_d(1.0);
-  c.e4km = S::from_d(p.eps * 0.25 * (1.0 - p.kappa));
-  c.e4kp = S::from_d(p.eps * 0.25 * (1.0 + p.kappa));
-  c.harten = S::from_d(p.harten);
-  c.va_d2 = S::from_d(p.va_delta2);
+  c.gm1 = S::c(p.gamma - 1.0);
+  c.g_gm1 = S::c(p.gamma / (p.gamma - 1.0));
+  c.half = S::c(0.5);
+  c.one = S::c(1.0);
+  c.e4km = S::c(p.eps * 0.25 * (1.0 - p.kappa));
+  c.e4kp = S::c(p.eps * 0.25 * (1.0 + p.kappa));
+  c.harten = S::c(p.harten);
+  c.va_d2 = S::c(p.va_delta2);
   c.limiter = p.limiter;
   c.fix_all = p.fix_all;
   c.has_fix = p.harten > 0.0;
@@ -64,14 +64,15 @@ __device__ __forceinline__ T limited(const FaceC<T>& C, T a, T b) {
     // zero, e.g. a transverse velocity): zero slope, as the oracle's guarded
     // ratio gives to within 2e-30; it also keeps the binary32 reciprocal of a
     // subnormal sum from overflowing.
-    T aa = S::abs(a), ab = S::abs(b);
-    T den = aa + ab;
-    if (!S::above(den, 1e-30f)) return S::c(0.0);
-    return (a * ab + aa * b) * S::rcp(den);
+    const T aa = S::abs(a), ab = S::abs(b);
+    const T den = aa + ab;
+    const T phi = (a * ab + aa * b) * S::rcp(den);
+    return S::sel(S::above(den, 1e-30f), phi, S::c(0.0));
   }
   // van Albada in smooth product form: b (a^2 + a b)/(a^2 + b^2 + delta^2)
-  T a2 = a * a;
-  return b * (a2 + a * b) * S::rcp(a2 + b * b + C.va_d2);
+  const T a2 = a * a;
+  const T num = b * (a2 + a * b);
+  return num * S::rcp(a2 + b * b + C.va_d2);
 }
 
 // Eq. (flux) for one component from V_{i-1}, V_i, V_{i+1}, V_{i+2}
@@ -87,9 +88,9 @@ __device__ __forceinline__ void muscl(const FaceC<T>& C, T vm1, T v0, T vp1, T v
   }
 }
 
+// Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d
 template <class T>
 __device__ __forceinline__ T entropy_fixed(const FaceC<T>& C, T lam, T delta) {
-  // Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d
   if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * (C.half * Sc<T>::rcp(delta));
   return lam;
 }
@@ -165,6 +166,17 @@ __device__ __forceinline__ void face_flux(const FaceC<T>& C, const T* c0, const 
   T VL[5], VR[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) muscl(C, c0[n * cs], c1[n * cs], c2[n * cs], c3[n * cs], VL[n], VR[n]);
+  roe_flux(C, VL, VR, nx, ny, nz, A, out);
+}
+
+// Full face from stencil values held in registers: v[c][n] is component n of
+// stencil cell c (c = 0..3 along the face normal).
+template <class T>
+__device__ __forceinline__ void face_flux_vals(const FaceC<T>& C, const T (&v)[4][5], T nx, T ny, T nz, T A,
+                                               T out[5]) {
+  T VL[5], VR[5];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) muscl(C, v[0][n], v[1][n], v[2][n], v[3][n], VL[n], VR[n]);
   roe_flux(C, VL, VR, nx, ny, nz, A, out);
 }
 

@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
       do_face(Vs + ((kf - 2) & 3) * 5 * PL + c, Vs + ((kf - 1) & 3) * 5 * PL + c, Vs + (kf & 3) * 5 * PL + c,
               Vs + ((kf + 1) & 3) * 5 * PL + c, 2, fm + kf * kfz, dst, NZETA);
     };
-
     if (DIM3) {
       for (int s = -2; s <= 1; ++s) load_plane(k0 + s, (k0 + s) & 3);
       __syncthreads();
@@ -284,8 +283,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
       }
       __syncthreads();
       // ---- per cell: flux differences in a fixed order, then the RK update ----
-      if (tid < TX * TY) {
-        const int y = tid / TX, x = tid - y * TX;
+      for (int cc = tid; cc < TX * TY; cc += NT) {
+        const int y = cc / TX, x = cc - y * TX;
         const int i = i0 + x, j = j0 + y;
         if (i < ni && j < nj) {
           const long long cell = ((long long)k * nj + j) * ni + i;
@@ -304,8 +303,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
               df64 h = two_sum(rx.hi, ry.hi);
               float lo = FADD(FADD(rx.lo, ry.lo), h.lo);
               if (DIM3) {
-                const df64 rz = two_sum(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
-                                        -Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
+                const df64 rz = two_sum(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
+                                        -Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
                 const df64 h2 = two_sum(h.hi, rz.hi);
                 lo = FADD(FADD(lo, rz.lo), h2.lo);
                 h.hi = h2.hi;
@@ -320,8 +319,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
             } else {
               AT r = Acc<T>::diff(x1, x0) + Acc<T>::diff(y1, y0);
               if (DIM3)
-                r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + tid],
-                                     Fz[(k & 1) * 5 * NZETA + n * NZETA + tid]);
+                r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
+                                     Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
               if constexpr (std::is_same<AT, df64>::value) {
                 if (args.srcvol2) {
                   const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);
