@@ -77,7 +77,7 @@ class Problem:
 
 def default_params(**over) -> dict:
     p = dict(gamma=GAMMA, eps=1.0, kappa=-1.0, limiter=1, harten=0.1,
-             fix_all=0, va_delta2=1e-12, n_stages=4)
+             fix_all=0, va_delta2=1e-12, n_stages=4, flux=0)
     p.update(over)
     p["alpha"] = RK_ALPHA[p["n_stages"]]
     return p

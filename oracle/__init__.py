@@ -60,6 +60,7 @@ def lib():
         L.oracle_residual_jvp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 9
         L.oracle_rk_update.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] + [_dp] * 4
         L.oracle_roe_flux.argtypes = [_dp] * 5
+        L.oracle_face_flux.argtypes = [_dp] * 5
         L.oracle_muscl.argtypes = [_dp] * 3
         L.oracle_limited.argtypes = [_dp, ctypes.c_double, ctypes.c_double]
         L.oracle_limited.restype = ctypes.c_double
@@ -90,7 +91,8 @@ def set_threads(n: int) -> None:
 
 def params_array(params: dict, dim: int) -> np.ndarray:
     return np.array([params["gamma"], params["eps"], params["kappa"], params["limiter"],
-                     params["harten"], params["fix_all"], params["va_delta2"], dim], dtype=np.float64)
+                     params["harten"], params["fix_all"], params["va_delta2"], dim,
+                     params.get("flux", 0)], dtype=np.float64)
 
 
 # ---------------------------------------------------------------------------
@@ -104,6 +106,17 @@ def roe_flux(params: dict, VL, VR, S, dim: int = 3) -> np.ndarray:
     lib().oracle_roe_flux(_p(pa), _p(np.ascontiguousarray(VL, dtype=np.float64)),
                           _p(np.ascontiguousarray(VR, dtype=np.float64)),
                           _p(np.ascontiguousarray(S, dtype=np.float64)), _p(out))
+    return out
+
+
+def face_flux(params: dict, VL, VR, S, dim: int = 3) -> np.ndarray:
+    """Face flux of the configured function (params["flux"]: 0 Roe, 1 van Leer
+    flux-vector splitting, 2 Steger-Warming) times |S|."""
+    out = np.zeros(5)
+    pa = params_array(params, dim)
+    lib().oracle_face_flux(_p(pa), _p(np.ascontiguousarray(VL, dtype=np.float64)),
+                           _p(np.ascontiguousarray(VR, dtype=np.float64)),
+                           _p(np.ascontiguousarray(S, dtype=np.float64)), _p(out))
     return out
 
 

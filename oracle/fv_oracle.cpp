@@ -92,12 +92,14 @@ struct Params {
   int fix_all;        // also fix |V_n|
   double va_delta2;   // van Albada smoothing delta^2
   int dim;            // 2 or 3
+  int flux;           // 0 Roe, 1 van Leer flux-vector splitting, 2 Steger-Warming
 };
 
 Params unpack(const double* p) {
   Params q;
   q.gamma = p[0]; q.eps = p[1]; q.kappa = p[2]; q.limiter = (int)p[3];
   q.harten = p[4]; q.fix_all = (int)p[5]; q.va_delta2 = p[6]; q.dim = (int)p[7];
+  q.flux = (int)p[8];
   return q;
 }
 
@@ -244,6 +246,89 @@ void roe_flux(const Params& P, const T VL[5], const T VR[5], const double S[3], 
 }
 
 // ---------------------------------------------------------------------------
+// Flux-vector splittings, the other two face fluxes SENSEI offers (Section 2):
+// F^ = F+(V_L) + F-(V_R), times the face area.
+// ---------------------------------------------------------------------------
+
+// physical normal flux F.n of Section 2
+template <class T>
+void normal_flux(const Params& P, const T V[5], double nx, double ny, double nz, T F[5]) {
+  T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  T Vn = T(nx) * u + T(ny) * v + T(nz) * w;
+  T ht = T(P.gamma / (P.gamma - 1.0)) * p / r + T(0.5) * (u * u + v * v + w * w);
+  F[0] = r * Vn;
+  F[1] = r * u * Vn + T(nx) * p;
+  F[2] = r * v * Vn + T(ny) * p;
+  F[3] = r * w * Vn + T(nz) * p;
+  F[4] = r * ht * Vn;
+}
+
+// van Leer (1982): Mach-number splitting; sign = +1 for F+, -1 for F-
+template <class T>
+void vanleer_part(const Params& P, const T V[5], double nx, double ny, double nz, int sign, T F[5]) {
+  const double g = P.gamma;
+  T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  T c = sqrt_(T(g) * p / r);
+  T Vn = T(nx) * u + T(ny) * v + T(nz) * w;
+  T M = Vn / c;
+  if (val(M) >= 1.0 || val(M) <= -1.0) {
+    const bool whole = (val(M) >= 1.0) == (sign > 0);
+    if (whole) { normal_flux(P, V, nx, ny, nz, F); }
+    else { for (int n = 0; n < 5; ++n) F[n] = T(0.0); }
+    return;
+  }
+  T s = T((double)sign);
+  T mp = M + s;                                   // M +- 1
+  T fm = s * r * c * mp * mp / T(4.0);            // +- rho c (M +- 1)^2 / 4
+  T a = (T(0.0) - Vn + s * T(2.0) * c) / T(g);    // (-V_n +- 2c) / gamma
+  T e = T(g - 1.0) * Vn + s * T(2.0) * c;         // (gamma-1) V_n +- 2c
+  F[0] = fm;
+  F[1] = fm * (u + T(nx) * a);
+  F[2] = fm * (v + T(ny) * a);
+  F[3] = fm * (w + T(nz) * a);
+  F[4] = fm * (e * e / T(2.0 * (g * g - 1.0)) + T(0.5) * (u * u + v * v + w * w - Vn * Vn));
+}
+
+// Steger and Warming (1981): eigenvalue splitting l+- = (l +- |l|)/2 of
+// l1 = V_n - c, l2 = V_n, l5 = V_n + c
+template <class T>
+void steger_warming_part(const Params& P, const T V[5], double nx, double ny, double nz, int sign, T F[5]) {
+  const double g = P.gamma;
+  T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  T c = sqrt_(T(g) * p / r);
+  T Vn = T(nx) * u + T(ny) * v + T(nz) * w;
+  T s = T((double)sign);
+  T l1 = T(0.5) * ((Vn - c) + s * abs_(Vn - c));
+  T l2 = T(0.5) * (Vn + s * abs_(Vn));
+  T l5 = T(0.5) * ((Vn + c) + s * abs_(Vn + c));
+  T q2 = u * u + v * v + w * w;
+  T H = c * c / T(g - 1.0) + T(0.5) * q2;
+  T k = r / T(2.0 * g);
+  T a2 = T(2.0 * (g - 1.0)) * l2;
+  F[0] = k * (a2 + l1 + l5);
+  F[1] = k * (a2 * u + l1 * (u - T(nx) * c) + l5 * (u + T(nx) * c));
+  F[2] = k * (a2 * v + l1 * (v - T(ny) * c) + l5 * (v + T(ny) * c));
+  F[3] = k * (a2 * w + l1 * (w - T(nz) * c) + l5 * (w + T(nz) * c));
+  F[4] = k * (a2 * (T(0.5) * q2) + l1 * (H - c * Vn) + l5 * (H + c * Vn));
+}
+
+template <class T>
+void face_flux_fn(const Params& P, const T VL[5], const T VR[5], const double S[3], T out[5]) {
+  if (P.flux == 0) { roe_flux(P, VL, VR, S, out); return; }
+  double area = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  double nx = S[0] / area, ny = S[1] / area, nz = S[2] / area;
+  T Fp[5], Fm[5];
+  if (P.flux == 1) {
+    vanleer_part(P, VL, nx, ny, nz, +1, Fp);
+    vanleer_part(P, VR, nx, ny, nz, -1, Fm);
+  } else {
+    steger_warming_part(P, VL, nx, ny, nz, +1, Fp);
+    steger_warming_part(P, VR, nx, ny, nz, -1, Fm);
+  }
+  for (int n = 0; n < 5; ++n) out[n] = (Fp[n] + Fm[n]) * T(area);
+}
+
+// ---------------------------------------------------------------------------
 // block geometry helpers
 // ---------------------------------------------------------------------------
 struct Blk {
@@ -292,7 +377,7 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
       muscl(P, Vn[cm2], Vn[cm2 + stride], Vn[cm2 + 2 * stride], Vn[cm2 + 3 * stride], VL[n], VR[n]);
     }
     double S[3] = {Sarr[fidx], Sarr[nfaces + fidx], Sarr[2 * nfaces + fidx]};
-    roe_flux(P, VL, VR, S, out);
+    face_flux_fn(P, VL, VR, S, out);
     for (int n = 0; n < 5; ++n) F[n * nfaces + fidx] = out[n];
   };
 
@@ -513,6 +598,12 @@ void oracle_roe_flux(const double* params, const double* VL, const double* VR, c
                      double* out) {
   Params P = unpack(params);
   roe_flux<double>(P, VL, VR, S, out);
+}
+
+// Face flux of the configured function (Roe, van Leer or Steger-Warming).
+void oracle_face_flux(const double* params, const double* VL, const double* VR, const double* S, double* out) {
+  Params P = unpack(params);
+  face_flux_fn<double>(P, VL, VR, S, out);
 }
 
 void oracle_muscl(const double* params, const double* v4, double* LR) {

@@ -230,3 +230,78 @@ def test_primitive_recovery():
     u = q[1:4] / q[0]
     assert np.allclose(V[:4], [1.2, *u], rtol=1e-15)
     assert V[4] == pytest.approx(0.4 * (2.5 - 0.5 * 1.2 * (u @ u)), rel=1e-15)
+
+
+# ------------------------------------------------- flux-vector splittings ---
+
+FVS = [1, 2]   # van Leer, Steger-Warming (Section 2 lists both beside Roe)
+
+
+@pytest.mark.parametrize("flux", FVS)
+def test_fvs_consistency(flux):
+    """F+(V) + F-(V) = F(V): each splitting of Section 2's normal flux
+    sums back to it, subsonic and supersonic."""
+    rng = np.random.default_rng(20 + flux)
+    P = default_params(flux=flux)
+    for _ in range(60):
+        V = rand_state(rng)
+        V[1:4] *= rng.choice([0.3, 1.0, 4.0])          # subsonic and supersonic
+        S = rng.normal(size=3) * 0.05
+        got = oracle.face_flux(P, V, V, S)
+        ref = physical_flux(V, S)
+        assert np.allclose(got, ref, rtol=1e-13, atol=1e-14 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("flux", FVS)
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_fvs_supersonic_upwinding(flux, sign):
+    V0, _ = dimensional_state("inlet_2d")              # Mach 4, Section 8.1 table
+    rng = np.random.default_rng(30 + flux)
+    P = default_params(flux=flux)
+    S = np.array([0.02, 0.0, 0.0])
+    for _ in range(20):
+        VL = V0 * (1 + 0.05 * rng.uniform(-1, 1, size=5))
+        VR = V0 * (1 + 0.05 * rng.uniform(-1, 1, size=5))
+        VL[1:4] *= sign
+        VR[1:4] *= sign
+        got = oracle.face_flux(P, VL, VR, S)
+        ref = physical_flux(VL if sign > 0 else VR, S)
+        assert np.allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("flux", FVS)
+def test_fvs_mirror_symmetry(flux):
+    rng = np.random.default_rng(40 + flux)
+    P = default_params(flux=flux)
+    for _ in range(40):
+        VL, VR = rand_state(rng), rand_state(rng)
+        S = rng.normal(size=3)
+        a = oracle.face_flux(P, VL, VR, S)
+        b = oracle.face_flux(P, VR, VL, -S)
+        assert np.allclose(a, -b, rtol=1e-13, atol=1e-14 * np.abs(a).max())
+
+
+def test_van_leer_splitting_is_continuous_at_sonic_points():
+    """van Leer's split fluxes join the full flux continuously at M = +-1:
+    the face flux just below and just above a sonic state agrees to O(dM)."""
+    P = default_params(flux=1)
+    c = np.sqrt(1.4)
+    for M in (1.0, -1.0):
+        lo = np.array([1.0, (M - 1e-7) * c, 0, 0, 1.0])
+        hi = np.array([1.0, (M + 1e-7) * c, 0, 0, 1.0])
+        S = [1.0, 0.0, 0.0]
+        fl = oracle.face_flux(P, lo, lo, S)
+        fh = oracle.face_flux(P, hi, hi, S)
+        assert np.allclose(fl, fh, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("flux", FVS)
+def test_fvs_dissipative_for_a_density_jump(flux):
+    """A subsonic rightward entropy wave: the upwind splittings move the mass
+    flux from the central average towards the upstream (left) state."""
+    P = default_params(flux=flux)
+    VL = np.array([1.0, 0.5, 0.0, 0.0, 1.0])
+    VR = np.array([0.5, 0.5, 0.0, 0.0, 1.0])
+    got = oracle.face_flux(P, VL, VR, [1.0, 0.0, 0.0])
+    central = 0.5 * (1.0 * 0.5 + 0.5 * 0.5)
+    assert got[0] > central + 0.1 * (0.5 - central)

@@ -281,3 +281,21 @@ def test_jvp_matches_central_differences(lim, fix_all):
     h = 1e-6
     fd = (o.residual(q + h * dq) - o.residual(q - h * dq)) / (2 * h)
     assert np.abs(fd - dR).max() <= 1e-6 * np.abs(dR).max()
+
+
+@pytest.mark.parametrize("flux", [1, 2])
+def test_fvs_truncation_error_second_order_and_free_stream(flux):
+    """The flux-vector splittings keep the scheme's properties: second-order
+    truncation error under the manufactured solution (unlimited) and
+    free-stream preservation on the perturbed grid."""
+    errs = []
+    for n in (8, 16, 32):
+        pb = cases.mms_3d(n, curvilinear=True, limiter=0, flux=flux)
+        o = oracle.Oracle(pb)
+        tau = o.residual(pb.q.copy()).reshape(5, n, n, n) / o.metrics[0][3]
+        errs.append(math.sqrt((tau ** 2).mean()))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert (orders > 1.8).all(), orders
+    pb = cases.uniform_3d(12, curvilinear=True, flux=flux)
+    o = oracle.Oracle(pb)
+    assert np.abs(o.residual(pb.q.copy())).max() <= 1e-13 * flux_scale(o, pb.q)
