@@ -63,6 +63,14 @@ def alu_peak(precision: str) -> float:
 
 
 def workload(name: str):
+    """Benchmark workloads; a suffix '+vl' or '+sw' selects the van Leer or
+    Steger-Warming face flux instead of Roe."""
+    if "+" in name:
+        base, suf = name.split("+", 1)
+        pb = workload(base)
+        pb.params["flux"] = {"vl": 1, "sw": 2}[suf]
+        pb.name += "_" + {"vl": "vanleer_fvs", "sw": "steger_warming"}[suf]
+        return pb
     if name == "mms128":
         return cases.mms_3d(128, curvilinear=True)
     if name == "large":
@@ -514,7 +522,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
-    ap.add_argument("--variant-workloads", default="mms128,multiblock,large")
+    ap.add_argument("--variant-workloads", default="mms128,multiblock,large,mms128+vl,mms128+sw")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -65,6 +65,10 @@ typedef enum {
 
 typedef enum { FV_LIM_NONE = 0, FV_LIM_VANLEER = 1, FV_LIM_VANALBADA = 2 } fv_limiter;
 
+/* Face flux (Section 2: Roe's flux-difference splitting, Steger-Warming and
+ * van Leer flux-vector splitting are SENSEI's inviscid fluxes). */
+typedef enum { FV_FLUX_ROE = 0, FV_FLUX_VANLEER = 1, FV_FLUX_STEGER_WARMING = 2 } fv_flux;
+
 typedef struct fv_ctx* fv_handle;
 
 /* One block.  nodes: HOST pointer to (nk+1)(nj+1)(ni+1) x 3 doubles
@@ -111,7 +115,9 @@ typedef struct {
  *     prefetched by cp.async - 6 and 7 for FV_PREC_FP32FLUX only -, 8: 32x7 / 256).
  *   kchunk: k-planes per tile; 0 = automatic (about three tiles per resident
  *     CTA slot); -w = about w tiles per resident CTA slot.  Tiles are handed
- *     to persistent CTAs largest first through a device counter. */
+ *     to persistent CTAs largest first through a device counter.
+ *   flux: fv_flux (Roe by default); van Leer F+- split by the normal Mach
+ *     number, Steger-Warming by the eigenvalues; F^ = F+(V_L) + F-(V_R). */
 typedef struct {
   double gamma, eps, kappa, harten, va_delta2;
   int limiter, fix_all, dim, n_stages;
@@ -119,11 +125,12 @@ typedef struct {
   int precision;
   int tile;
   int kchunk;
+  int flux;
 } fv_config;
 
 /* Fill *cfg with the defaults: gamma 1.4, eps 1, kappa -1, van Leer,
  * harten 0.1, fix_all 0, va_delta2 1e-12, dim 3, 4 stages with
- * alpha = (1/4, 1/3, 1/2, 1), FV_PREC_FP64, automatic tiles. */
+ * alpha = (1/4, 1/3, 1/2, 1), FV_PREC_FP64, automatic tiles, Roe flux. */
 void fv_config_default(fv_config* cfg);
 
 /* Create the solver state on the current CUDA device: validates blocks and
@@ -219,7 +226,8 @@ int fv_get_launch(fv_handle h, int* out4);
  * lam_in_dev (packed interior field) <- (dQ^(m)/dQ^(m-1))^T lam_out,
  * including the transpose of the exchange (ghost cotangents added into their
  * donor cells); lam_q0_dev (packed interior field) += lam_out.  qin_dev is
- * not modified.  Fixed ghost cells are constants. */
+ * not modified.  Fixed ghost cells are constants.  Built for FV_PREC_FP64
+ * handles with the Roe flux (FV_ERR_UNSUPPORTED otherwise). */
 int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
                    double* lam_in_dev, double* lam_q0_dev, void* stream);
 

@@ -49,7 +49,8 @@ class fv_config(ctypes.Structure):
                 ("harten", ctypes.c_double), ("va_delta2", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("fix_all", ctypes.c_int), ("dim", ctypes.c_int),
                 ("n_stages", ctypes.c_int), ("alpha", ctypes.c_double * 8),
-                ("precision", ctypes.c_int), ("tile", ctypes.c_int), ("kchunk", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("tile", ctypes.c_int), ("kchunk", ctypes.c_int),
+                ("flux", ctypes.c_int)]
 
 
 _lib = None
@@ -157,6 +158,7 @@ class Solver:
         cfg.va_delta2 = params.get("va_delta2", 1e-12)
         cfg.limiter = int(params.get("limiter", 1))
         cfg.fix_all = int(params.get("fix_all", 0))
+        cfg.flux = int(params.get("flux", 0))
         cfg.dim = int(dim)
         alpha = params.get("alpha", (0.25, 1.0 / 3.0, 0.5, 1.0))
         cfg.n_stages = len(alpha)

@@ -313,6 +313,7 @@ FvStageArgs base_args(fv_ctx* h) {
   a.fp.va_delta2 = h->cfg.va_delta2;
   a.fp.limiter = h->cfg.limiter;
   a.fp.fix_all = h->cfg.fix_all;
+  a.fp.flux = h->cfg.flux;
   return a;
 }
 
@@ -451,6 +452,7 @@ int validate(const fv_block_desc* blocks, int nblocks, const fv_connection* conn
   if (cfg->n_stages < 2 || cfg->n_stages > 8) return fail(nullptr, FV_ERR_INVALID_ARG, "n_stages must be 2..8");
   if (cfg->precision < 0 || cfg->precision > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown precision");
   if (cfg->limiter < 0 || cfg->limiter > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown limiter");
+  if (cfg->flux < 0 || cfg->flux > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown face flux");
   if (!(cfg->gamma > 1.0)) return fail(nullptr, FV_ERR_INVALID_ARG, "gamma must exceed 1");
   for (int b = 0; b < nblocks; ++b) {
     const fv_block_desc& d = blocks[b];
@@ -890,6 +892,7 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
   if (!qin_dev || !lam_out_dev || !lam_in_dev || !lam_q0_dev) return fail(h, FV_ERR_INVALID_ARG, "NULL pointer");
   if (h->cfg.precision != FV_PREC_FP64)
     return fail(h, FV_ERR_UNSUPPORTED, "the adjoint runs in binary64: create the handle with FV_PREC_FP64");
+  if (h->cfg.flux != FV_FLUX_ROE) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint is built for the Roe flux");
   cudaStream_t s = (cudaStream_t)stream;
   const int nd = h->cfg.dim;
   // per-direction offsets of each block's faces in the contribution scratch

@@ -180,6 +180,8 @@ template <> struct Sc<double> {
   static __device__ __forceinline__ bool above(double a, float t) { return a > (double)t; }
   using mask = bool;
   static __device__ __forceinline__ double sel(bool m, double a, double b) { return m ? a : b; }
+  static __device__ __forceinline__ bool ge(double a, float t) { return a >= (double)t; }
+  static __device__ __forceinline__ bool le(double a, float t) { return a <= (double)t; }
 };
 
 template <> struct Sc<float> {
@@ -199,6 +201,8 @@ template <> struct Sc<float> {
   static __device__ __forceinline__ bool above(float a, float t) { return a > t; }
   using mask = bool;
   static __device__ __forceinline__ float sel(bool m, float a, float b) { return m ? a : b; }
+  static __device__ __forceinline__ bool ge(float a, float t) { return a >= t; }
+  static __device__ __forceinline__ bool le(float a, float t) { return a <= t; }
 };
 
 template <> struct Sc<df64> {
@@ -218,4 +222,6 @@ template <> struct Sc<df64> {
   static __device__ __forceinline__ bool above(df64 a, float t) { return a.hi > t; }
   using mask = bool;
   static __device__ __forceinline__ df64 sel(bool m, df64 a, df64 b) { return m ? a : b; }
+  static __device__ __forceinline__ bool ge(df64 a, float t) { return a.hi > t || (a.hi == t && a.lo >= 0.0f); }
+  static __device__ __forceinline__ bool le(df64 a, float t) { return a.hi < t || (a.hi == t && a.lo <= 0.0f); }
 };

@@ -18,6 +18,9 @@ struct FaceC {
   T e4km, e4kp;   // eps/4 (1 - kappa), eps/4 (1 + kappa)
   T harten;       // entropy-fix width / c~
   T va_d2;        // van Albada delta^2
+  T g, ig, i2g, gm1x2, igm1, i2g2m1, quarter, two;   // gamma, 1/gamma, 1/(2 gamma), 2(gamma-1),
+                                                     // 1/(gamma-1), 1/(2(gamma^2-1)), 1/4, 2
+  int flux;       // 0 Roe, 1 van Leer flux-vector splitting, 2 Steger-Warming
   int limiter, fix_all, has_fix;
   int upwind_only;  // kappa == -1: the (1+kappa) terms of Eq. (flux) vanish
 };
@@ -34,6 +37,15 @@ __device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
   c.e4kp = S::c(p.eps * 0.25 * (1.0 + p.kappa));
   c.harten = S::c(p.harten);
   c.va_d2 = S::c(p.va_delta2);
+  c.g = S::c(p.gamma);
+  c.ig = S::c(1.0 / p.gamma);
+  c.i2g = S::c(0.5 / p.gamma);
+  c.gm1x2 = S::c(2.0 * (p.gamma - 1.0));
+  c.igm1 = S::c(1.0 / (p.gamma - 1.0));
+  c.i2g2m1 = S::c(0.5 / (p.gamma * p.gamma - 1.0));
+  c.quarter = S::c(0.25);
+  c.two = S::c(2.0);
+  c.flux = p.flux;
   c.limiter = p.limiter;
   c.fix_all = p.fix_all;
   c.has_fix = p.harten > 0.0;
@@ -157,6 +169,85 @@ __device__ __forceinline__ void roe_flux(const FaceC<T>& C, const T VL[5], const
   out[4] = ((mL * hL + mR * hR) - D4) * hA;
 }
 
+// ---------------------------------------------------------------------------
+// Flux-vector splittings (Section 2 lists them beside Roe): F^ = F+(V_L) +
+// F-(V_R), times the face area.
+// ---------------------------------------------------------------------------
+
+// van Leer: split by the normal Mach number; sgn = +1 (F+) or -1 (F-)
+template <class T>
+__device__ __forceinline__ void vanleer_part(const FaceC<T>& C, const T V[5], T nx, T ny, T nz, int sgn,
+                                             T F[5]) {
+  using S = Sc<T>;
+  const T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  const T c = S::sqrt(C.g * p * S::rcp(r));
+  const T Vn = nx * u + ny * v + nz * w;
+  const T M = Vn * S::rcp(c);
+  const bool sup = S::ge(M, 1.0f), sub = S::le(M, -1.0f);
+  if (sup || sub) {
+    if (sup == (sgn > 0)) {
+      const T ht = C.g_gm1 * p * S::rcp(r) + C.half * (u * u + v * v + w * w);
+      const T m = r * Vn;
+      F[0] = m; F[1] = m * u + nx * p; F[2] = m * v + ny * p; F[3] = m * w + nz * p; F[4] = m * ht;
+    } else {
+#pragma unroll
+      for (int n = 0; n < 5; ++n) F[n] = S::c(0.0);
+    }
+    return;
+  }
+  const T one = sgn > 0 ? C.one : S::c(-1.0);
+  const T mp = M + one;
+  const T fm = one * r * c * mp * mp * C.quarter;
+  const T c2 = C.two * c;
+  const T a = (one * c2 - Vn) * C.ig;
+  const T e = C.gm1 * Vn + one * c2;
+  F[0] = fm;
+  F[1] = fm * (u + nx * a);
+  F[2] = fm * (v + ny * a);
+  F[3] = fm * (w + nz * a);
+  F[4] = fm * (e * e * C.i2g2m1 + C.half * (u * u + v * v + w * w - Vn * Vn));
+}
+
+// Steger-Warming: eigenvalue splitting l+- = (l +- |l|)/2
+template <class T>
+__device__ __forceinline__ void steger_warming_part(const FaceC<T>& C, const T V[5], T nx, T ny, T nz, int sgn,
+                                                    T F[5]) {
+  using S = Sc<T>;
+  const T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  const T c = S::sqrt(C.g * p * S::rcp(r));
+  const T Vn = nx * u + ny * v + nz * w;
+  const T one = sgn > 0 ? C.one : S::c(-1.0);
+  const T l1 = C.half * ((Vn - c) + one * S::abs(Vn - c));
+  const T l2 = C.half * (Vn + one * S::abs(Vn));
+  const T l5 = C.half * ((Vn + c) + one * S::abs(Vn + c));
+  const T q2 = u * u + v * v + w * w;
+  const T H = c * c * C.igm1 + C.half * q2;
+  const T k = r * C.i2g;
+  const T a2 = C.gm1x2 * l2;
+  const T l15 = l1 + l5, d51 = (l5 - l1) * c;
+  F[0] = k * (a2 + l15);
+  F[1] = k * (a2 * u + l15 * u + d51 * nx);
+  F[2] = k * (a2 * v + l15 * v + d51 * ny);
+  F[3] = k * (a2 * w + l15 * w + d51 * nz);
+  F[4] = k * (a2 * (C.half * q2) + l15 * H + d51 * Vn);
+}
+
+template <class T>
+__device__ __forceinline__ void face_riemann(const FaceC<T>& C, const T VL[5], const T VR[5], T nx, T ny, T nz, T A,
+                                             T out[5]) {
+  if (C.flux == 0) { roe_flux(C, VL, VR, nx, ny, nz, A, out); return; }
+  T Fp[5], Fm[5];
+  if (C.flux == 1) {
+    vanleer_part(C, VL, nx, ny, nz, +1, Fp);
+    vanleer_part(C, VR, nx, ny, nz, -1, Fm);
+  } else {
+    steger_warming_part(C, VL, nx, ny, nz, +1, Fp);
+    steger_warming_part(C, VR, nx, ny, nz, -1, Fm);
+  }
+#pragma unroll
+  for (int n = 0; n < 5; ++n) out[n] = (Fp[n] + Fm[n]) * A;
+}
+
 // Full face: reconstruct the 5 primitive components along the stencil
 // c0..c3 (pointers to component 0 of each cell, components `cs` apart) and
 // evaluate the Roe flux times area.
@@ -166,7 +257,7 @@ __device__ __forceinline__ void face_flux(const FaceC<T>& C, const T* c0, const 
   T VL[5], VR[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) muscl(C, c0[n * cs], c1[n * cs], c2[n * cs], c3[n * cs], VL[n], VR[n]);
-  roe_flux(C, VL, VR, nx, ny, nz, A, out);
+  face_riemann(C, VL, VR, nx, ny, nz, A, out);
 }
 
 // Full face from stencil values held in registers: v[c][n] is component n of
@@ -177,7 +268,7 @@ __device__ __forceinline__ void face_flux_vals(const FaceC<T>& C, const T (&v)[4
   T VL[5], VR[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) muscl(C, v[0][n], v[1][n], v[2][n], v[3][n], VL[n], VR[n]);
-  roe_flux(C, VL, VR, nx, ny, nz, A, out);
+  face_riemann(C, VL, VR, nx, ny, nz, A, out);
 }
 
 // The double-float face is large; one out-of-line copy per kernel keeps the

@@ -37,7 +37,7 @@ struct FvConnDev {
 
 struct FvFaceParams {
   double gamma, eps, kappa, harten, va_delta2;
-  int limiter, fix_all;
+  int limiter, fix_all, flux;
 };
 
 enum { FV_MODE_RK = 0, FV_MODE_RESIDUAL = 1 };
