@@ -185,9 +185,9 @@ template <> struct Sc<double> {
 };
 
 template <> struct Sc<float> {
-  // hardware conversion: runs on the otherwise idle FP64 unit instead of
-  // ~12 integer instructions on the shared FP32/INT lanes
-  static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+  // integer conversion: the hardware one runs on the FP64 unit, which GB300
+  // gives 1/64 of the binary32 rate and which then limits the whole kernel
+  static __device__ __forceinline__ float from_d(double x) { return fv_d2f_rn(x); }
   static __device__ __forceinline__ double to_d(float x) { return fv_f2d(x); }
   static __device__ __forceinline__ float c(double x) { return (float)x; }
   // approximate (MUFU) reciprocal and square root: the binary32 flux form

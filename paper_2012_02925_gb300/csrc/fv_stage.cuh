@@ -208,10 +208,18 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
     auto face_item = [&](int it, int& dir, int& off, int& dst, long long& met) {
       dir = -1;
       if (it < NXI) {
-        const int y = it / (TX + 1), x = it - y * (TX + 1);     // face between cells x-1 and x
+        // the TX faces x < TX of every row first, row by row, then the last
+        // face of each row: a warp then reads whole rows of the plane
+        // without shared-memory bank conflicts
+        int y, x;                                              // face between cells x-1 and x
+        if (it < TX * TY) {
+          y = it / TX; x = it - y * TX;
+        } else {
+          y = it - TX * TY; x = TX;
+        }
         const int i = i0 + x, j = j0 + y;
         if (i <= ni && j < nj) {
-          dir = 0; off = (y + 2) * W + x; dst = it;
+          dir = 0; off = (y + 2) * W + x; dst = y * (TX + 1) + x;
           met = B.face_off[0] + (long long)j * (ni + 1) + i;
         }
       } else if (it < NXI + NETA) {
@@ -339,6 +347,12 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
             if constexpr (std::is_same<AT, double>::value) {
 #pragma unroll
               for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], args.alpha_dt, iv, R[n]);
+            } else if constexpr (std::is_same<T, float>::value) {
+              // binary32 increment (its rounding is far below the error of
+              // the binary32 face fluxes it sums), one binary64 add
+              const float fac = FMUL(fv_d2f_rn(args.alpha_dt), fv_d2f_rn(iv));
+#pragma unroll
+              for (int n = 0; n < 5; ++n) qo[n * pl] = q0[n * pl] - fv_f2d(FMUL(fac, FADD(R[n].hi, R[n].lo)));
             } else {
               const df64 fac = fv_d2df(args.alpha_dt) * fv_d2df(iv);
 #pragma unroll
