@@ -286,8 +286,12 @@ int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
   int rc;
   switch (h->cfg.precision) {
     case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, h->launch, s); break;
-    case FV_PREC_DF64: rc = fv_launch_stage_df64(a, h->launch, s); break;
-    default: rc = fv_launch_stage_fp32(a, h->launch, s); break;
+    case FV_PREC_DF64:
+      rc = h->launch.fast ? fv_launch_stage_df64_fast(a, h->launch, s) : fv_launch_stage_df64(a, h->launch, s);
+      break;
+    default:
+      rc = h->launch.fast ? fv_launch_stage_fp32_fast(a, h->launch, s) : fv_launch_stage_fp32(a, h->launch, s);
+      break;
   }
   if (rc == -2) return fail(h, FV_ERR_UNSUPPORTED, "tile shape not compiled");
   if (rc != 0) return cuda_fail(h, cudaGetLastError(), "stage kernel launch");
@@ -387,14 +391,17 @@ void choose_launch(fv_ctx* h) {
   l.tx = FV_SHAPE_TABLE[shape - 1][0];
   l.ty = FV_SHAPE_TABLE[shape - 1][1];
   l.threads = FV_SHAPE_TABLE[shape - 1][2];
+  l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.kappa, c.harten, c.fix_all);
   h->launch = l;
 }
 
 int query_occupancy(fv_ctx* h, size_t* smem) {
   switch (h->cfg.precision) {
     case FV_PREC_FP64: return fv_stage_occupancy_fp64(h->launch, smem);
-    case FV_PREC_DF64: return fv_stage_occupancy_df64(h->launch, smem);
-    default: return fv_stage_occupancy_fp32(h->launch, smem);
+    case FV_PREC_DF64:
+      return h->launch.fast ? fv_stage_occupancy_df64_fast(h->launch, smem) : fv_stage_occupancy_df64(h->launch, smem);
+    default:
+      return h->launch.fast ? fv_stage_occupancy_fp32_fast(h->launch, smem) : fv_stage_occupancy_fp32(h->launch, smem);
   }
 }
 

@@ -23,6 +23,31 @@ struct FaceC {
   int flux;       // 0 Roe, 1 van Leer flux-vector splitting, 2 Steger-Warming
   int limiter, fix_all, has_fix;
   int upwind_only;  // kappa == -1: the (1+kappa) terms of Eq. (flux) vanish
+  // the scheme switches as the face code reads them
+  __device__ __forceinline__ int k_flux() const { return flux; }
+  __device__ __forceinline__ int k_lim() const { return limiter; }
+  __device__ __forceinline__ int k_upw() const { return upwind_only; }
+  __device__ __forceinline__ int k_fix() const { return has_fix; }
+  __device__ __forceinline__ int k_fixall() const { return fix_all; }
+  static __device__ __forceinline__ FaceC from(const FaceC& b) { return b; }
+};
+
+// The default scheme fixed at compile time - Roe flux, van Leer limiter,
+// kappa = -1, Harten fix on the acoustic waves only - so that the face code
+// carries no run-time switches (their branches split the face into basic
+// blocks the scheduler cannot interleave).  Same data as FaceC.
+template <class T>
+struct FaceCFast : FaceC<T> {
+  __device__ __forceinline__ int k_flux() const { return 0; }
+  __device__ __forceinline__ int k_lim() const { return 1; }
+  __device__ __forceinline__ int k_upw() const { return 1; }
+  __device__ __forceinline__ int k_fix() const { return 1; }
+  __device__ __forceinline__ int k_fixall() const { return 0; }
+  static __device__ __forceinline__ FaceCFast from(const FaceC<T>& b) {
+    FaceCFast f;
+    static_cast<FaceC<T>&>(f) = b;
+    return f;
+  }
 };
 
 template <class T>
@@ -54,8 +79,8 @@ __device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
 }
 
 // Q = (rho, rho u, rho v, rho w, rho e_t) -> V = (rho, u, v, w, p)
-template <class T>
-__device__ __forceinline__ void prim_from_cons(const FaceC<T>& C, const T q[5], T V[5]) {
+template <class T, class CC>
+__device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]) {
   T rinv = Sc<T>::rcp(q[0]);
   T u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
   V[0] = q[0];
@@ -66,11 +91,11 @@ __device__ __forceinline__ void prim_from_cons(const FaceC<T>& C, const T q[5], 
 }
 
 // Psi(a/b) * b
-template <class T>
-__device__ __forceinline__ T limited(const FaceC<T>& C, T a, T b) {
+template <class T, class CC>
+__device__ __forceinline__ T limited(const CC& C, T a, T b) {
   using S = Sc<T>;
-  if (C.limiter == 0) return b;
-  if (C.limiter == 1) {
+  if (C.k_lim() == 0) return b;
+  if (C.k_lim() == 1) {
     // van Leer, Psi(r) = (r + |r|)/(1 + |r|):  Psi(a/b) b = (a|b| + |a| b)/(|a| + |b|)
     // Both differences below 1e-30 (rounding noise of a quantity that is
     // zero, e.g. a transverse velocity): zero slope, as the oracle's guarded
@@ -88,10 +113,10 @@ __device__ __forceinline__ T limited(const FaceC<T>& C, T a, T b) {
 }
 
 // Eq. (flux) for one component from V_{i-1}, V_i, V_{i+1}, V_{i+2}
-template <class T>
-__device__ __forceinline__ void muscl(const FaceC<T>& C, T vm1, T v0, T vp1, T vp2, T& L, T& R) {
+template <class T, class CC>
+__device__ __forceinline__ void muscl(const CC& C, T vm1, T v0, T vp1, T vp2, T& L, T& R) {
   T dm = v0 - vm1, d0 = vp1 - v0, dp = vp2 - vp1;
-  if (C.upwind_only) {
+  if (C.k_upw()) {
     L = v0 + C.e4km * limited(C, d0, dm);
     R = vp1 - C.e4km * limited(C, d0, dp);
   } else {
@@ -101,16 +126,16 @@ __device__ __forceinline__ void muscl(const FaceC<T>& C, T vm1, T v0, T vp1, T v
 }
 
 // Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d
-template <class T>
-__device__ __forceinline__ T entropy_fixed(const FaceC<T>& C, T lam, T delta) {
+template <class T, class CC>
+__device__ __forceinline__ T entropy_fixed(const CC& C, T lam, T delta) {
   if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * (C.half * Sc<T>::rcp(delta));
   return lam;
 }
 
 // Roe flux times face area for reconstructed primitive states VL, VR and the
 // unit normal (nx, ny, nz) with area A.
-template <class T>
-__device__ __forceinline__ void roe_flux(const FaceC<T>& C, const T VL[5], const T VR[5], T nx, T ny,
+template <class T, class CC>
+__device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[5], T nx, T ny,
                                          T nz, T A, T out[5]) {
   using S = Sc<T>;
   const T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
@@ -140,11 +165,11 @@ __device__ __forceinline__ void roe_flux(const FaceC<T>& C, const T VL[5], const
   const T dVn = VnR - VnL;
 
   T l1 = S::abs(Vnt - ct), l2 = S::abs(Vnt), l5 = S::abs(Vnt + ct);
-  if (C.has_fix) {
+  if (C.k_fix()) {
     const T delta = C.harten * ct;
     l1 = entropy_fixed(C, l1, delta);
     l5 = entropy_fixed(C, l5, delta);
-    if (C.fix_all) l2 = entropy_fixed(C, l2, delta);
+    if (C.k_fixall()) l2 = entropy_fixed(C, l2, delta);
   }
   const T rcd = rt * ct * dVn;
   const T hic2 = C.half * ic2;
@@ -175,8 +200,8 @@ __device__ __forceinline__ void roe_flux(const FaceC<T>& C, const T VL[5], const
 // ---------------------------------------------------------------------------
 
 // van Leer: split by the normal Mach number; sgn = +1 (F+) or -1 (F-)
-template <class T>
-__device__ __forceinline__ void vanleer_part(const FaceC<T>& C, const T V[5], T nx, T ny, T nz, int sgn,
+template <class T, class CC>
+__device__ __forceinline__ void vanleer_part(const CC& C, const T V[5], T nx, T ny, T nz, int sgn,
                                              T F[5]) {
   using S = Sc<T>;
   const T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
@@ -209,8 +234,8 @@ __device__ __forceinline__ void vanleer_part(const FaceC<T>& C, const T V[5], T 
 }
 
 // Steger-Warming: eigenvalue splitting l+- = (l +- |l|)/2
-template <class T>
-__device__ __forceinline__ void steger_warming_part(const FaceC<T>& C, const T V[5], T nx, T ny, T nz, int sgn,
+template <class T, class CC>
+__device__ __forceinline__ void steger_warming_part(const CC& C, const T V[5], T nx, T ny, T nz, int sgn,
                                                     T F[5]) {
   using S = Sc<T>;
   const T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
@@ -232,12 +257,12 @@ __device__ __forceinline__ void steger_warming_part(const FaceC<T>& C, const T V
   F[4] = k * (a2 * (C.half * q2) + l15 * H + d51 * Vn);
 }
 
-template <class T>
-__device__ __forceinline__ void face_riemann(const FaceC<T>& C, const T VL[5], const T VR[5], T nx, T ny, T nz, T A,
+template <class T, class CC>
+__device__ __forceinline__ void face_riemann(const CC& C, const T VL[5], const T VR[5], T nx, T ny, T nz, T A,
                                              T out[5]) {
-  if (C.flux == 0) { roe_flux(C, VL, VR, nx, ny, nz, A, out); return; }
+  if (C.k_flux() == 0) { roe_flux(C, VL, VR, nx, ny, nz, A, out); return; }
   T Fp[5], Fm[5];
-  if (C.flux == 1) {
+  if (C.k_flux() == 1) {
     vanleer_part(C, VL, nx, ny, nz, +1, Fp);
     vanleer_part(C, VR, nx, ny, nz, -1, Fm);
   } else {
@@ -251,8 +276,8 @@ __device__ __forceinline__ void face_riemann(const FaceC<T>& C, const T VL[5], c
 // Full face: reconstruct the 5 primitive components along the stencil
 // c0..c3 (pointers to component 0 of each cell, components `cs` apart) and
 // evaluate the Roe flux times area.
-template <class T>
-__device__ __forceinline__ void face_flux(const FaceC<T>& C, const T* c0, const T* c1, const T* c2,
+template <class T, class CC>
+__device__ __forceinline__ void face_flux(const CC& C, const T* c0, const T* c1, const T* c2,
                                           const T* c3, int cs, T nx, T ny, T nz, T A, T out[5]) {
   T VL[5], VR[5];
 #pragma unroll
@@ -262,26 +287,11 @@ __device__ __forceinline__ void face_flux(const FaceC<T>& C, const T* c0, const 
 
 // Full face from stencil values held in registers: v[c][n] is component n of
 // stencil cell c (c = 0..3 along the face normal).
-template <class T>
-__device__ __forceinline__ void face_flux_vals(const FaceC<T>& C, const T (&v)[4][5], T nx, T ny, T nz, T A,
+template <class T, class CC>
+__device__ __forceinline__ void face_flux_vals(const CC& C, const T (&v)[4][5], T nx, T ny, T nz, T A,
                                                T out[5]) {
   T VL[5], VR[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) muscl(C, v[0][n], v[1][n], v[2][n], v[3][n], VL[n], VR[n]);
   face_riemann(C, VL, VR, nx, ny, nz, A, out);
-}
-
-// The double-float face is large; one out-of-line copy per kernel keeps the
-// code size (and the compile time) in check.  Constants come from shared
-// memory and results go straight to their shared-memory destination so that
-// the call needs no stack frame.
-template <class T>
-__device__ __noinline__ void face_flux_outlined(const FaceC<T>* __restrict__ Cp, const T* c0, const T* c1,
-                                                const T* c2, const T* c3, int cs, T nx, T ny, T nz, T A,
-                                                T* dst, int dstr) {
-  const FaceC<T> C = *Cp;
-  T out[5];
-  face_flux(C, c0, c1, c2, c3, cs, nx, ny, nz, A, out);
-#pragma unroll
-  for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
 }

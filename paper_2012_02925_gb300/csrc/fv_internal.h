@@ -69,15 +69,28 @@ struct FvLaunch {
   int tx, ty, threads;          // tile shape
   int grid;                     // CTAs (persistent)
   int three_d;
+  int fast;                     // the kernel with the default scheme compiled in
 };
 
+// The default scheme (Roe flux, van Leer limiter, kappa = -1, Harten fix on
+// the acoustic waves only) has kernels with its switches fixed at compile time.
+inline bool fv_default_scheme(int flux, int limiter, double kappa, double harten, int fix_all) {
+  return flux == 0 && limiter == 1 && kappa == -1.0 && harten > 0.0 && fix_all == 0;
+}
+
+// binary64 has the generic kernels only; the other forms have both, in two
+// translation units each (fv_stage_<form>.cu, fv_stage_<form>_fast.cu)
 int fv_launch_stage_fp64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
 int fv_launch_stage_df64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_df64_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
 int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_fp32_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
 // occupancy queries: CTAs per SM for a tile shape (0 = shape not compiled)
 int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem_bytes);
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
 constexpr int FV_NUM_SHAPES = 8;

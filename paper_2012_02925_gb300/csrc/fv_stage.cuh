@@ -79,9 +79,10 @@ constexpr int stage_min_ctas() {
   return sizeof(T) == 4 ? (NT <= 128 ? 8 : 4) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
 }
 
-template <class T, int TX, int TY, int NT, bool DIM3, bool PF>
+template <class T, int TX, int TY, int NT, bool DIM3, bool PF, bool FAST>
 __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel(const FvStageArgs args) {
   using S = Sc<T>;
+  using CC = typename std::conditional<FAST, FaceCFast<T>, FaceC<T>>::type;
   using AT = typename Acc<T>::type;
   using MT = typename MetricStore<T>::type;
   using SM = StageSmem<T, TX, TY>;
@@ -98,10 +99,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
   double* stg = reinterpret_cast<double*>(smem_raw + ((SM::typed(DIM3) + 15) / 16) * 16);  // [5][H][W] (PF)
 
   const int tid = threadIdx.x;
-  const FaceC<T> C = make_face_consts<T>(args.fp);
-  __shared__ FaceC<T> Cs;
-  if (tid == 0) Cs = C;
-  __syncthreads();
+  const CC C = CC::from(make_face_consts<T>(args.fp));
   const MT* mxi = reinterpret_cast<const MT*>(args.metric[0]);
   const MT* meta = reinterpret_cast<const MT*>(args.metric[1]);
   const MT* mzeta = reinterpret_cast<const MT*>(args.metric[2]);
@@ -191,14 +189,10 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         nx = MetricStore<T>::ld(m, f); ny = MetricStore<T>::ld(m, f + ms);
         nz = MetricStore<T>::ld(m, f + 2 * ms); A = MetricStore<T>::ld(m, f + 3 * ms);
       }
-      if constexpr (std::is_same<T, df64>::value) {
-        face_flux_outlined(&Cs, s0, s1, s2, s3, PL, nx, ny, nz, A, dst, dstr);
-      } else {
-        T out[5];
-        face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
+      T out[5];
+      face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
 #pragma unroll
-        for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
-      }
+      for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
     };
     // ... and, for each face item it = tid + r*NT, the face it evaluates:
     // direction, stencil offset inside a plane (xi, eta) or column offset
@@ -241,27 +235,18 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
     };
     const long long kfx = (long long)nj * (ni + 1), kfy = (long long)(nj + 1) * ni, kfz = (long long)nj * ni;
     // zeta face between planes kf-1 and kf (stencil kf-2 .. kf+1) at column offset c
-    auto zeta_face = [&](int kf, int c, long long fm, T* dst) {
-      do_face(Vs + ((kf - 2) & 3) * 5 * PL + c, Vs + ((kf - 1) & 3) * 5 * PL + c, Vs + (kf & 3) * 5 * PL + c,
-              Vs + ((kf + 1) & 3) * 5 * PL + c, 2, fm + kf * kfz, dst, NZETA);
-    };
     if (DIM3) {
-      for (int s = -2; s <= 1; ++s) load_plane(k0 + s, (k0 + s) & 3);
-      __syncthreads();
-      if (PF) prefetch_plane(k0 + 2);
-      for (int it = tid; it < NFACE; it += NT) {
-        int d, off, dst;
-        long long met;
-        face_item(it, d, off, dst, met);
-        if (d == 2) zeta_face(k0, off, met, Fz + (k0 & 1) * 5 * NZETA + dst);
-      }
-      __syncthreads();
+      // planes k0-2 .. k0 now; plane k0+1 arrives in the first pass below
+      for (int s = -2; s <= 0; ++s) load_plane(k0 + s, (k0 + s) & 3);
+      if (PF) prefetch_plane(k0 + 1);
     } else {
       load_plane(0, 0);
       __syncthreads();
     }
 
-    for (int k = k0; k < k1; ++k) {
+    // In 3D the first pass (k = k0 - 1) evaluates only the zeta faces below
+    // plane k0; every later pass is one plane.
+    for (int k = DIM3 ? k0 - 1 : k0; k < k1; ++k) {
       const int slot = DIM3 ? (k & 3) : 0;
       if (DIM3) {
         if (PF) {
@@ -274,22 +259,40 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         }
       }
       const T* P = Vs + slot * 5 * PL;
-      // ---- every face of this plane (and the zeta faces above it), once ----
+      // ---- every face of this plane (and the zeta faces above it), once;
+      // one call site of the face code for all three directions ----
       for (int it = tid; it < NFACE; it += NT) {
         int d, off, dst;
         long long met;
         face_item(it, d, off, dst, met);
-        if (d == 0) {
-          const T* c0 = P + off;
-          do_face(c0, c0 + 1, c0 + 2, c0 + 3, 0, met + k * kfx, Fx + dst, NXI);
-        } else if (d == 1) {
-          const T* c0 = P + off;
-          do_face(c0, c0 + W, c0 + 2 * W, c0 + 3 * W, 1, met + k * kfy, Fy + dst, NETA);
-        } else if (DIM3 && d == 2) {
-          zeta_face(k + 1, off, met, Fz + ((k + 1) & 1) * 5 * NZETA + dst);
+        if (d < 0 || (DIM3 && k < k0 && d != 2)) continue;
+        const T *s0, *s1, *s2, *s3;
+        T* dp;
+        int dstr;
+        long long f;
+        if (DIM3 && d == 2) {
+          // zeta face between planes k and k+1: stencil k-1 .. k+2 from the ring
+          s0 = Vs + ((k - 1) & 3) * 5 * PL + off;
+          s1 = Vs + (k & 3) * 5 * PL + off;
+          s2 = Vs + ((k + 1) & 3) * 5 * PL + off;
+          s3 = Vs + ((k + 2) & 3) * 5 * PL + off;
+          dp = Fz + ((k + 1) & 1) * 5 * NZETA + dst;
+          dstr = NZETA;
+          f = met + (k + 1) * kfz;
+        } else {
+          const int st = d == 0 ? 1 : W;
+          s0 = P + off;
+          s1 = s0 + st;
+          s2 = s1 + st;
+          s3 = s2 + st;
+          dp = (d == 0 ? Fx : Fy) + dst;
+          dstr = d == 0 ? NXI : NETA;
+          f = met + k * (d == 0 ? kfx : kfy);
         }
+        do_face(s0, s1, s2, s3, d, f, dp, dstr);
       }
       __syncthreads();
+      if (DIM3 && k < k0) continue;
       // ---- per cell: flux differences in a fixed order, then the RK update ----
       for (int cc = tid; cc < TX * TY; cc += NT) {
         const int y = cc / TX, x = cc - y * TX;
@@ -388,27 +391,27 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
 
 // The dynamic shared-memory limit is raised once by occupancy_t (at handle
 // creation), so a launch is a plain enqueue that stream capture accepts.
-template <class T, int TX, int TY, int NT, bool PF>
+template <class T, int TX, int TY, int NT, bool PF, bool FAST>
 static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
   const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0, PF);
   if (l.three_d) {
-    fv_stage_kernel<T, TX, TY, NT, true, PF><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, true, PF, FAST><<<l.grid, NT, smem, s>>>(a);
   } else {
-    fv_stage_kernel<T, TX, TY, NT, false, false><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, false, false, FAST><<<l.grid, NT, smem, s>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <class T, int TX, int TY, int NT, bool PF>
+template <class T, int TX, int TY, int NT, bool PF, bool FAST>
 static int occupancy_t(bool three_d, size_t* smem_out) {
   const size_t smem = StageSmem<T, TX, TY>::bytes(three_d, PF);
   int n = 0;
   if (three_d) {
-    auto k = fv_stage_kernel<T, TX, TY, NT, true, PF>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, true, PF, FAST>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   } else {
-    auto k = fv_stage_kernel<T, TX, TY, NT, false, false>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, false, false, FAST>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   }
@@ -430,22 +433,30 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
   X(7, 32, 4, 128, true)  \
   X(8, 32, 7, 256, false)
 
-template <class T>
+// FAST selects the compile-time default scheme (FaceCFast); each form's
+// translation units instantiate one value of it.
+template <class T, bool FAST>
 int fv_dispatch_launch(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
   constexpr bool allow_pf = std::is_same<T, float>::value;
-#define FV_LAUNCH_CASE(ID, TX, TY, NT, PF) \
-  if (l.shape == ID) { if (PF && !allow_pf) return -2; return launch_stage_t<T, TX, TY, NT, PF && allow_pf>(a, l, s); }
+#define FV_LAUNCH_CASE(ID, TX, TY, NT, PF)                                     \
+  if (l.shape == ID) {                                                          \
+    if (PF && !allow_pf) return -2;                                             \
+    return launch_stage_t<T, TX, TY, NT, PF && allow_pf, FAST>(a, l, s);        \
+  }
   FV_SHAPES(FV_LAUNCH_CASE)
 #undef FV_LAUNCH_CASE
   return -2;
 }
 
-template <class T>
+template <class T, bool FAST>
 int fv_dispatch_occupancy(const FvLaunch& l, size_t* smem) {
   constexpr bool allow_pf = std::is_same<T, float>::value;
   const bool d3 = l.three_d != 0;
-#define FV_OCC_CASE(ID, TX, TY, NT, PF) \
-  if (l.shape == ID) { if (PF && !allow_pf) return 0; return occupancy_t<T, TX, TY, NT, PF && allow_pf>(d3, smem); }
+#define FV_OCC_CASE(ID, TX, TY, NT, PF)                                         \
+  if (l.shape == ID) {                                                          \
+    if (PF && !allow_pf) return 0;                                              \
+    return occupancy_t<T, TX, TY, NT, PF && allow_pf, FAST>(d3, smem);          \
+  }
   FV_SHAPES(FV_OCC_CASE)
 #undef FV_OCC_CASE
   return 0;

@@ -1,7 +1,7 @@
-// Fused stage kernel instantiated for the binary32-flux form.
+// Fused stage kernel instantiated for the binary32-flux form, generic scheme switches.
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<float>(a, l, s);
+  return fv_dispatch_launch<float, false>(a, l, s);
 }
-int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<float>(l, smem); }
+int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<float, false>(l, smem); }

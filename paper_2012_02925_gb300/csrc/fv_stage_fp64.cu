@@ -1,7 +1,7 @@
-// Fused stage kernel instantiated for the binary64 form.
+// Fused stage kernel instantiated for the binary64 form (generic scheme switches).
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<double>(a, l, s);
+  return fv_dispatch_launch<double, false>(a, l, s);
 }
-int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<double>(l, smem); }
+int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<double, false>(l, smem); }
