@@ -391,7 +391,7 @@ void choose_launch(fv_ctx* h) {
   l.tx = FV_SHAPE_TABLE[shape - 1][0];
   l.ty = FV_SHAPE_TABLE[shape - 1][1];
   l.threads = FV_SHAPE_TABLE[shape - 1][2];
-  l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.kappa, c.harten, c.fix_all);
+  l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.eps, c.kappa, c.harten, c.fix_all);
   h->launch = l;
 }
 

@@ -23,17 +23,19 @@ struct FaceC {
   int flux;       // 0 Roe, 1 van Leer flux-vector splitting, 2 Steger-Warming
   int limiter, fix_all, has_fix;
   int upwind_only;  // kappa == -1: the (1+kappa) terms of Eq. (flux) vanish
+  int unit_slope;   // eps (1 - kappa) / 2 == 1: the upwind slope enters with weight one
   // the scheme switches as the face code reads them
   __device__ __forceinline__ int k_flux() const { return flux; }
   __device__ __forceinline__ int k_lim() const { return limiter; }
   __device__ __forceinline__ int k_upw() const { return upwind_only; }
+  __device__ __forceinline__ int k_unit() const { return unit_slope; }
   __device__ __forceinline__ int k_fix() const { return has_fix; }
   __device__ __forceinline__ int k_fixall() const { return fix_all; }
   static __device__ __forceinline__ FaceC from(const FaceC& b) { return b; }
 };
 
 // The default scheme fixed at compile time - Roe flux, van Leer limiter,
-// kappa = -1, Harten fix on the acoustic waves only - so that the face code
+// eps = 1, kappa = -1, Harten fix on the acoustic waves only - so that the face code
 // carries no run-time switches (their branches split the face into basic
 // blocks the scheduler cannot interleave).  Same data as FaceC.
 template <class T>
@@ -41,6 +43,7 @@ struct FaceCFast : FaceC<T> {
   __device__ __forceinline__ int k_flux() const { return 0; }
   __device__ __forceinline__ int k_lim() const { return 1; }
   __device__ __forceinline__ int k_upw() const { return 1; }
+  __device__ __forceinline__ int k_unit() const { return 1; }
   __device__ __forceinline__ int k_fix() const { return 1; }
   __device__ __forceinline__ int k_fixall() const { return 0; }
   static __device__ __forceinline__ FaceCFast from(const FaceC<T>& b) {
@@ -75,6 +78,7 @@ __device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
   c.fix_all = p.fix_all;
   c.has_fix = p.harten > 0.0;
   c.upwind_only = (p.kappa == -1.0);
+  c.unit_slope = (p.eps * 0.5 * (1.0 - p.kappa) == 1.0);
   return c;
 }
 
@@ -90,21 +94,28 @@ __device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]
   V[4] = C.gm1 * (q[4] - C.half * q[0] * (u * u + v * v + w * w));
 }
 
+// Half the van Leer limited slope, Psi(a/b) b / 2 with Psi(r) = (r + |r|)/(1 + |r|).
+// Psi(a/b) b = (a|b| + |a| b)/(|a| + |b|), which is 2ab/(a + b) when a and b
+// have the same sign and 0 otherwise.  Both differences below 1e-30
+// (rounding noise of a quantity that is zero, e.g. a transverse velocity):
+// zero slope, as the oracle's guarded ratio gives to within 2e-30; it also
+// keeps the binary32 reciprocal of a subnormal sum from overflowing.
+template <class T>
+__device__ __forceinline__ T vanleer_half(T a, T b) {
+  using S = Sc<T>;
+  const T p = a * b, s = a + b;
+  const T h = p * S::rcp(s);
+  return S::sel(S::pos(p) && S::above(S::abs(s), 1e-30f), h, S::c(0.0));
+}
+
 // Psi(a/b) * b
 template <class T, class CC>
 __device__ __forceinline__ T limited(const CC& C, T a, T b) {
   using S = Sc<T>;
   if (C.k_lim() == 0) return b;
   if (C.k_lim() == 1) {
-    // van Leer, Psi(r) = (r + |r|)/(1 + |r|):  Psi(a/b) b = (a|b| + |a| b)/(|a| + |b|)
-    // Both differences below 1e-30 (rounding noise of a quantity that is
-    // zero, e.g. a transverse velocity): zero slope, as the oracle's guarded
-    // ratio gives to within 2e-30; it also keeps the binary32 reciprocal of a
-    // subnormal sum from overflowing.
-    const T aa = S::abs(a), ab = S::abs(b);
-    const T den = aa + ab;
-    const T phi = (a * ab + aa * b) * S::rcp(den);
-    return S::sel(S::above(den, 1e-30f), phi, S::c(0.0));
+    const T h = vanleer_half(a, b);
+    return h + h;
   }
   // van Albada in smooth product form: b (a^2 + a b)/(a^2 + b^2 + delta^2)
   const T a2 = a * a;
@@ -116,7 +127,11 @@ __device__ __forceinline__ T limited(const CC& C, T a, T b) {
 template <class T, class CC>
 __device__ __forceinline__ void muscl(const CC& C, T vm1, T v0, T vp1, T vp2, T& L, T& R) {
   T dm = v0 - vm1, d0 = vp1 - v0, dp = vp2 - vp1;
-  if (C.k_upw()) {
+  if (C.k_upw() && C.k_unit() && C.k_lim() == 1) {
+    // eps (1 - kappa)/4 * Psi(a/b) b = Psi(a/b) b / 2
+    L = v0 + vanleer_half(d0, dm);
+    R = vp1 - vanleer_half(d0, dp);
+  } else if (C.k_upw()) {
     L = v0 + C.e4km * limited(C, d0, dm);
     R = vp1 - C.e4km * limited(C, d0, dp);
   } else {

@@ -72,10 +72,11 @@ struct FvLaunch {
   int fast;                     // the kernel with the default scheme compiled in
 };
 
-// The default scheme (Roe flux, van Leer limiter, kappa = -1, Harten fix on
-// the acoustic waves only) has kernels with its switches fixed at compile time.
-inline bool fv_default_scheme(int flux, int limiter, double kappa, double harten, int fix_all) {
-  return flux == 0 && limiter == 1 && kappa == -1.0 && harten > 0.0 && fix_all == 0;
+// The default scheme (Roe flux, van Leer limiter, eps = 1, kappa = -1,
+// Harten fix on the acoustic waves only) has kernels with its switches fixed
+// at compile time.
+inline bool fv_default_scheme(int flux, int limiter, double eps, double kappa, double harten, int fix_all) {
+  return flux == 0 && limiter == 1 && eps == 1.0 && kappa == -1.0 && harten > 0.0 && fix_all == 0;
 }
 
 // binary64 has the generic kernels only; the other forms have both, in two
