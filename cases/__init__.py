@@ -22,17 +22,23 @@ from .core import (GAMMA, GHOST, BlockDesc, Connection, Problem, prim_to_cons,
                    ghosted_shape, pack_state, unpack_state, packed_size,
                    interior_view, nominal_dt, FACE_IMIN, FACE_IMAX, FACE_JMIN,
                    FACE_JMAX, FACE_KMIN, FACE_KMAX, periodic_connections,
-                   conn_array)
+                   conn_array, BCPatch, bc_arrays, BC_FIXED, BC_SUPERSONIC_INFLOW,
+                   BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD, BC_NAMES)
 from .workloads import (vortex_2d, mms_3d, multiblock_batched, large_periodic,
                         perturbed_nodes, uniform_3d, split_problem_i,
-                        mms_primitives, mms_source, rotated_split_problem)
+                        mms_primitives, mms_source, rotated_split_problem,
+                        inlet_2d, ellipse_ogrid, channel_uniform, table_state,
+                        INLET_INFLOW, AIRFOIL_FARFIELD, WING_FARFIELD)
 
 __all__ = [
     "GAMMA", "GHOST", "BlockDesc", "Connection", "Problem", "prim_to_cons",
     "ghosted_shape", "pack_state", "unpack_state", "packed_size",
     "interior_view", "nominal_dt", "FACE_IMIN", "FACE_IMAX", "FACE_JMIN",
     "FACE_JMAX", "FACE_KMIN", "FACE_KMAX", "periodic_connections", "conn_array",
+    "BCPatch", "bc_arrays", "BC_FIXED", "BC_SUPERSONIC_INFLOW", "BC_EXTRAPOLATE",
+    "BC_SLIP_WALL", "BC_FARFIELD", "BC_NAMES",
     "vortex_2d", "mms_3d", "multiblock_batched", "large_periodic",
     "perturbed_nodes", "uniform_3d", "split_problem_i", "mms_primitives",
-    "mms_source", "rotated_split_problem",
+    "mms_source", "rotated_split_problem", "inlet_2d", "ellipse_ogrid",
+    "channel_uniform", "table_state", "INLET_INFLOW", "AIRFOIL_FARFIELD", "WING_FARFIELD",
 ]

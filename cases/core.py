@@ -59,6 +59,26 @@ class Connection:
     transform: Sequence[int] = (1, 2)
 
 
+# Physical boundary kinds of a BCPatch.
+BC_FIXED, BC_SUPERSONIC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD = range(5)
+BC_NAMES = {BC_FIXED: "fixed", BC_SUPERSONIC_INFLOW: "supersonic_inflow", BC_EXTRAPOLATE: "extrapolate",
+            BC_SLIP_WALL: "slip_wall", BC_FARFIELD: "farfield"}
+
+
+@dataclass
+class BCPatch:
+    """Physical boundary on face ``face`` of block ``block`` over tangential
+    cells ``[lo[0], hi[0]) x [lo[1], hi[1])`` (tangential axes in (i,j,k)
+    order with the face normal removed).  ``state`` is the primitive
+    (rho, u, v, w, p) of a supersonic inflow or the farfield free stream."""
+    block: int
+    face: int
+    lo: Sequence[int]
+    hi: Sequence[int]
+    kind: int
+    state: Sequence[float] = (0.0, 0.0, 0.0, 0.0, 0.0)
+
+
 @dataclass
 class Problem:
     blocks: List[BlockDesc]
@@ -69,6 +89,7 @@ class Problem:
     dt: float = 0.0
     params: dict = field(default_factory=dict)
     name: str = ""
+    bcs: List[BCPatch] = field(default_factory=list)
 
     @property
     def ncells(self) -> int:
@@ -171,3 +192,17 @@ def conn_array(conns: Sequence[Connection]) -> np.ndarray:
         a[n] = [c.dst_block, c.dst_face, c.dst_lo[0], c.dst_lo[1], c.dst_hi[0], c.dst_hi[1],
                 c.src_block, c.src_face, c.src_lo[0], c.src_lo[1], c.transform[0], c.transform[1]]
     return a
+
+
+BC_FIELDS = 7
+
+
+def bc_arrays(bcs: Sequence[BCPatch]):
+    """Boundary patches as an (n, 7) int32 table (block, face, lo[2], hi[2],
+    kind) and an (n, 5) float64 table of primitive states."""
+    a = np.zeros((len(bcs), BC_FIELDS), dtype=np.int32)
+    st = np.zeros((len(bcs), 5), dtype=np.float64)
+    for n, b in enumerate(bcs):
+        a[n] = [b.block, b.face, b.lo[0], b.lo[1], b.hi[0], b.hi[1], b.kind]
+        st[n] = b.state
+    return a, st

@@ -7,6 +7,13 @@ are not available, so these synthetic problems stand in for them:
 * ``mms_3d``             3D single curvilinear block with a manufactured solution.
 * ``multiblock_batched`` 64 uneven Cartesian blocks with seeded connections.
 * ``large_periodic``     one large periodic Cartesian block, Mach 2 + density bumps.
+* ``inlet_2d``           2D supersonic compression-ramp channel: inflow, outflow, walls
+                         (stands in for the paper's 2D inlet; inflow of its table).
+* ``ellipse_ogrid``      O-grid around a 12 % ellipse, wall + farfield + periodic cut,
+                         2D or extruded 3D (stands in for the airfoil / wing cases;
+                         free stream of the airfoil table).
+* ``channel_uniform``    uniform flow in a perturbed box with every boundary kind
+                         (free-stream preservation).
 
 Every array is produced from fixed constants or from ``numpy.random.default_rng``
 with the stated seed.
@@ -18,9 +25,10 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-from .core import (GAMMA, GHOST, BlockDesc, Connection, Problem, default_params,
-                   ghosted_shape, nominal_dt, pack_state, periodic_connections,
-                   prim_to_cons, unpack_state)
+from .core import (GAMMA, GHOST, BC_EXTRAPOLATE, BC_FARFIELD, BC_SLIP_WALL,
+                   BC_SUPERSONIC_INFLOW, BCPatch, BlockDesc, Connection, Problem,
+                   default_params, ghosted_shape, nominal_dt, pack_state,
+                   periodic_connections, prim_to_cons, unpack_state)
 
 # ---------------------------------------------------------------------------
 # geometry helpers (node coordinates and sampling points; no metrics)
@@ -38,7 +46,8 @@ def perturbed_nodes(ni: int, nj: int, nk: int, amp: float = 0.1, lo_pad: int = 0
       x = X + amp*hx*sin(2 pi Y) sin(2 pi Z)
       y = Y + amp*hy*sin(2 pi Z) sin(2 pi X)
       z = Z + amp*hz*sin(2 pi X) sin(2 pi Y)
-    Boundary faces of [0,1]^3 stay planar."""
+    A node on a boundary face of [0,1]^3 moves only along that face's normal
+    (the boundary faces are wavy, not planar)."""
     hx, hy, hz = 1.0 / ni, 1.0 / nj, 1.0 / nk
     X = _node_grid(-lo_pad, ni + hi_pad, hx)
     Y = _node_grid(-lo_pad, nj + hi_pad, hy)
@@ -406,3 +415,149 @@ def rotated_split_problem(pb: Problem, m: int) -> Problem:
         srcs = [sa, sb]
     return Problem([A, B], conns, pb.dim, pack_state([A, B], [qa, qb]), srcs, pb.dt,
                    dict(pb.params), pb.name + "_rot")
+
+
+# ---------------------------------------------------------------------------
+# physical-boundary workloads (Section 8 cases, synthetic geometry)
+# ---------------------------------------------------------------------------
+
+R_AIR = 287.0   # J/(kg K), the gas constant used to turn the tables' (p, T) into rho
+
+
+def table_state(mach: float, p: float, T: float, alpha_deg: float = 0.0, gamma: float = GAMMA):
+    """Primitive (rho, u, v, w, p) of a free stream given by Mach number,
+    static pressure [Pa], temperature [K] and angle of attack (in the x-y
+    plane), with rho = p / (R T)."""
+    rho = p / (R_AIR * T)
+    c = math.sqrt(gamma * p / rho)
+    a = math.radians(alpha_deg)
+    return np.array([rho, mach * c * math.cos(a), mach * c * math.sin(a), 0.0, p])
+
+
+INLET_INFLOW = dict(mach=4.0, p=12270.0, T=217.0)            # Section 8.1 table
+AIRFOIL_FARFIELD = dict(mach=0.25, p=84307.0, T=300.0, alpha_deg=5.0)   # Section 8.2 table
+WING_FARFIELD = dict(mach=0.8395, p=315979.763, T=255.556, alpha_deg=3.06)   # Section 8.3 table
+
+
+def _perturbed_state(prim0: np.ndarray, shape, perturb: float, seed: Optional[int]) -> np.ndarray:
+    """prim0 broadcast over ``shape`` with rho and p scaled by 1 + perturb*N(0,1)
+    and the velocity shifted by perturb*|u0|*N(0,1) per component (seeded)."""
+    prim = prim0.reshape(5, 1, 1, 1) * np.ones((1,) + tuple(shape))
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        speed = max(float(np.linalg.norm(prim0[1:4])), 1e-12)
+        prim[0] *= 1.0 + perturb * rng.standard_normal(shape)
+        prim[4] *= 1.0 + perturb * rng.standard_normal(shape)
+        for c in (1, 2, 3):
+            prim[c] += perturb * speed * rng.standard_normal(shape)
+    return prim
+
+
+def _min_spacing(nodes: np.ndarray, dim: int):
+    """Smallest node-to-node distance along each index direction."""
+    d = []
+    for ax in (2, 1, 0)[:dim]:
+        diff = np.diff(nodes, axis=ax)
+        d.append(float(np.sqrt((diff ** 2).sum(-1)).min()))
+    while len(d) < 3:
+        d.append(1.0)
+    return d
+
+
+def inlet_2d(ni: int = 416, nj: int = 128, ramp_deg: float = 10.0, perturb: float = 0.0,
+             seed: Optional[int] = None, cfl: float = 0.5, **param_over) -> Problem:
+    """2D supersonic channel x in [0, 3] between a lower wall that turns up by
+    ``ramp_deg`` at x = 1 and a flat upper wall at y = 1 (nodes clustered
+    towards the lower wall, eta = (e^{2s} - 1)/(e^2 - 1)).  Inflow (i = 0) is the
+    paper's inlet table (Mach 4, 12270 Pa, 217 K), outflow (i = ni) is
+    extrapolated, both walls are slip walls.  The initial state is the inflow
+    everywhere (optionally perturbed, seeded)."""
+    x = 3.0 * np.arange(ni + 1) / ni
+    yl = np.where(x > 1.0, (x - 1.0) * math.tan(math.radians(ramp_deg)), 0.0)
+    s = np.arange(nj + 1) / nj
+    eta = (np.exp(2.0 * s) - 1.0) / (math.exp(2.0) - 1.0)
+    nodes = np.zeros((2, nj + 1, ni + 1, 3))
+    for kk in range(2):
+        nodes[kk, :, :, 0] = x[None, :]
+        nodes[kk, :, :, 1] = yl[None, :] + (1.0 - yl[None, :]) * eta[:, None]
+        nodes[kk, :, :, 2] = float(kk)
+    b = BlockDesc(ni, nj, 1, nodes)
+    V0 = table_state(**INLET_INFLOW)
+    prim = _perturbed_state(V0, ghosted_shape(b)[1:], perturb, seed)
+    q = prim_to_cons(prim)
+    dt = nominal_dt([prim], [_min_spacing(nodes, 2)], cfl, 2)
+    bcs = [BCPatch(0, 0, (0, 0), (nj, 1), BC_SUPERSONIC_INFLOW, tuple(V0)),
+           BCPatch(0, 1, (0, 0), (nj, 1), BC_EXTRAPOLATE),
+           BCPatch(0, 2, (0, 0), (ni, 1), BC_SLIP_WALL),
+           BCPatch(0, 3, (0, 0), (ni, 1), BC_SLIP_WALL)]
+    return Problem([b], [], 2, pack_state([b], [q]), None, dt, default_params(**param_over),
+                   "inlet_2d_%dx%d" % (ni, nj), bcs)
+
+
+def ellipse_ogrid(ni: int = 512, nj: int = 128, nk: int = 1, thickness: float = 0.12,
+                  radius: float = 20.0, span: float = 1.0, beta: float = 6.0, perturb: float = 0.0,
+                  seed: Optional[int] = None, cfl: float = 0.5, **param_over) -> Problem:
+    """O-grid around an ellipse of chord 1 and the given thickness ratio,
+    blended to a circle of ``radius``: node (i, j) at angle
+    theta_i = -2 pi i / ni (clockwise, so that (i, j, k) is right-handed) is
+    (1 - w) (cos t / 2, thickness sin t / 2) + w radius (cos t, sin t) with
+    w = (e^{beta s} - 1)/(e^beta - 1), s = j / nj.  The i = 0 / i = ni cut is a
+    periodic self-connection, j = 0 is a slip wall, j = nj a farfield.  nk = 1
+    is the 2D case, with the paper's airfoil table (Mach 0.25, 84307 Pa, 300 K,
+    5 degrees); nk > 1 extrudes it over ``span`` in z with slip walls on both k
+    faces (symmetry planes) and takes the wing table (Mach 0.8395,
+    315979.763 Pa, 255.556 K, 3.06 degrees)."""
+    dim = 2 if nk == 1 else 3
+    th = -2.0 * math.pi * np.arange(ni + 1) / ni
+    s = np.arange(nj + 1) / nj
+    w = (np.exp(beta * s) - 1.0) / (math.exp(beta) - 1.0)
+    xe, ye = 0.5 * np.cos(th), 0.5 * thickness * np.sin(th)
+    xo, yo = radius * np.cos(th), radius * np.sin(th)
+    X = (1.0 - w[:, None]) * xe[None, :] + w[:, None] * xo[None, :]
+    Y = (1.0 - w[:, None]) * ye[None, :] + w[:, None] * yo[None, :]
+    X[:, ni] = X[:, 0]
+    Y[:, ni] = Y[:, 0]
+    zs = np.arange(nk + 1) * (span / nk if dim == 3 else 1.0)
+    nodes = np.zeros((nk + 1, nj + 1, ni + 1, 3))
+    nodes[..., 0] = X[None]
+    nodes[..., 1] = Y[None]
+    nodes[..., 2] = zs[:, None, None]
+    b = BlockDesc(ni, nj, nk, nodes)
+    V0 = table_state(**(AIRFOIL_FARFIELD if dim == 2 else WING_FARFIELD))
+    prim = _perturbed_state(V0, ghosted_shape(b)[1:], perturb, seed)
+    q = prim_to_cons(prim)
+    dt = nominal_dt([prim], [_min_spacing(nodes, dim)], cfl, dim)
+    conns = periodic_connections(0, b, axes=(0,))
+    bcs = [BCPatch(0, 2, (0, 0), (ni, nk), BC_SLIP_WALL),
+           BCPatch(0, 3, (0, 0), (ni, nk), BC_FARFIELD, tuple(V0))]
+    if dim == 3:
+        bcs += [BCPatch(0, 4, (0, 0), (ni, nj), BC_SLIP_WALL),
+                BCPatch(0, 5, (0, 0), (ni, nj), BC_SLIP_WALL)]
+    return Problem([b], conns, dim, pack_state([b], [q]), None, dt, default_params(**param_over),
+                   "ellipse_%dx%dx%d" % (ni, nj, nk), bcs)
+
+
+def channel_uniform(n: int = 12, supersonic: bool = True, amp: float = 0.1, **param_over) -> Problem:
+    """Uniform flow along x through the unit box with perturbed interior nodes
+    (every boundary node stays on its planar face).  Supersonic (Mach 2): inflow at i = 0, extrapolated outflow at
+    i = n, slip walls on the four other faces.  Subsonic (Mach 0.5): farfield
+    on every face.  Either way the exact discrete residual is zero."""
+    # x_d = X_d + amp h sin(2 pi X) sin(2 pi Y) sin(2 pi Z): every boundary node stays put
+    X = np.arange(n + 1) / n
+    Zg, Yg, Xg = np.meshgrid(X, X, X, indexing="ij")
+    bump = amp / n * np.sin(2 * math.pi * Xg) * np.sin(2 * math.pi * Yg) * np.sin(2 * math.pi * Zg)
+    nodes = np.stack([Xg + bump, Yg - bump, Zg + bump], axis=-1)
+    b = BlockDesc(n, n, n, nodes)
+    mach = 2.0 if supersonic else 0.5
+    V0 = np.array([1.2, mach * math.sqrt(GAMMA * 0.9 / 1.2), 0.0, 0.0, 0.9])
+    prim = V0.reshape(5, 1, 1, 1) * np.ones((1,) + ghosted_shape(b)[1:])
+    q = prim_to_cons(prim)
+    dt = nominal_dt([prim], [(1.0 / n,) * 3], 0.5, 3)
+    if supersonic:
+        bcs = [BCPatch(0, 0, (0, 0), (n, n), BC_SUPERSONIC_INFLOW, tuple(V0)),
+               BCPatch(0, 1, (0, 0), (n, n), BC_EXTRAPOLATE)]
+        bcs += [BCPatch(0, f, (0, 0), (n, n), BC_SLIP_WALL) for f in (2, 3, 4, 5)]
+    else:
+        bcs = [BCPatch(0, f, (0, 0), (n, n), BC_FARFIELD, tuple(V0)) for f in range(6)]
+    return Problem([b], [], 3, pack_state([b], [q]), None, dt, default_params(**param_over),
+                   "channel_%s_%d" % ("sup" if supersonic else "sub", n), bcs)

@@ -66,6 +66,11 @@ def lib():
         L.oracle_limited.restype = ctypes.c_double
         L.oracle_cons_to_prim.argtypes = [ctypes.c_double, _dp, _dp]
         L.oracle_face_opcount.argtypes = [_dp, _dp, _dp, _lp]
+        L.oracle_residual_bc.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 6 + [
+            ctypes.c_char_p, _dp]
+        L.oracle_bc_fill.argtypes = [_dp] + [ctypes.c_int] * 3 + [_dp] * 3 + [ctypes.c_int] * 6 + [_dp, _dp]
+        L.oracle_farfield_state.argtypes = [ctypes.c_double] + [_dp] * 4
+        L.oracle_wall_flux.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -140,6 +145,23 @@ def cons_to_prim(q, gamma: float = 1.4) -> np.ndarray:
     return out
 
 
+def farfield_state(Vi, Vinf, n_out, gamma: float = 1.4) -> np.ndarray:
+    """Characteristic farfield boundary state (primitive) from the interior
+    state, the free stream and the outward unit normal."""
+    out = np.zeros(5)
+    lib().oracle_farfield_state(gamma, _p(np.ascontiguousarray(Vi, dtype=np.float64)),
+                                _p(np.ascontiguousarray(Vinf, dtype=np.float64)),
+                                _p(np.ascontiguousarray(n_out, dtype=np.float64)), _p(out))
+    return out
+
+
+def wall_flux(p1: float, p2: float, S) -> np.ndarray:
+    """Overwritten slip-wall face flux from the two nearest interior pressures."""
+    out = np.zeros(5)
+    lib().oracle_wall_flux(float(p1), float(p2), _p(np.ascontiguousarray(S, dtype=np.float64)), _p(out))
+    return out
+
+
 def face_opcount(params: dict) -> dict:
     """Operation counts of one face (5 reconstructed components + Roe flux)."""
     rng = np.random.default_rng(0)
@@ -191,6 +213,23 @@ class Oracle:
         self.src = problem.source
         self.ncell = [b.ni * b.nj * b.nk for b in self.blocks]
         self.roffs = np.concatenate([[0], np.cumsum([5 * n for n in self.ncell])]).astype(np.int64)
+        # physical boundaries: patches and, per block, the six face maps of
+        # overwritten-flux codes (None when the block has no such face)
+        self.bcs = list(getattr(problem, "bcs", []) or [])
+        self.codes = []
+        for n, b in enumerate(self.blocks):
+            sizes = [b.nj * b.nk, b.nj * b.nk, b.ni * b.nk, b.ni * b.nk, b.ni * b.nj, b.ni * b.nj]
+            maps = [np.zeros(sz, dtype=np.int8) for sz in sizes]
+            any_code = False
+            for pt in self.bcs:
+                if pt.block != n or pt.kind not in (cases.BC_SLIP_WALL, cases.BC_FARFIELD):
+                    continue
+                ext0 = b.nj if pt.face < 2 else b.ni
+                m = maps[pt.face]
+                for t1 in range(pt.lo[1], pt.hi[1]):
+                    m[t1 * ext0 + pt.lo[0]:t1 * ext0 + pt.hi[0]] = pt.kind
+                any_code = True
+            self.codes.append(np.ascontiguousarray(np.concatenate(maps)) if any_code else None)
 
     # -- pieces ---------------------------------------------------------------
     def block_view(self, q: np.ndarray, n: int) -> np.ndarray:
@@ -204,21 +243,47 @@ class Oracle:
             lib().oracle_exchange(len(self.conns), _p(self.conns), _p(self.dims), _p(self.offs), _p(q))
         return q
 
+    def apply_bcs(self, q: np.ndarray) -> np.ndarray:
+        """Physical-boundary ghost fill of every patch, in place (Section 2;
+        Section 7.2, V2/V3)."""
+        for pt in self.bcs:
+            b = self.blocks[pt.block]
+            Sxi, Seta, Szeta, _ = self.metrics[pt.block]
+            qb = self.block_view(q, pt.block)
+            assert qb.flags["C_CONTIGUOUS"]
+            st = np.ascontiguousarray(pt.state, dtype=np.float64)
+            lib().oracle_bc_fill(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), int(pt.face),
+                                 int(pt.lo[0]), int(pt.lo[1]), int(pt.hi[0]), int(pt.hi[1]), int(pt.kind),
+                                 _p(st), qb.ctypes.data_as(_dp))
+        return q
+
+    def fill_ghosts(self, q: np.ndarray) -> np.ndarray:
+        """Connected-boundary exchange, then the physical boundaries."""
+        return self.apply_bcs(self.exchange(q))
+
     def residual(self, q: np.ndarray) -> np.ndarray:
-        """Residual of every block of the packed state ``q`` as it stands."""
+        """Residual of every block of the packed state ``q`` as it stands
+        (wall and farfield faces overwritten, Section 7.2 V7)."""
         R = np.zeros(int(self.roffs[-1]))
         for n, b in enumerate(self.blocks):
             Sxi, Seta, Szeta, vol = self.metrics[n]
             qb = np.ascontiguousarray(self.block_view(q, n))
             src = None if self.src is None else np.ascontiguousarray(self.src[n], dtype=np.float64)
             Rb = np.zeros(5 * self.ncell[n])
-            lib().oracle_residual(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), _p(vol),
-                                  _p(qb), _p(src), _p(Rb))
+            if self.codes[n] is not None:
+                lib().oracle_residual_bc(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), _p(vol),
+                                         _p(qb), _p(src), self.codes[n].ctypes.data_as(ctypes.c_char_p), _p(Rb))
+            else:
+                lib().oracle_residual(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), _p(vol),
+                                      _p(qb), _p(src), _p(Rb))
             R[self.roffs[n]:self.roffs[n + 1]] = Rb
         return R
 
     def residual_jvp(self, q: np.ndarray, dq: np.ndarray):
-        """(R, dR) with dR = dR/dq . dq by dual numbers (ghosts as they stand)."""
+        """(R, dR) with dR = dR/dq . dq by dual numbers (ghosts as they stand;
+        no overwritten boundary faces)."""
+        if any(c is not None for c in self.codes):
+            raise NotImplementedError("residual_jvp: wall/farfield face overwrites are not linearised")
         R = np.zeros(int(self.roffs[-1]))
         dR = np.zeros_like(R)
         for n, b in enumerate(self.blocks):
@@ -248,8 +313,9 @@ class Oracle:
 
     # -- Runge-Kutta ------------------------------------------------------------
     def rk_stage(self, q0: np.ndarray, qin: np.ndarray, m: int, dt: float) -> np.ndarray:
-        """Stage m (1..M): exchange ghosts of Q^(m-1), R(Q^(m-1)), update."""
-        qin = self.exchange(qin.copy())
+        """Stage m (1..M): fill the ghosts of Q^(m-1) (connections, then
+        physical boundaries), R(Q^(m-1)), update."""
+        qin = self.fill_ghosts(qin.copy())
         R = self.residual(qin)
         return self.update(q0, R, self.alpha[m - 1] * dt)
 

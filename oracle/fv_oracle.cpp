@@ -20,7 +20,11 @@
 //     Eq. (flux), with limiter values Psi^{+/-};
 //   * Roe's approximate Riemann flux: Section 2 (flux-difference splitting);
 //   * ghost cells for connected boundaries: Section 2 and Section 4;
-//   * explicit M-step Runge-Kutta time marching: Section 2.
+//   * explicit M-step Runge-Kutta time marching: Section 2;
+//   * physical boundaries enforced through ghost cells (slip wall, supersonic
+//     inflow, extrapolated outflow, farfield): Section 2 and Section 7.2
+//     (V2/V3); wall and farfield face fluxes overwritten after the boundary
+//     enforcement: Section 7.2 (V7).
 // Points the paper leaves open are fixed as follows:
 //   limiter: van Leer Psi(r) = (r+|r|)/(1+|r|) with r = a/b, b guarded to
 //     copysign(max(|b|,1e-30), b) (sign(0)=+1); van Albada in the smooth
@@ -31,7 +35,18 @@
 //   metrics: face vector S = 1/2 (x_c - x_a) x (x_d - x_b) for the face's
 //     nodes a,b,c,d in order; volume = 1/3 sum_faces xbar_f . S_f (outward);
 //   residual summation order: xi pair, eta pair, zeta pair, then the source;
-//   RK: Q^(m) = Q^(0) - alpha_m dt / Omega R(Q^(m-1)).
+//   RK: Q^(m) = Q^(0) - alpha_m dt / Omega R(Q^(m-1));
+//   boundaries: ghosts at depth d mirror interior depth d across a slip wall
+//     (normal momentum reflected with the boundary face's unit normal); an
+//     extrapolated outflow copies the first interior cell into both layers; a
+//     supersonic inflow holds the prescribed state; a farfield holds the
+//     characteristic state built from the first interior cell and the free
+//     stream with the 1D Riemann invariants V_n +- 2c/(gamma-1) along the
+//     outward normal (entropy and tangential velocity from the upwind side;
+//     all from the interior/free stream when |V_n|/c >= 1 inside);
+//   overwritten fluxes: a slip-wall face carries only pressure, p_w S with
+//     p_w = (3 p_1 - p_2)/2 from the two nearest interior cells; a farfield
+//     face carries the physical flux F(V_b).S of the ghost state.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -350,9 +365,36 @@ inline void cross_half(const double* xa, const double* xb, const double* xc, con
   S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
 }
 
+// Physical boundary kinds (codes shared with the boundary tables).
+enum { BC_FIXED = 0, BC_SUPERSONIC_INFLOW = 1, BC_EXTRAPOLATE = 2, BC_SLIP_WALL = 3, BC_FARFIELD = 4 };
+
+// Slip-wall face flux (Section 7.2, V7): pressure only, p_w S.
+template <class T>
+void wall_flux(T p1, T p2, const double S[3], T out[5]) {
+  T pw = T(1.5) * p1 - T(0.5) * p2;
+  out[0] = T(0.0);
+  out[1] = pw * T(S[0]);
+  out[2] = pw * T(S[1]);
+  out[3] = pw * T(S[2]);
+  out[4] = T(0.0);
+}
+
+// Farfield face flux (Section 7.2, V7): F(V_b).S of the boundary state.
+template <class T>
+void farfield_flux(const Params& P, const T Vb[5], const double S[3], T out[5]) {
+  const double a = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  normal_flux(P, Vb, S[0] / a, S[1] / a, S[2] / a, out);
+  for (int n = 0; n < 5; ++n) out[n] = out[n] * T(a);
+}
+
+// bcode: the six face maps of the block (imin, imax, jmin, jmax, kmin, kmax;
+// each indexed by the two tangential cell indices in (i,j,k) order, first
+// fastest) or nullptr; a slip-wall or farfield code replaces that boundary
+// face's flux.
 template <class T>
 void residual_block(const Params& P, const Blk& B, const double* Sxi, const double* Seta,
-                    const double* Szeta, const double* vol, const T* q, const double* src, T* R) {
+                    const double* Szeta, const double* vol, const T* q, const double* src, T* R,
+                    const signed char* const* bcode = nullptr) {
   const int ni = B.ni, nj = B.nj, nk = B.nk;
   // primitives of every cell, ghosts included
   std::vector<T> V(5 * B.plane);
@@ -369,15 +411,38 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
   const long n_xi = (long)nk * nj * nfx, n_eta = (long)nk * nfy * ni, n_zeta = (long)(nk + 1) * nj * ni;
   std::vector<T> Fx(5 * n_xi), Fy(5 * n_eta), Fz(P.dim == 3 ? 5 * n_zeta : 0);
 
-  // face fluxes in one direction: face f between cells f-1 and f along the axis
-  auto face = [&](long cm2, long stride, const double* Sarr, long nfaces, long fidx, T* F) {
-    T VL[5], VR[5], out[5];
-    for (int n = 0; n < 5; ++n) {
-      const T* Vn = &V[n * B.plane];
-      muscl(P, Vn[cm2], Vn[cm2 + stride], Vn[cm2 + 2 * stride], Vn[cm2 + 3 * stride], VL[n], VR[n]);
-    }
+  // code of the boundary face at tangential position (t0, t1) of block face bf
+  auto code_at = [&](int bf, int t0, int t1) -> int {
+    if (!bcode || !bcode[bf]) return BC_FIXED;
+    const int ext0 = bf < 2 ? nj : ni;
+    return bcode[bf][(long)t1 * ext0 + t0];
+  };
+
+  // face fluxes in one direction: face f between cells f-1 and f along the
+  // axis; stencil cells cm2 .. cm2 + 3 stride.  side: 0 on the block's min
+  // face (interior cells at cm2 + 2, 3 strides, first ghost at cm2 + stride),
+  // 1 on its max face (interior at cm2 + stride, cm2; ghost at cm2 + 2 stride)
+  auto face = [&](long cm2, long stride, const double* Sarr, long nfaces, long fidx, T* F, int code,
+                  int side) {
+    T out[5];
     double S[3] = {Sarr[fidx], Sarr[nfaces + fidx], Sarr[2 * nfaces + fidx]};
-    face_flux_fn(P, VL, VR, S, out);
+    if (code == BC_SLIP_WALL) {
+      const long c1 = side == 0 ? cm2 + 2 * stride : cm2 + stride;
+      const long c2 = side == 0 ? cm2 + 3 * stride : cm2;
+      wall_flux(V[4 * B.plane + c1], V[4 * B.plane + c2], S, out);
+    } else if (code == BC_FARFIELD) {
+      const long g1 = side == 0 ? cm2 + stride : cm2 + 2 * stride;
+      T Vb[5];
+      for (int n = 0; n < 5; ++n) Vb[n] = V[n * B.plane + g1];
+      farfield_flux(P, Vb, S, out);
+    } else {
+      T VL[5], VR[5];
+      for (int n = 0; n < 5; ++n) {
+        const T* Vn = &V[n * B.plane];
+        muscl(P, Vn[cm2], Vn[cm2 + stride], Vn[cm2 + 2 * stride], Vn[cm2 + 3 * stride], VL[n], VR[n]);
+      }
+      face_flux_fn(P, VL, VR, S, out);
+    }
     for (int n = 0; n < 5; ++n) F[n * nfaces + fidx] = out[n];
   };
 
@@ -386,14 +451,16 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
     for (int j = 0; j < nj; ++j)
       for (int i = 0; i <= ni; ++i) {
         long f = ((long)k * nj + j) * nfx + i;
-        face(B.at(i - 2, j, k), B.sx, Sxi, n_xi, f, Fx.data());
+        int code = i == 0 ? code_at(0, j, k) : (i == ni ? code_at(1, j, k) : BC_FIXED);
+        face(B.at(i - 2, j, k), B.sx, Sxi, n_xi, f, Fx.data(), code, i == 0 ? 0 : 1);
       }
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nk; ++k)
     for (int j = 0; j <= nj; ++j)
       for (int i = 0; i < ni; ++i) {
         long f = ((long)k * nfy + j) * ni + i;
-        face(B.at(i, j - 2, k), B.sy, Seta, n_eta, f, Fy.data());
+        int code = j == 0 ? code_at(2, i, k) : (j == nj ? code_at(3, i, k) : BC_FIXED);
+        face(B.at(i, j - 2, k), B.sy, Seta, n_eta, f, Fy.data(), code, j == 0 ? 0 : 1);
       }
   if (P.dim == 3) {
 #pragma omp parallel for schedule(static)
@@ -401,7 +468,8 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
       for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
           long f = ((long)k * nj + j) * ni + i;
-          face(B.at(i, j, k - 2), B.sz, Szeta, n_zeta, f, Fz.data());
+          int code = k == 0 ? code_at(4, i, j) : (k == nk ? code_at(5, i, j) : BC_FIXED);
+          face(B.at(i, j, k - 2), B.sz, Szeta, n_zeta, f, Fz.data(), code, k == 0 ? 0 : 1);
         }
   }
   // Eq. (governing), discretely: R = sum over faces of F^ |S| (outward) - S Omega
@@ -454,6 +522,116 @@ void exchange_one(const int* dims, const long* offs, T* q, const int* c) {
         long si = S.at(sc[0], sc[1], sc[2]);
         for (int v = 0; v < 5; ++v) qd[v * D.plane + di] = qs[v * S.plane + si];
       }
+}
+
+// ---------------------------------------------------------------------------
+// Physical boundaries through ghost cells (Section 2; Section 7.2, V2/V3)
+// ---------------------------------------------------------------------------
+
+void prim_to_cons_d(const double V[5], double gamma, double q[5]) {
+  q[0] = V[0];
+  q[1] = V[0] * V[1];
+  q[2] = V[0] * V[2];
+  q[3] = V[0] * V[3];
+  q[4] = V[4] / (gamma - 1.0) + 0.5 * V[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+}
+
+// Farfield boundary state from the interior state Vi, the free stream Vinf
+// and the outward unit normal n: 1D Riemann invariants along n.
+void farfield_state(double gamma, const double Vi[5], const double Vinf[5], const double n[3], double Vb[5]) {
+  const double gm1 = gamma - 1.0;
+  const double ci = std::sqrt(gamma * Vi[4] / Vi[0]);
+  const double cinf = std::sqrt(gamma * Vinf[4] / Vinf[0]);
+  const double vni = Vi[1] * n[0] + Vi[2] * n[1] + Vi[3] * n[2];
+  const double vninf = Vinf[1] * n[0] + Vinf[2] * n[1] + Vinf[3] * n[2];
+  if (vni >= ci) {          // supersonic outflow: everything from inside
+    for (int m = 0; m < 5; ++m) Vb[m] = Vi[m];
+    return;
+  }
+  if (vni <= -ci) {         // supersonic inflow: everything from the free stream
+    for (int m = 0; m < 5; ++m) Vb[m] = Vinf[m];
+    return;
+  }
+  const double rp = vni + 2.0 * ci / gm1;       // outgoing invariant (interior)
+  const double rm = vninf - 2.0 * cinf / gm1;   // incoming invariant (free stream)
+  const double vnb = 0.5 * (rp + rm);
+  const double cb = 0.25 * gm1 * (rp - rm);
+  const double* ref = vnb >= 0.0 ? Vi : Vinf;   // upwind side
+  const double s = ref[4] / std::pow(ref[0], gamma);
+  const double rhob = std::pow(cb * cb / (gamma * s), 1.0 / gm1);
+  const double vnref = ref[1] * n[0] + ref[2] * n[1] + ref[3] * n[2];
+  Vb[0] = rhob;
+  for (int m = 0; m < 3; ++m) Vb[1 + m] = ref[1 + m] + (vnb - vnref) * n[m];
+  Vb[4] = rhob * cb * cb / gamma;
+}
+
+// One boundary patch of a block: ghosts of face bf (0..5) over tangential
+// cells [lo0,hi0) x [lo1,hi1) (tangential axes in (i,j,k) order).
+// Sface: the block's face-vector array of the face's direction
+// ([3][..] as the metrics store it).  state: primitive (rho,u,v,w,p).
+void bc_fill_patch(const Params& P, const Blk& B, const double* Sface, int bf, int lo0, int lo1, int hi0,
+                   int hi1, int kind, const double* state, double* q) {
+  if (kind == BC_FIXED) return;
+  const int ax = bf / 2, side = bf % 2;
+  const int ext[3] = {B.ni, B.nj, B.nk};
+  int tan[2], m = 0;
+  for (int x = 0; x < 3; ++x)
+    if (x != ax) tan[m++] = x;
+  // face-vector array extents: one more face along the face's own axis
+  int fe[3] = {B.ni, B.nj, B.nk};
+  fe[ax] += 1;
+  const long nfaces = (long)fe[0] * fe[1] * fe[2];
+  double qs[5];
+  if (kind == BC_SUPERSONIC_INFLOW) prim_to_cons_d(state, P.gamma, qs);
+  for (int b = lo1; b < hi1; ++b)
+    for (int a = lo0; a < hi0; ++a) {
+      int c[3];
+      c[tan[0]] = a;
+      c[tan[1]] = b;
+      // boundary face and its unit normal
+      int fc[3] = {c[0], c[1], c[2]};
+      fc[ax] = side == 0 ? 0 : ext[ax];
+      const long fi = ((long)fc[2] * fe[1] + fc[1]) * fe[0] + fc[0];
+      double S[3] = {Sface[fi], Sface[nfaces + fi], Sface[2 * nfaces + fi]};
+      const double area = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      double nrm[3] = {S[0] / area, S[1] / area, S[2] / area};
+      // first interior cell
+      int c1[3] = {c[0], c[1], c[2]};
+      c1[ax] = side == 0 ? 0 : ext[ax] - 1;
+      const long i1 = B.at(c1[0], c1[1], c1[2]);
+      double qb[5];
+      if (kind == BC_FARFIELD) {
+        double qi[5], Vi[5], Vb[5];
+        for (int v = 0; v < 5; ++v) qi[v] = q[v * B.plane + i1];
+        cons_to_prim(qi, P.gamma, Vi);
+        const double sgn = side == 0 ? -1.0 : 1.0;   // S points +axis; outward on the max face
+        double nout[3] = {sgn * nrm[0], sgn * nrm[1], sgn * nrm[2]};
+        farfield_state(P.gamma, Vi, state, nout, Vb);
+        prim_to_cons_d(Vb, P.gamma, qb);
+      }
+      for (int d = 1; d <= G; ++d) {
+        int cg[3] = {c[0], c[1], c[2]};
+        cg[ax] = side == 0 ? -d : ext[ax] - 1 + d;
+        const long gi = B.at(cg[0], cg[1], cg[2]);
+        if (kind == BC_SUPERSONIC_INFLOW) {
+          for (int v = 0; v < 5; ++v) q[v * B.plane + gi] = qs[v];
+        } else if (kind == BC_EXTRAPOLATE) {
+          for (int v = 0; v < 5; ++v) q[v * B.plane + gi] = q[v * B.plane + i1];
+        } else if (kind == BC_FARFIELD) {
+          for (int v = 0; v < 5; ++v) q[v * B.plane + gi] = qb[v];
+        } else if (kind == BC_SLIP_WALL) {
+          // mirror of the interior cell at the same depth, normal momentum reflected
+          int cm[3] = {c[0], c[1], c[2]};
+          cm[ax] = side == 0 ? d - 1 : ext[ax] - d;
+          const long mi = B.at(cm[0], cm[1], cm[2]);
+          double mom[3] = {q[1 * B.plane + mi], q[2 * B.plane + mi], q[3 * B.plane + mi]};
+          const double mn = mom[0] * nrm[0] + mom[1] * nrm[1] + mom[2] * nrm[2];
+          q[gi] = q[mi];
+          for (int x = 0; x < 3; ++x) q[(1 + x) * B.plane + gi] = mom[x] - 2.0 * mn * nrm[x];
+          q[4 * B.plane + gi] = q[4 * B.plane + mi];
+        }
+      }
+    }
 }
 
 }  // namespace
@@ -557,6 +735,37 @@ void oracle_residual(const double* params, int ni, int nj, int nk, const double*
   Blk B(ni, nj, nk);
   residual_block<double>(P, B, Sxi, Seta, Szeta, vol, q, src, R);
 }
+
+// Residual with overwritten boundary-face fluxes: codes holds the six face
+// maps of the block concatenated in face order (sizes nj*nk, nj*nk, ni*nk,
+// ni*nk, ni*nj, ni*nj; the first tangential index fastest).
+void oracle_residual_bc(const double* params, int ni, int nj, int nk, const double* Sxi,
+                        const double* Seta, const double* Szeta, const double* vol,
+                        const double* q, const double* src, const signed char* codes, double* R) {
+  Params P = unpack(params);
+  Blk B(ni, nj, nk);
+  const signed char* maps[6];
+  const long sz[6] = {(long)nj * nk, (long)nj * nk, (long)ni * nk, (long)ni * nk, (long)ni * nj, (long)ni * nj};
+  long o = 0;
+  for (int f = 0; f < 6; ++f) { maps[f] = codes ? codes + o : nullptr; o += sz[f]; }
+  residual_block<double>(P, B, Sxi, Seta, Szeta, vol, q, src, R, codes ? maps : nullptr);
+}
+
+// Ghost fill of one physical boundary patch of one block (in place).
+void oracle_bc_fill(const double* params, int ni, int nj, int nk, const double* Sxi, const double* Seta,
+                    const double* Szeta, int face, int lo0, int lo1, int hi0, int hi1, int kind,
+                    const double* state, double* q) {
+  Params P = unpack(params);
+  Blk B(ni, nj, nk);
+  const double* Sface = face / 2 == 0 ? Sxi : (face / 2 == 1 ? Seta : Szeta);
+  bc_fill_patch(P, B, Sface, face, lo0, lo1, hi0, hi1, kind, state, q);
+}
+
+// Pieces of the boundary treatment for the closed-form checks.
+void oracle_farfield_state(double gamma, const double* Vi, const double* Vinf, const double* n, double* Vb) {
+  farfield_state(gamma, Vi, Vinf, n, Vb);
+}
+void oracle_wall_flux(double p1, double p2, const double* S, double* out) { wall_flux<double>(p1, p2, S, out); }
 
 // Jacobian-vector product of the residual: dR = (dR/dq) dq (forward mode).
 void oracle_residual_jvp(const double* params, int ni, int nj, int nk, const double* Sxi,
