@@ -211,6 +211,39 @@ def test_closed_box_conservation_and_wall_forces():
     assert np.allclose(R[1:4], force, rtol=0, atol=1e-12 * scale)
 
 
+def test_farfield_face_flux_is_the_boundary_state_flux():
+    """Walls on five faces, a subsonic farfield on imax: the total mass and
+    energy residuals are the fluxes of the characteristic boundary states
+    (built here from each first interior cell with the pinned farfield
+    state) through the imax faces, whose outward vector is (h^2, 0, 0)."""
+    n = 6
+    b = cases.channel_uniform(n, True).blocks[0]
+    rng = np.random.default_rng(21)
+    shape = cases.ghosted_shape(b)[1:]
+    P = np.empty((5,) + shape)
+    P[0] = 1.0 + 0.1 * rng.random(shape)
+    P[1:4] = 0.2 * rng.standard_normal((3,) + shape)
+    P[4] = 1.0 + 0.1 * rng.random(shape)
+    Vf = np.array([1.1, 0.3, -0.1, 0.05, 0.9])
+    bcs = [cases.BCPatch(0, f, (0, 0), (n, n), cases.BC_SLIP_WALL) for f in (0, 2, 3, 4, 5)]
+    bcs.append(cases.BCPatch(0, 1, (0, 0), (n, n), cases.BC_FARFIELD, tuple(Vf)))
+    pb = cases.Problem([b], [], 3, cases.pack_state([b], [cases.prim_to_cons(P)]), None, 1e-3,
+                       default_params(), "ff", bcs)
+    o = oracle.Oracle(pb)
+    R = o.residual(o.fill_ghosts(pb.q.copy())).reshape(5, -1).sum(1)
+    g = cases.GHOST
+    a = (1.0 / n) ** 2
+    mass = energy = 0.0
+    for k in range(n):
+        for j in range(n):
+            Vb = oracle.farfield_state(P[:, g + k, g + j, g + n - 1], Vf, np.array([1.0, 0.0, 0.0]))
+            un = Vb[1] * a
+            mass += Vb[0] * un
+            energy += (G / (G - 1) * Vb[4] + 0.5 * Vb[0] * (Vb[1:4] ** 2).sum()) * un
+    assert R[0] == pytest.approx(mass, rel=1e-12, abs=1e-14)
+    assert R[4] == pytest.approx(energy, rel=1e-12, abs=1e-14)
+
+
 def test_inflow_and_outflow_ghost_wiring():
     pb = cases.inlet_2d(20, 8, perturb=0.05, seed=4)
     o = oracle.Oracle(pb)
