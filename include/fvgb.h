@@ -12,6 +12,10 @@
  *   - Roe's flux-difference splitting as the face flux, Section 2;
  *   - two ghost layers per block face; connected faces take their ghosts from
  *     the neighbouring block each sub-step, Section 2 and Section 4;
+ *   - physical boundaries enforced through the ghost cells (slip wall,
+ *     supersonic inflow, extrapolated outflow, farfield), Section 2 and
+ *     Section 7.2 (V2/V3), with the wall and farfield face fluxes overwritten
+ *     after the enforcement, Section 7.2 (V7);
  *   - explicit M-step Runge-Kutta time marching, Section 2.
  *
  * Conventions used by every call:
@@ -100,6 +104,45 @@ typedef struct {
   int transform[2];
 } fv_connection;
 
+/* Physical boundary kinds (Section 2 names slip walls, supersonic/subsonic
+ * inflow and outflow and farfield boundaries, enforced through ghost cells).
+ * Readings of what the paper does not spell out:
+ *   FIXED: ghosts keep the values of the state set by the caller.
+ *   SUPERSONIC_INFLOW: both ghost layers hold the prescribed state.
+ *   EXTRAPOLATE (supersonic outflow): both layers copy the first interior cell.
+ *   SLIP_WALL: ghost at depth d mirrors the interior cell at depth d, with the
+ *     momentum reflected about the boundary face's unit normal n:
+ *     m_g = m - 2 (m.n) n (density and total energy copied).  The wall face
+ *     flux is overwritten with pressure only, (0, p_w S, 0) with
+ *     p_w = (3 p_1 - p_2)/2 from the two nearest interior cells.
+ *   FARFIELD: both layers hold the characteristic state V_b built from the
+ *     first interior cell V_i and the free stream V_f along the outward unit
+ *     normal: supersonic (|V_n,i| >= c_i) takes everything from V_i (outflow)
+ *     or V_f (inflow); otherwise V_n,b = (R+ + R-)/2 and
+ *     c_b = (gamma-1)(R+ - R-)/4 with R+ = V_n,i + 2 c_i/(gamma-1),
+ *     R- = V_n,f - 2 c_f/(gamma-1), and the entropy p/rho^gamma and the
+ *     tangential velocity of the upwind side.  The farfield face flux is
+ *     overwritten with the physical flux F(V_b).S. */
+typedef enum {
+  FV_BC_FIXED = 0,
+  FV_BC_SUPERSONIC_INFLOW = 1,
+  FV_BC_EXTRAPOLATE = 2,
+  FV_BC_SLIP_WALL = 3,
+  FV_BC_FARFIELD = 4
+} fv_bc_kind;
+
+/* One physical boundary patch: face `face` (0..5) of block `block` over the
+ * tangential cells [lo[0], hi[0]) x [lo[1], hi[1]) (tangential axes in i, j, k
+ * order without the face normal, as for connections).  state: primitive
+ * (rho, u, v, w, p) of a supersonic inflow or of the farfield free stream
+ * (ignored by the other kinds). */
+typedef struct {
+  int block, face;
+  int lo[2], hi[2];
+  int kind;
+  double state[5];
+} fv_bc_patch;
+
 /* Method parameters.  Readings of points the paper leaves open:
  *   limiter: van Leer Psi(r) = (r+|r|)/(1+|r|); van Albada in the smooth
  *     product form Psi(a/b) b = b (a^2+ab)/(a^2+b^2+va_delta2); NONE: Psi = 1.
@@ -177,24 +220,40 @@ int fv_get_state(fv_handle h, int buffer, double* q, void* stream);
  * NULL removes the source. */
 int fv_set_source(fv_handle h, const double* s, void* stream);
 
-/* Connected-boundary ghost fill of state buffer `buffer`: for every
+/* Physical boundaries of the handle (replacing any earlier set; n = 0 clears
+ * them).  patches: HOST array of n fv_bc_patch, copied.  Validates block and
+ * face indices (faces 4, 5 only when dim = 3), patch ranges inside the face,
+ * the kind, a finite state with rho > 0 and p > 0 for SUPERSONIC_INFLOW and
+ * FARFIELD, and at least two interior cells along the normal of a SLIP_WALL
+ * face; FV_ERR_INVALID_ARG otherwise (the old set stays).  A CUDA or
+ * allocation failure after validation leaves no patches set.  Patches are filled
+ * in order after the connections, so a later patch wins where two overlap.
+ * Discards cached step graphs.  Blocking. */
+int fv_set_boundaries(fv_handle h, const fv_bc_patch* patches, int n);
+
+/* Ghost fill of state buffer `buffer`: first the connections - for every
  * connection, ghost cells at depth 1 and 2 of the dst patch <- src interior
  * cells at the same depth (Section 2, Section 4; Section 7.2 V1 packs such
- * slabs for MPI - on one device the copy is direct).  One kernel launch. */
+ * slabs for MPI - on one device the copy is direct) - then the physical
+ * boundary patches (fv_set_boundaries).  One kernel launch for each of the
+ * two parts that is present. */
 int fv_exchange_ghosts(fv_handle h, int buffer, void* stream);
 
 /* Residual R = sum over faces of F^(V_L, V_R) |S| - S Omega of buffer
  * `buffer` as it stands (no exchange), written to r_dev as a packed interior
  * field (device pointer, fv_field_size doubles).  Sum order per cell: xi pair,
- * eta pair, zeta pair, source. */
+ * eta pair, zeta pair, source.  Slip-wall and farfield boundary faces carry
+ * their overwritten fluxes (fv_bc_kind). */
 int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
 
-/* Runge-Kutta stage m (1..n_stages) with time step dt: exchange the ghosts of
- * Q^(m-1), evaluate R(Q^(m-1)) and write Q^(m) = Q^(0) - alpha_m dt / Omega R.
+/* Runge-Kutta stage m (1..n_stages) with time step dt: fill the ghosts of
+ * Q^(m-1) (fv_exchange_ghosts), evaluate R(Q^(m-1)) and write
+ * Q^(m) = Q^(0) - alpha_m dt / Omega R.
  * Buffers: stage 1 reads Q^(m-1) = Q^(0) from buffer 0; stage m < n_stages
  * writes buffer 1 when m is odd and buffer 2 when m is even; the last stage
- * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Two
- * kernel launches (exchange, fused residual + update). */
+ * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Up to
+ * three kernel launches (connections, physical boundaries, fused residual +
+ * update). */
 int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
 
 /* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage
@@ -227,7 +286,8 @@ int fv_get_launch(fv_handle h, int* out4);
  * including the transpose of the exchange (ghost cotangents added into their
  * donor cells); lam_q0_dev (packed interior field) += lam_out.  qin_dev is
  * not modified.  Fixed ghost cells are constants.  Built for FV_PREC_FP64
- * handles with the Roe flux (FV_ERR_UNSUPPORTED otherwise). */
+ * handles with the Roe flux and no physical boundary patches
+ * (FV_ERR_UNSUPPORTED otherwise). */
 int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
                    double* lam_in_dev, double* lam_q0_dev, void* stream);
 

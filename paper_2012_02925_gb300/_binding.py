@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": PREC_FP64, "df64": PREC_DF64, "fp32flux": PREC_FP32FLUX}
 EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error", "fv_state_size",
            "fv_field_size", "fv_cell_count", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-           "fv_adjoint_vjp", "fv_autotune", "fv_get_launch")
+           "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries")
 
 
 class FvError(RuntimeError):
@@ -42,6 +42,12 @@ class fv_connection(ctypes.Structure):
                 ("dst_lo", ctypes.c_int * 2), ("dst_hi", ctypes.c_int * 2),
                 ("src_block", ctypes.c_int), ("src_face", ctypes.c_int),
                 ("src_lo", ctypes.c_int * 2), ("transform", ctypes.c_int * 2)]
+
+
+class fv_bc_patch(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("face", ctypes.c_int),
+                ("lo", ctypes.c_int * 2), ("hi", ctypes.c_int * 2),
+                ("kind", ctypes.c_int), ("state", ctypes.c_double * 5)]
 
 
 class fv_config(ctypes.Structure):
@@ -89,9 +95,10 @@ def load_library(path: Optional[str] = None):
     L.fv_adjoint_vjp.argtypes = [vp, i32, dbl, vp, vp, vp, vp, vp]
     L.fv_autotune.argtypes = [vp, dbl, i32, vp]
     L.fv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.fv_set_boundaries.argtypes = [vp, ctypes.POINTER(fv_bc_patch), i32]
     for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-              "fv_adjoint_vjp", "fv_autotune", "fv_get_launch"):
+              "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -176,7 +183,11 @@ class Solver:
 
     @classmethod
     def from_problem(cls, pb, precision: str = "fp64", **kw) -> "Solver":
-        return cls(pb.blocks, pb.conns, pb.dim, pb.params, precision, **kw)
+        s = cls(pb.blocks, pb.conns, pb.dim, pb.params, precision, **kw)
+        bcs = getattr(pb, "bcs", None)
+        if bcs:
+            s.set_boundaries(bcs)
+        return s
 
     # -- plumbing ---------------------------------------------------------------
     def _check(self, rc: int):
@@ -229,6 +240,20 @@ class Solver:
 
     def set_source(self, s, stream=None):
         self._check(self._L.fv_set_source(self._h, None if s is None else _ptr(s), _stream(stream)))
+
+    def set_boundaries(self, patches: Sequence) -> None:
+        """Physical boundary patches (objects with block, face, lo, hi, kind,
+        state; see fv_bc_kind); an empty sequence clears them."""
+        arr = (fv_bc_patch * max(1, len(patches)))()
+        for n, p in enumerate(patches):
+            a = arr[n]
+            a.block, a.face, a.kind = int(p.block), int(p.face), int(p.kind)
+            a.lo[0], a.lo[1] = int(p.lo[0]), int(p.lo[1])
+            a.hi[0], a.hi[1] = int(p.hi[0]), int(p.hi[1])
+            st = tuple(getattr(p, "state", (0.0,) * 5))
+            for v in range(5):
+                a.state[v] = float(st[v])
+        self._check(self._L.fv_set_boundaries(self._h, arr, len(patches)))
 
     def exchange_ghosts(self, buffer: int = 0, stream=None):
         self._check(self._L.fv_exchange_ghosts(self._h, int(buffer), _stream(stream)))

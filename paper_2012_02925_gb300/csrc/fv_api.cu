@@ -48,6 +48,11 @@ struct fv_ctx {
   double* adj_lamg = nullptr;       // adjoint: ghosted cotangent of Q^(m-1)
   double* adj_qx = nullptr;         // adjoint: X(Q^(m-1)), the exchanged stage input
   std::vector<FvConnDev> hconns;
+  std::vector<fv_bc_patch> bcs;     // physical boundary patches as set
+  FvBcDev* d_bcs = nullptr;
+  int nbc = 0;
+  long long bc_items = 0;
+  signed char* d_bcmap = nullptr;   // overwritten-flux face maps of all blocks
   int device = 0, nsm = 0;
   std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
   std::string err;
@@ -223,6 +228,132 @@ __global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvC
 }
 
 // ---------------------------------------------------------------------------
+// physical boundaries: work item = (patch, tangential a, b); both ghost
+// layers of that boundary position (Section 2; Section 7.2, V2/V3)
+// ---------------------------------------------------------------------------
+static_assert(FV_BCK_SLIP_WALL == FV_BC_SLIP_WALL && FV_BCK_FARFIELD == FV_BC_FARFIELD &&
+                  FV_BCK_SUPERSONIC_INFLOW == FV_BC_SUPERSONIC_INFLOW && FV_BCK_EXTRAPOLATE == FV_BC_EXTRAPOLATE,
+              "boundary kinds");
+
+__device__ __forceinline__ double metric_d(const double* m, long long i) { return m[i]; }
+__device__ __forceinline__ double metric_d(const float2* m, long long i) {
+  const float2 v = m[i];
+  return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ double metric_d(const float* m, long long i) { return (double)m[i]; }
+
+__device__ void bc_prim_to_cons(const double V[5], double g, double q[5]) {
+  q[0] = V[0];
+  q[1] = V[0] * V[1];
+  q[2] = V[0] * V[2];
+  q[3] = V[0] * V[3];
+  q[4] = V[4] / (g - 1.0) + 0.5 * V[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+}
+
+// characteristic farfield state (1D Riemann invariants along the outward normal n)
+__device__ void bc_farfield(double g, const double Vi[5], const double Vf[5], const double n[3], double Vb[5]) {
+  const double gm1 = g - 1.0;
+  const double ci = sqrt(g * Vi[4] / Vi[0]), cf = sqrt(g * Vf[4] / Vf[0]);
+  const double vni = Vi[1] * n[0] + Vi[2] * n[1] + Vi[3] * n[2];
+  const double vnf = Vf[1] * n[0] + Vf[2] * n[1] + Vf[3] * n[2];
+  if (vni >= ci || vni <= -ci) {
+    const double* src = vni >= ci ? Vi : Vf;
+    for (int m = 0; m < 5; ++m) Vb[m] = src[m];
+    return;
+  }
+  const double rp = vni + 2.0 * ci / gm1, rm = vnf - 2.0 * cf / gm1;
+  const double vnb = 0.5 * (rp + rm), cb = 0.25 * gm1 * (rp - rm);
+  const double* ref = vnb >= 0.0 ? Vi : Vf;
+  const double ent = ref[4] / pow(ref[0], g);
+  const double rhob = pow(cb * cb / (g * ent), 1.0 / gm1);
+  const double vnr = ref[1] * n[0] + ref[2] * n[1] + ref[3] * n[2];
+  Vb[0] = rhob;
+  for (int m = 0; m < 3; ++m) Vb[1 + m] = ref[1 + m] + (vnb - vnr) * n[m];
+  Vb[4] = rhob * cb * cb / g;
+}
+
+template <class MT>
+__global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBcDev* __restrict__ bcs, int nbc,
+                               long long nitems, const MT* m0, const MT* m1, const MT* m2, long long ms0,
+                               long long ms1, long long ms2, double g, double* q) {
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
+       it += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nbc - 1;
+    while (lo < hi) {               // last patch with item_off <= it
+      const int mid = (lo + hi + 1) >> 1;
+      if (bcs[mid].item_off <= it) lo = mid; else hi = mid - 1;
+    }
+    const FvBcDev& P = bcs[lo];
+    const long long local = it - P.item_off;
+    const int a = (int)(local % P.L0), b = (int)(local / P.L0);
+    const FvBlockDev& B = blocks[P.block];
+    const int ax = P.face >> 1, side = P.face & 1;
+    const int ext[3] = {B.ni, B.nj, B.nk};
+    const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+    int c[3];
+    c[t0] = P.lo0 + a;
+    c[t1] = P.lo1 + b;
+    auto qidx = [&](int i, int j, int k) {
+      return B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
+    };
+    // unit normal of the boundary face (pointing +axis)
+    double n[3];
+    if (B.cartesian) {
+      for (int x = 0; x < 3; ++x) n[x] = B.cart_n[ax][x];
+    } else {
+      int fe[3] = {ext[0], ext[1], ext[2]};
+      fe[ax] += 1;
+      int fc[3] = {c[0], c[1], c[2]};
+      fc[ax] = side ? ext[ax] : 0;
+      const long long fi = B.face_off[ax] + ((long long)fc[2] * fe[1] + fc[1]) * fe[0] + fc[0];
+      const MT* m = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
+      const long long ms = ax == 0 ? ms0 : (ax == 1 ? ms1 : ms2);
+      for (int x = 0; x < 3; ++x) n[x] = metric_d(m, fi + x * ms);
+    }
+    int c1[3] = {c[0], c[1], c[2]};
+    c1[ax] = side ? ext[ax] - 1 : 0;
+    const long long i1 = qidx(c1[0], c1[1], c1[2]);
+    double qb[5];
+    if (P.kind == FV_BCK_SUPERSONIC_INFLOW) {
+      bc_prim_to_cons(P.state, g, qb);
+    } else if (P.kind == FV_BCK_EXTRAPOLATE) {
+      for (int v = 0; v < 5; ++v) qb[v] = q[i1 + v * B.plane];
+    } else if (P.kind == FV_BCK_FARFIELD) {
+      double qi[5], Vi[5], Vb[5];
+      for (int v = 0; v < 5; ++v) qi[v] = q[i1 + v * B.plane];
+      Vi[0] = qi[0];
+      Vi[1] = qi[1] / qi[0];
+      Vi[2] = qi[2] / qi[0];
+      Vi[3] = qi[3] / qi[0];
+      Vi[4] = (g - 1.0) * (qi[4] - 0.5 * qi[0] * (Vi[1] * Vi[1] + Vi[2] * Vi[2] + Vi[3] * Vi[3]));
+      const double sg = side ? 1.0 : -1.0;
+      const double nout[3] = {sg * n[0], sg * n[1], sg * n[2]};
+      bc_farfield(g, Vi, P.state, nout, Vb);
+      bc_prim_to_cons(Vb, g, qb);
+    }
+    for (int d = 1; d <= FV_GHOST; ++d) {
+      int cg[3] = {c[0], c[1], c[2]};
+      cg[ax] = side ? ext[ax] - 1 + d : -d;
+      const long long gi = qidx(cg[0], cg[1], cg[2]);
+      if (P.kind == FV_BCK_SLIP_WALL) {
+        int cm[3] = {c[0], c[1], c[2]};
+        cm[ax] = side ? ext[ax] - d : d - 1;
+        const long long mi = qidx(cm[0], cm[1], cm[2]);
+        const double mx = q[mi + B.plane], my = q[mi + 2 * B.plane], mz = q[mi + 3 * B.plane];
+        const double mn = mx * n[0] + my * n[1] + mz * n[2];
+        q[gi] = q[mi];
+        q[gi + B.plane] = mx - 2.0 * mn * n[0];
+        q[gi + 2 * B.plane] = my - 2.0 * mn * n[1];
+        q[gi + 3 * B.plane] = mz - 2.0 * mn * n[2];
+        q[gi + 4 * B.plane] = q[mi + 4 * B.plane];
+      } else {
+        for (int v = 0; v < 5; ++v) q[gi + v * B.plane] = qb[v];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // residual norms (deterministic two-level reduction)
 // ---------------------------------------------------------------------------
 constexpr int NORM_THREADS = 256;
@@ -331,12 +462,32 @@ int stage_out(const fv_ctx* h, int m) {
   return m == h->cfg.n_stages ? 0 : ((m & 1) ? 1 : 2);
 }
 
+// connections first, then the physical boundaries
 int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
-  if (h->conn_items == 0) return FV_OK;
   const int threads = 256;
-  exchange_kernel<<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(h->d_blocks, h->d_conns, h->nconn,
-                                                                            h->conn_items, q);
-  CK(h, cudaGetLastError());
+  if (h->conn_items) {
+    exchange_kernel<<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(h->d_blocks, h->d_conns, h->nconn,
+                                                                              h->conn_items, q);
+    CK(h, cudaGetLastError());
+  }
+  if (h->bc_items) {
+    const int grid = grid_for(h->bc_items, threads, h->nsm);
+    const long long* ms = h->nfaces;
+    if (h->cfg.precision == FV_PREC_FP64) {
+      bc_fill_kernel<double><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
+                                                      (const double*)h->metric[0], (const double*)h->metric[1],
+                                                      (const double*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+    } else if (h->cfg.precision == FV_PREC_DF64) {
+      bc_fill_kernel<float2><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
+                                                      (const float2*)h->metric[0], (const float2*)h->metric[1],
+                                                      (const float2*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+    } else {
+      bc_fill_kernel<float><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
+                                                     (const float*)h->metric[0], (const float*)h->metric[1],
+                                                     (const float*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+    }
+    CK(h, cudaGetLastError());
+  }
   return FV_OK;
 }
 
@@ -674,6 +825,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol); cudaFree(h->srcvol2);
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
+  cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
   delete h;
   return FV_OK;
 }
@@ -742,6 +894,103 @@ int fv_set_source(fv_handle hh, const double* src, void* stream) {
     split_kernel<<<grid_for(5 * h->ncell, 256, h->nsm), 256, 0, s>>>(h->srcvol, h->srcvol2, 5 * h->ncell);
   }
   CK(h, cudaGetLastError());
+  return FV_OK;
+}
+
+int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (n < 0 || (n > 0 && !patches)) return fail(h, FV_ERR_INVALID_ARG, "bad boundary patch list");
+  std::vector<FvBcDev> dev(n);
+  std::vector<long long> map_off(h->hb.size(), -1);
+  long long map_total = 0, items = 0;
+  for (int p = 0; p < n; ++p) {
+    const fv_bc_patch& P = patches[p];
+    char msg[160];
+    if (P.block < 0 || P.block >= h->nblocks) {
+      std::snprintf(msg, sizeof(msg), "boundary patch %d: block %d out of range", p, P.block);
+      return fail(h, FV_ERR_INVALID_ARG, msg);
+    }
+    const FvBlockDev& B = h->hb[P.block];
+    if (P.face < 0 || P.face > 5 || (h->cfg.dim == 2 && P.face > 3)) {
+      std::snprintf(msg, sizeof(msg), "boundary patch %d: face %d not valid for dim %d", p, P.face, h->cfg.dim);
+      return fail(h, FV_ERR_INVALID_ARG, msg);
+    }
+    const int ax = P.face / 2;
+    const int ext[3] = {B.ni, B.nj, B.nk};
+    const int e0 = ext[ax == 0 ? 1 : 0], e1 = ext[ax == 2 ? 1 : 2];
+    if (P.lo[0] < 0 || P.lo[1] < 0 || P.hi[0] > e0 || P.hi[1] > e1 || P.lo[0] >= P.hi[0] || P.lo[1] >= P.hi[1]) {
+      std::snprintf(msg, sizeof(msg), "boundary patch %d: range [%d,%d)x[%d,%d) outside the %dx%d face", p, P.lo[0],
+                    P.hi[0], P.lo[1], P.hi[1], e0, e1);
+      return fail(h, FV_ERR_INVALID_ARG, msg);
+    }
+    if (P.kind < FV_BC_FIXED || P.kind > FV_BC_FARFIELD) {
+      std::snprintf(msg, sizeof(msg), "boundary patch %d: unknown kind %d", p, P.kind);
+      return fail(h, FV_ERR_INVALID_ARG, msg);
+    }
+    if (P.kind == FV_BC_SUPERSONIC_INFLOW || P.kind == FV_BC_FARFIELD) {
+      bool ok = P.state[0] > 0.0 && P.state[4] > 0.0;
+      for (int v = 0; v < 5; ++v) ok = ok && std::isfinite(P.state[v]);
+      if (!ok) {
+        std::snprintf(msg, sizeof(msg), "boundary patch %d: state needs finite values, rho > 0 and p > 0", p);
+        return fail(h, FV_ERR_INVALID_ARG, msg);
+      }
+    }
+    if (P.kind == FV_BC_SLIP_WALL && ext[ax] < 2) {
+      std::snprintf(msg, sizeof(msg), "boundary patch %d: a slip wall needs two cells along the face normal", p);
+      return fail(h, FV_ERR_INVALID_ARG, msg);
+    }
+    FvBcDev& D = dev[p];
+    std::memset(&D, 0, sizeof(D));
+    D.block = P.block; D.face = P.face; D.lo0 = P.lo[0]; D.lo1 = P.lo[1];
+    D.L0 = P.hi[0] - P.lo[0]; D.L1 = P.hi[1] - P.lo[1]; D.kind = P.kind;
+    D.item_off = items;
+    for (int v = 0; v < 5; ++v) D.state[v] = P.state[v];
+    items += (long long)D.L0 * D.L1;
+    if ((P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD) && map_off[P.block] < 0) {
+      map_off[P.block] = map_total;
+      map_total += 2LL * ((long long)B.nj * B.nk + (long long)B.ni * B.nk + (long long)B.ni * B.nj);
+    }
+  }
+  // face maps: every patch writes its kind over its range, in order
+  std::vector<signed char> maps(map_total, 0);
+  for (int p = 0; p < n; ++p) {
+    const fv_bc_patch& P = patches[p];
+    if (map_off[P.block] < 0) continue;
+    const FvBlockDev& B = h->hb[P.block];
+    const long long sz[6] = {(long long)B.nj * B.nk, (long long)B.nj * B.nk, (long long)B.ni * B.nk,
+                             (long long)B.ni * B.nk, (long long)B.ni * B.nj, (long long)B.ni * B.nj};
+    long long base = map_off[P.block];
+    for (int f = 0; f < P.face; ++f) base += sz[f];
+    const int ext0 = P.face < 2 ? B.nj : B.ni;
+    const signed char code = (P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD) ? (signed char)P.kind : 0;
+    for (int t1 = P.lo[1]; t1 < P.hi[1]; ++t1)
+      for (int t0 = P.lo[0]; t0 < P.hi[0]; ++t0) maps[base + (long long)t1 * ext0 + t0] = code;
+  }
+  CK(h, cudaDeviceSynchronize());
+  // drop the old set first (a failed allocation below leaves no boundaries)
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  h->nbc = 0;
+  h->bc_items = 0;
+  h->bcs.clear();
+  for (auto& B : h->hb) B.bcmap = nullptr;
+  CK(h, cudaMemcpy(h->d_blocks, h->hb.data(), sizeof(FvBlockDev) * h->hb.size(), cudaMemcpyHostToDevice));
+  cudaFree(h->d_bcs); h->d_bcs = nullptr;
+  cudaFree(h->d_bcmap); h->d_bcmap = nullptr;
+  if (n) {
+    CK(h, cudaMalloc(&h->d_bcs, sizeof(FvBcDev) * n));
+    CK(h, cudaMemcpy(h->d_bcs, dev.data(), sizeof(FvBcDev) * n, cudaMemcpyHostToDevice));
+  }
+  if (map_total) {
+    CK(h, cudaMalloc(&h->d_bcmap, map_total));
+    CK(h, cudaMemcpy(h->d_bcmap, maps.data(), map_total, cudaMemcpyHostToDevice));
+  }
+  for (size_t b = 0; b < h->hb.size(); ++b) h->hb[b].bcmap = map_off[b] < 0 ? nullptr : h->d_bcmap + map_off[b];
+  CK(h, cudaMemcpy(h->d_blocks, h->hb.data(), sizeof(FvBlockDev) * h->hb.size(), cudaMemcpyHostToDevice));
+  h->bcs.assign(patches, patches + n);
+  h->nbc = n;
+  h->bc_items = items;
   return FV_OK;
 }
 
@@ -900,6 +1149,7 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
   if (h->cfg.precision != FV_PREC_FP64)
     return fail(h, FV_ERR_UNSUPPORTED, "the adjoint runs in binary64: create the handle with FV_PREC_FP64");
   if (h->cfg.flux != FV_FLUX_ROE) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint is built for the Roe flux");
+  if (h->nbc) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint does not linearise physical boundary patches");
   cudaStream_t s = (cudaStream_t)stream;
   const int nd = h->cfg.dim;
   // per-direction offsets of each block's faces in the contribution scratch
@@ -918,7 +1168,7 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
   double* cdir[3] = {h->adj_contrib, h->adj_contrib + 20 * tot[0], h->adj_contrib + 20 * (tot[0] + tot[1])};
   // linearise around the state the forward stage saw: X(Q^(m-1)), ghosts exchanged
   const double* qx = qin_dev;
-  if (h->conn_items) {
+  if (h->conn_items || h->bc_items) {
     if (!h->adj_qx) CK(h, cudaMalloc(&h->adj_qx, sizeof(double) * h->state_elems));
     int rc = copy_state(h, qin_dev, h->adj_qx, true, s);
     if (rc) return rc;

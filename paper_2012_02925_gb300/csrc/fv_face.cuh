@@ -288,6 +288,37 @@ __device__ __forceinline__ void face_riemann(const CC& C, const T VL[5], const T
   for (int n = 0; n < 5; ++n) out[n] = (Fp[n] + Fm[n]) * A;
 }
 
+// ---------------------------------------------------------------------------
+// Overwritten boundary-face fluxes (Section 7.2, V7), times the face area.
+// ---------------------------------------------------------------------------
+
+// slip wall: pressure only, p_w = (3 p_1 - p_2)/2 from the two nearest cells
+template <class T, class CC>
+__device__ __forceinline__ void wall_face_flux(const CC& C, T p1, T p2, T nx, T ny, T nz, T A, T out[5]) {
+  using S = Sc<T>;
+  const T pwA = (S::c(1.5) * p1 - S::c(0.5) * p2) * A;
+  out[0] = S::c(0.0);
+  out[1] = pwA * nx;
+  out[2] = pwA * ny;
+  out[3] = pwA * nz;
+  out[4] = S::c(0.0);
+}
+
+// farfield: the physical normal flux F(V_b).n of the boundary state (the ghost)
+template <class T, class CC>
+__device__ __forceinline__ void normal_face_flux(const CC& C, const T V[5], T nx, T ny, T nz, T A, T out[5]) {
+  using S = Sc<T>;
+  const T r = V[0], u = V[1], v = V[2], w = V[3], p = V[4];
+  const T Vn = nx * u + ny * v + nz * w;
+  const T ht = C.g_gm1 * p * S::rcp(r) + C.half * (u * u + v * v + w * w);
+  const T m = r * Vn;
+  out[0] = m * A;
+  out[1] = (m * u + nx * p) * A;
+  out[2] = (m * v + ny * p) * A;
+  out[3] = (m * w + nz * p) * A;
+  out[4] = (m * ht) * A;
+}
+
 // Full face: reconstruct the 5 primitive components along the stencil
 // c0..c3 (pointers to component 0 of each cell, components `cs` apart) and
 // evaluate the Roe flux times area.

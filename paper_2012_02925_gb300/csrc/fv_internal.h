@@ -18,6 +18,11 @@ struct FvBlockDev {
   long long face_off[3];        // first face in the per-direction metric arrays
   int cartesian;                // metrics are per-block constants
   int pad_;
+  // codes of the boundary faces whose flux is overwritten (slip wall,
+  // farfield): six face maps (imin, imax, jmin, jmax, kmin, kmax; sizes
+  // nj*nk, nj*nk, ni*nk, ni*nk, ni*nj, ni*nj; first tangential index
+  // fastest) back to back, or null when the block has none
+  const signed char* bcmap;
   double cart_n[3][3];          // Cartesian unit normal of each face family
   double cart_area[3];          // Cartesian face areas
   double cart_invvol;           // Cartesian 1/volume
@@ -33,6 +38,17 @@ struct FvConnDev {
   int dst_block, dst_face, dlo0, dlo1, L0, L1;
   int src_block, src_face, slo0, slo1, t0, t1;
   long long item_off;           // first work item (a, b, depth) of this connection
+};
+
+// Physical boundary kinds as the kernels see them (the values of fv_bc_kind).
+constexpr int FV_BCK_FIXED = 0, FV_BCK_SUPERSONIC_INFLOW = 1, FV_BCK_EXTRAPOLATE = 2, FV_BCK_SLIP_WALL = 3,
+              FV_BCK_FARFIELD = 4;
+
+// One physical boundary patch; work items (a, b) = tangential cells.
+struct FvBcDev {
+  int block, face, lo0, lo1, L0, L1, kind, pad_;
+  long long item_off;           // first work item of this patch
+  double state[5];              // primitive (rho, u, v, w, p)
 };
 
 struct FvFaceParams {

@@ -177,8 +177,10 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
 
     // Evaluate one face from its stencil cells s0..s3 (ring/plane pointers),
     // direction `dir` and face index f, storing the 5 fluxes at dst[n * dstr].
+    // code: 0, or the boundary kind whose flux overwrites this face (slip
+    // wall, farfield); side: 0 on the block's min face, 1 on its max face
     auto do_face = [&](const T* s0, const T* s1, const T* s2, const T* s3, int dir, long long f, T* dst,
-                       int dstr) {
+                       int dstr, int code, int side) {
       T nx, ny, nz, A;
       if (cart) {
         nx = S::from_d(B.cart_n[dir][0]); ny = S::from_d(B.cart_n[dir][1]);
@@ -190,7 +192,18 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         nz = MetricStore<T>::ld(m, f + 2 * ms); A = MetricStore<T>::ld(m, f + 3 * ms);
       }
       T out[5];
-      face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
+      if (code == FV_BCK_SLIP_WALL) {
+        // nearest interior cells: s2, s3 on a min face, s1, s0 on a max face
+        wall_face_flux(C, (side ? s1 : s2)[4 * PL], (side ? s0 : s3)[4 * PL], nx, ny, nz, A, out);
+      } else if (code == FV_BCK_FARFIELD) {
+        const T* gc = side ? s2 : s1;   // first ghost layer: the boundary state
+        T Vb[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) Vb[n] = gc[n * PL];
+        normal_face_flux(C, Vb, nx, ny, nz, A, out);
+      } else {
+        face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
+      }
 #pragma unroll
       for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
     };
@@ -289,7 +302,32 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
           dstr = d == 0 ? NXI : NETA;
           f = met + k * (d == 0 ? kfx : kfy);
         }
-        do_face(s0, s1, s2, s3, d, f, dp, dstr);
+        // physical boundary face with an overwritten flux?
+        int code = 0, side = 0;
+        if (B.bcmap) {
+          if (d == 0) {
+            const int fy = dst / (TX + 1), fi = i0 + dst - fy * (TX + 1);
+            if (fi == 0 || fi == ni) {
+              side = fi != 0;
+              code = B.bcmap[(side ? (long long)nj * nk : 0) + (long long)k * nj + (j0 + fy)];
+            }
+          } else if (d == 1) {
+            const int fy = dst / TX, fj = j0 + fy;
+            if (fj == 0 || fj == nj) {
+              side = fj != 0;
+              code = B.bcmap[2LL * nj * nk + (side ? (long long)ni * nk : 0) + (long long)k * ni + (i0 + dst - fy * TX)];
+            }
+          } else {
+            const int fk = k + 1;
+            if (fk == 0 || fk == nk) {
+              side = fk != 0;
+              const int fy = dst / TX;
+              code = B.bcmap[2LL * nj * nk + 2LL * ni * nk + (side ? (long long)ni * nj : 0) +
+                             (long long)(j0 + fy) * ni + (i0 + dst - fy * TX)];
+            }
+          }
+        }
+        do_face(s0, s1, s2, s3, d, f, dp, dstr, code, side);
       }
       __syncthreads();
       if (DIM3 && k < k0) continue;
