@@ -79,6 +79,10 @@ def workload(name: str):
         return cases.multiblock_batched()
     if name == "vortex":
         return cases.vortex_2d(64)
+    if name == "inlet":       # the paper's largest inlet grids are ~7 M cells
+        return cases.inlet_2d(4096, 1536)
+    if name == "ogrid":       # wing-sized (4.2 M cells) extruded O-grid
+        return cases.ellipse_ogrid(512, 128, 64)
     if name.startswith("mms"):
         return cases.mms_3d(int(name[3:]), curvilinear=True)
     raise SystemExit("unknown workload " + name)
@@ -86,19 +90,21 @@ def workload(name: str):
 
 def algorithmic_bytes(pb, stage: int, curvilinear: bool) -> float:
     """Bytes a cell-update must move at least: read Q^(m-1) (40 B), read Q^(0)
-    for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics 80 B
-    (3 face vectors + 1/Omega); a source term 40 B; exchanged ghost cells read
-    and write 80 B each."""
+    for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics 24 B per
+    face family (3 in 3D, 2 in 2D) + 8 B of 1/Omega; a source term 40 B;
+    exchanged ghost cells read and write 80 B each; a physical boundary
+    position writes its two ghost layers and reads one interior cell (120 B)."""
     n = pb.ncells
     per = 80.0 + (40.0 if stage > 1 else 0.0)
     if curvilinear:
-        per += 80.0
+        per += 24.0 * pb.dim + 8.0
     if pb.source is not None:
         per += 40.0
     ghosts = 0
     for c in pb.conns:
         ghosts += 2 * (c.dst_hi[0] - c.dst_lo[0]) * (c.dst_hi[1] - c.dst_lo[1])
-    return per * n + 80.0 * ghosts
+    bc = sum((p.hi[0] - p.lo[0]) * (p.hi[1] - p.lo[1]) for p in getattr(pb, "bcs", []) or [])
+    return per * n + 80.0 * ghosts + 120.0 * bc
 
 
 def peaks():
@@ -229,7 +235,7 @@ def time_stage_kernels(s, pb, reps):
         torch.cuda.synchronize()
         out.append(e0.elapsed_time(e1) / 1e3 / reps)
     ex = 0.0
-    if pb.conns:
+    if pb.conns or getattr(pb, "bcs", None):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         for _ in range(reps):
@@ -440,7 +446,7 @@ def run_variants(args, pk, peak_kind, traffic):
             st, ex = time_stage_kernels(s, pb, 3)
             out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
                         "value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
-                        "launch": s.launch(),
+                        "launch": s.launch(), "ghost_fill_s": ex,
                         "roofline": roofline(pb, prec, st, ex, curv, pk, peak_kind, traffic)})
             s.close()
         except Exception as e:  # report, do not hide
@@ -522,7 +528,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
-    ap.add_argument("--variant-workloads", default="mms128,multiblock,large,mms128+vl,mms128+sw")
+    ap.add_argument("--variant-workloads", default="mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -242,18 +242,27 @@ __device__ __forceinline__ double metric_d(const float2* m, long long i) {
 }
 __device__ __forceinline__ double metric_d(const float* m, long long i) { return (double)m[i]; }
 
-__device__ void bc_prim_to_cons(const double V[5], double g, double q[5]) {
+// gas constants of the boundary kernels (one division each, on the host)
+struct BcGas {
+  double g, gm1, igm1, k2, ig;   // gamma, gamma-1, 1/(gamma-1), 2/(gamma-1), 1/gamma
+  int e;                         // 2/(gamma-1) when it is a small integer, else 0
+};
+
+__device__ __forceinline__ void bc_prim_to_cons(const double V[5], const BcGas& G, double q[5]) {
   q[0] = V[0];
   q[1] = V[0] * V[1];
   q[2] = V[0] * V[2];
   q[3] = V[0] * V[3];
-  q[4] = V[4] / (g - 1.0) + 0.5 * V[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+  q[4] = V[4] * G.igm1 + 0.5 * V[0] * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
 }
 
-// characteristic farfield state (1D Riemann invariants along the outward normal n)
-__device__ void bc_farfield(double g, const double Vi[5], const double Vf[5], const double n[3], double Vb[5]) {
-  const double gm1 = g - 1.0;
-  const double ci = sqrt(g * Vi[4] / Vi[0]), cf = sqrt(g * Vf[4] / Vf[0]);
+// Characteristic farfield state (1D Riemann invariants along the outward
+// normal n) from the interior primitive state Vi with sound speed ci and the
+// free stream Vf with sound speed cf.  FP64 is GB300's slow unit: two
+// divisions' worth of work in all (the free-stream sound speed comes from
+// the host, 1/(gamma-1) and 2/(gamma-1) are constants).
+__device__ __forceinline__ void bc_farfield(const BcGas& G, const double Vi[5], double ci, const double Vf[5], double cf,
+                                            const double n[3], double Vb[5]) {
   const double vni = Vi[1] * n[0] + Vi[2] * n[1] + Vi[3] * n[2];
   const double vnf = Vf[1] * n[0] + Vf[2] * n[1] + Vf[3] * n[2];
   if (vni >= ci || vni <= -ci) {
@@ -261,21 +270,30 @@ __device__ void bc_farfield(double g, const double Vi[5], const double Vf[5], co
     for (int m = 0; m < 5; ++m) Vb[m] = src[m];
     return;
   }
-  const double rp = vni + 2.0 * ci / gm1, rm = vnf - 2.0 * cf / gm1;
-  const double vnb = 0.5 * (rp + rm), cb = 0.25 * gm1 * (rp - rm);
-  const double* ref = vnb >= 0.0 ? Vi : Vf;
-  const double ent = ref[4] / pow(ref[0], g);
-  const double rhob = pow(cb * cb / (g * ent), 1.0 / gm1);
+  const double rp = vni + G.k2 * ci, rm = vnf - G.k2 * cf;
+  const double vnb = 0.5 * (rp + rm), cb = 0.25 * G.gm1 * (rp - rm);
+  const bool out = vnb >= 0.0;
+  const double* ref = out ? Vi : Vf;
+  // equal entropy p / rho^gamma: rho_b = rho_ref (c_b / c_ref)^(2/(gamma-1)),
+  // an integer power for gamma = 1.4 (and 5/3, ...); binary64 pow otherwise
+  const double ratio = cb / (out ? ci : cf);
+  double scale = ratio;
+  if (G.e > 0) {
+    for (int x = 1; x < G.e; ++x) scale *= ratio;
+  } else {
+    scale = pow(ratio, G.k2);
+  }
+  const double rhob = ref[0] * scale;
   const double vnr = ref[1] * n[0] + ref[2] * n[1] + ref[3] * n[2];
   Vb[0] = rhob;
   for (int m = 0; m < 3; ++m) Vb[1 + m] = ref[1 + m] + (vnb - vnr) * n[m];
-  Vb[4] = rhob * cb * cb / g;
+  Vb[4] = rhob * cb * cb * G.ig;
 }
 
 template <class MT>
 __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBcDev* __restrict__ bcs, int nbc,
                                long long nitems, const MT* m0, const MT* m1, const MT* m2, long long ms0,
-                               long long ms1, long long ms2, double g, double* q) {
+                               long long ms1, long long ms2, BcGas G, double* q) {
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
        it += (long long)gridDim.x * blockDim.x) {
     int lo = 0, hi = nbc - 1;
@@ -288,65 +306,67 @@ __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBc
     const int a = (int)(local % P.L0), b = (int)(local / P.L0);
     const FvBlockDev& B = blocks[P.block];
     const int ax = P.face >> 1, side = P.face & 1;
-    const int ext[3] = {B.ni, B.nj, B.nk};
-    const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
-    int c[3];
-    c[t0] = P.lo0 + a;
-    c[t1] = P.lo1 + b;
-    auto qidx = [&](int i, int j, int k) {
-      return B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
-    };
+    // tangential cell coordinates (scalars, so that nothing is indexed at run time)
+    const int ti = ax == 0 ? 0 : P.lo0 + a;
+    const int tj = ax == 0 ? P.lo0 + a : (ax == 1 ? 0 : P.lo1 + b);
+    const int tk = ax == 2 ? 0 : P.lo1 + b;
+    const int ext = ax == 0 ? B.ni : (ax == 1 ? B.nj : B.nk);
+    const long long astride = ax == 0 ? 1 : (ax == 1 ? B.jstride : B.kstride);
+    // state index of the cell at coordinate t along the face normal
+    const long long base = B.qoff + (long long)(tk + 2) * B.kstride + (long long)(tj + 2) * B.jstride + (ti + 2) -
+                           2 * astride;
+    auto at = [&](int t) { return base + (long long)(t + 2) * astride; };
     // unit normal of the boundary face (pointing +axis)
-    double n[3];
+    double n0, n1, n2;
     if (B.cartesian) {
-      for (int x = 0; x < 3; ++x) n[x] = B.cart_n[ax][x];
+      n0 = B.cart_n[ax][0]; n1 = B.cart_n[ax][1]; n2 = B.cart_n[ax][2];
     } else {
-      int fe[3] = {ext[0], ext[1], ext[2]};
-      fe[ax] += 1;
-      int fc[3] = {c[0], c[1], c[2]};
-      fc[ax] = side ? ext[ax] : 0;
-      const long long fi = B.face_off[ax] + ((long long)fc[2] * fe[1] + fc[1]) * fe[0] + fc[0];
+      const int tf = side ? ext : 0;
+      const long long fi = B.face_off[ax] +
+                           (ax == 0 ? ((long long)tk * B.nj + tj) * (B.ni + 1) + tf
+                                    : (ax == 1 ? ((long long)tk * (B.nj + 1) + tf) * B.ni + ti
+                                               : ((long long)tf * B.nj + tj) * B.ni + ti));
       const MT* m = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
       const long long ms = ax == 0 ? ms0 : (ax == 1 ? ms1 : ms2);
-      for (int x = 0; x < 3; ++x) n[x] = metric_d(m, fi + x * ms);
+      n0 = metric_d(m, fi); n1 = metric_d(m, fi + ms); n2 = metric_d(m, fi + 2 * ms);
     }
-    int c1[3] = {c[0], c[1], c[2]};
-    c1[ax] = side ? ext[ax] - 1 : 0;
-    const long long i1 = qidx(c1[0], c1[1], c1[2]);
+    const long long i1 = at(side ? ext - 1 : 0);   // first interior cell
     double qb[5];
     if (P.kind == FV_BCK_SUPERSONIC_INFLOW) {
-      bc_prim_to_cons(P.state, g, qb);
+      for (int v = 0; v < 5; ++v) qb[v] = P.qstate[v];
     } else if (P.kind == FV_BCK_EXTRAPOLATE) {
       for (int v = 0; v < 5; ++v) qb[v] = q[i1 + v * B.plane];
     } else if (P.kind == FV_BCK_FARFIELD) {
       double qi[5], Vi[5], Vb[5];
       for (int v = 0; v < 5; ++v) qi[v] = q[i1 + v * B.plane];
+      const double ri = 1.0 / qi[0];
       Vi[0] = qi[0];
-      Vi[1] = qi[1] / qi[0];
-      Vi[2] = qi[2] / qi[0];
-      Vi[3] = qi[3] / qi[0];
-      Vi[4] = (g - 1.0) * (qi[4] - 0.5 * qi[0] * (Vi[1] * Vi[1] + Vi[2] * Vi[2] + Vi[3] * Vi[3]));
+      Vi[1] = qi[1] * ri;
+      Vi[2] = qi[2] * ri;
+      Vi[3] = qi[3] * ri;
+      Vi[4] = G.gm1 * (qi[4] - 0.5 * (qi[1] * Vi[1] + qi[2] * Vi[2] + qi[3] * Vi[3]));
+      const double ci = sqrt(G.g * Vi[4] * ri);
       const double sg = side ? 1.0 : -1.0;
-      const double nout[3] = {sg * n[0], sg * n[1], sg * n[2]};
-      bc_farfield(g, Vi, P.state, nout, Vb);
-      bc_prim_to_cons(Vb, g, qb);
+      const double nout[3] = {sg * n0, sg * n1, sg * n2};
+      const double Vf[5] = {P.state[0], P.state[1], P.state[2], P.state[3], P.state[4]};
+      bc_farfield(G, Vi, ci, Vf, P.cstate, nout, Vb);
+      bc_prim_to_cons(Vb, G, qb);
     }
+#pragma unroll
     for (int d = 1; d <= FV_GHOST; ++d) {
-      int cg[3] = {c[0], c[1], c[2]};
-      cg[ax] = side ? ext[ax] - 1 + d : -d;
-      const long long gi = qidx(cg[0], cg[1], cg[2]);
+      const long long gi = at(side ? ext - 1 + d : -d);
       if (P.kind == FV_BCK_SLIP_WALL) {
-        int cm[3] = {c[0], c[1], c[2]};
-        cm[ax] = side ? ext[ax] - d : d - 1;
-        const long long mi = qidx(cm[0], cm[1], cm[2]);
+        // mirror of the interior cell at the same depth, normal momentum reflected
+        const long long mi = at(side ? ext - d : d - 1);
         const double mx = q[mi + B.plane], my = q[mi + 2 * B.plane], mz = q[mi + 3 * B.plane];
-        const double mn = mx * n[0] + my * n[1] + mz * n[2];
+        const double mn2 = 2.0 * (mx * n0 + my * n1 + mz * n2);
         q[gi] = q[mi];
-        q[gi + B.plane] = mx - 2.0 * mn * n[0];
-        q[gi + 2 * B.plane] = my - 2.0 * mn * n[1];
-        q[gi + 3 * B.plane] = mz - 2.0 * mn * n[2];
+        q[gi + B.plane] = mx - mn2 * n0;
+        q[gi + 2 * B.plane] = my - mn2 * n1;
+        q[gi + 3 * B.plane] = mz - mn2 * n2;
         q[gi + 4 * B.plane] = q[mi + 4 * B.plane];
-      } else {
+      } else if (P.kind != FV_BCK_FIXED) {
+#pragma unroll
         for (int v = 0; v < 5; ++v) q[gi + v * B.plane] = qb[v];
       }
     }
@@ -473,18 +493,25 @@ int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
   if (h->bc_items) {
     const int grid = grid_for(h->bc_items, threads, h->nsm);
     const long long* ms = h->nfaces;
+    BcGas G;
+    G.g = h->cfg.gamma;
+    G.gm1 = G.g - 1.0;
+    G.igm1 = 1.0 / G.gm1;
+    G.k2 = 2.0 / G.gm1;
+    G.ig = 1.0 / G.g;
+    G.e = (G.k2 == std::rint(G.k2) && G.k2 >= 1.0 && G.k2 <= 16.0) ? (int)G.k2 : 0;
     if (h->cfg.precision == FV_PREC_FP64) {
       bc_fill_kernel<double><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                       (const double*)h->metric[0], (const double*)h->metric[1],
-                                                      (const double*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+                                                      (const double*)h->metric[2], ms[0], ms[1], ms[2], G, q);
     } else if (h->cfg.precision == FV_PREC_DF64) {
       bc_fill_kernel<float2><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                       (const float2*)h->metric[0], (const float2*)h->metric[1],
-                                                      (const float2*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+                                                      (const float2*)h->metric[2], ms[0], ms[1], ms[2], G, q);
     } else {
       bc_fill_kernel<float><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                      (const float*)h->metric[0], (const float*)h->metric[1],
-                                                     (const float*)h->metric[2], ms[0], ms[1], ms[2], h->cfg.gamma, q);
+                                                     (const float*)h->metric[2], ms[0], ms[1], ms[2], G, q);
     }
     CK(h, cudaGetLastError());
   }
@@ -946,6 +973,14 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
     D.L0 = P.hi[0] - P.lo[0]; D.L1 = P.hi[1] - P.lo[1]; D.kind = P.kind;
     D.item_off = items;
     for (int v = 0; v < 5; ++v) D.state[v] = P.state[v];
+    if (P.kind == FV_BC_SUPERSONIC_INFLOW || P.kind == FV_BC_FARFIELD) {
+      const double g = h->cfg.gamma, r = P.state[0];
+      D.qstate[0] = r;
+      for (int v = 1; v < 4; ++v) D.qstate[v] = r * P.state[v];
+      D.qstate[4] = P.state[4] / (g - 1.0) +
+                    0.5 * r * (P.state[1] * P.state[1] + P.state[2] * P.state[2] + P.state[3] * P.state[3]);
+      D.cstate = std::sqrt(g * P.state[4] / r);
+    }
     items += (long long)D.L0 * D.L1;
     if ((P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD) && map_off[P.block] < 0) {
       map_off[P.block] = map_total;

@@ -49,6 +49,8 @@ struct FvBcDev {
   int block, face, lo0, lo1, L0, L1, kind, pad_;
   long long item_off;           // first work item of this patch
   double state[5];              // primitive (rho, u, v, w, p)
+  double qstate[5];             // the same, conserved
+  double cstate;                // its speed of sound
 };
 
 struct FvFaceParams {
