@@ -23,12 +23,13 @@ from .core import (GAMMA, GHOST, BlockDesc, Connection, Problem, prim_to_cons,
                    interior_view, nominal_dt, FACE_IMIN, FACE_IMAX, FACE_JMIN,
                    FACE_JMAX, FACE_KMIN, FACE_KMAX, periodic_connections,
                    conn_array, BCPatch, bc_arrays, BC_FIXED, BC_SUPERSONIC_INFLOW,
-                   BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD, BC_NAMES)
+                   BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD, BC_NOSLIP_WALL, BC_NAMES)
 from .workloads import (vortex_2d, mms_3d, multiblock_batched, large_periodic,
                         perturbed_nodes, uniform_3d, split_problem_i,
                         mms_primitives, mms_source, rotated_split_problem,
                         inlet_2d, ellipse_ogrid, channel_uniform, table_state,
-                        INLET_INFLOW, AIRFOIL_FARFIELD, WING_FARFIELD)
+                        INLET_INFLOW, AIRFOIL_FARFIELD, WING_FARFIELD, mms_periodic_3d,
+                        mms_viscous_divergence, viscosity)
 
 __all__ = [
     "GAMMA", "GHOST", "BlockDesc", "Connection", "Problem", "prim_to_cons",
@@ -36,9 +37,9 @@ __all__ = [
     "interior_view", "nominal_dt", "FACE_IMIN", "FACE_IMAX", "FACE_JMIN",
     "FACE_JMAX", "FACE_KMIN", "FACE_KMAX", "periodic_connections", "conn_array",
     "BCPatch", "bc_arrays", "BC_FIXED", "BC_SUPERSONIC_INFLOW", "BC_EXTRAPOLATE",
-    "BC_SLIP_WALL", "BC_FARFIELD", "BC_NAMES",
+    "BC_SLIP_WALL", "BC_FARFIELD", "BC_NOSLIP_WALL", "BC_NAMES",
     "vortex_2d", "mms_3d", "multiblock_batched", "large_periodic",
     "perturbed_nodes", "uniform_3d", "split_problem_i", "mms_primitives",
     "mms_source", "rotated_split_problem", "inlet_2d", "ellipse_ogrid",
-    "channel_uniform", "table_state", "INLET_INFLOW", "AIRFOIL_FARFIELD", "WING_FARFIELD",
+    "channel_uniform", "table_state", "INLET_INFLOW", "AIRFOIL_FARFIELD", "WING_FARFIELD", "mms_periodic_3d", "mms_viscous_divergence", "viscosity",
 ]

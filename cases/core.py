@@ -60,9 +60,9 @@ class Connection:
 
 
 # Physical boundary kinds of a BCPatch.
-BC_FIXED, BC_SUPERSONIC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD = range(5)
+BC_FIXED, BC_SUPERSONIC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_FARFIELD, BC_NOSLIP_WALL = range(6)
 BC_NAMES = {BC_FIXED: "fixed", BC_SUPERSONIC_INFLOW: "supersonic_inflow", BC_EXTRAPOLATE: "extrapolate",
-            BC_SLIP_WALL: "slip_wall", BC_FARFIELD: "farfield"}
+            BC_SLIP_WALL: "slip_wall", BC_FARFIELD: "farfield", BC_NOSLIP_WALL: "noslip_wall"}
 
 
 @dataclass
@@ -97,8 +97,13 @@ class Problem:
 
 
 def default_params(**over) -> dict:
+    """Method parameters.  visc = 1 adds the laminar viscous flux (Section 2):
+    constant viscosity ``mu`` (sutherland = 0) or Sutherland's law with
+    mu(t_ref) = mu (sutherland = 1, constant s_suth); Prandtl number
+    ``prandtl``; gas constant ``r_gas`` (T = p / (rho r_gas))."""
     p = dict(gamma=GAMMA, eps=1.0, kappa=-1.0, limiter=1, harten=0.1,
-             fix_all=0, va_delta2=1e-12, n_stages=4, flux=0)
+             fix_all=0, va_delta2=1e-12, n_stages=4, flux=0,
+             visc=0, mu=0.0, prandtl=0.72, r_gas=1.0, sutherland=0, t_ref=273.15, s_suth=110.4)
     p.update(over)
     p["alpha"] = RK_ALPHA[p["n_stages"]]
     return p

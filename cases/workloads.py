@@ -91,15 +91,23 @@ _MMS = {
     "p": (1.0 / GAMMA, 0.02, 0.01, -0.015, 2.0, 1.0, 1.5),
 }
 _MMS_ORDER = ("rho", "u", "v", "w", "p")
+# the same form with wave numbers that make every field 1-periodic in x, y, z
+_MMS_PERIODIC = {
+    "rho": (1.0, 0.15, -0.1, 0.1, 2.0, 2.0, 2.0),
+    "u": (0.4, 0.05, 0.03, 0.02, 2.0, 4.0, 2.0),
+    "v": (0.3, -0.04, 0.05, 0.02, 4.0, 2.0, 2.0),
+    "w": (0.25, 0.03, 0.02, -0.04, 2.0, 2.0, 4.0),
+    "p": (1.0 / GAMMA, 0.02, 0.01, -0.015, 2.0, 2.0, 2.0),
+}
 
 
-def mms_primitives(x, y, z):
+def mms_primitives(x, y, z, table=None):
     """Manufactured primitive fields (rho,u,v,w,p) and their gradients.
     Returns (P, dPdx, dPdy, dPdz), each of shape (5,) + x.shape."""
     pi = math.pi
     P, Dx, Dy, Dz = [], [], [], []
     for name in _MMS_ORDER:
-        f0, fx, fy, fz, ax, ay, az = _MMS[name]
+        f0, fx, fy, fz, ax, ay, az = (table or _MMS)[name]
         P.append(f0 + fx * np.sin(ax * pi * x) + fy * np.cos(ay * pi * y) + fz * np.sin(az * pi * z))
         Dx.append(fx * ax * pi * np.cos(ax * pi * x))
         Dy.append(-fy * ay * pi * np.sin(ay * pi * y))
@@ -107,13 +115,73 @@ def mms_primitives(x, y, z):
     return np.array(P), np.array(Dx), np.array(Dy), np.array(Dz)
 
 
-def mms_source(x, y, z, gamma: float = GAMMA) -> np.ndarray:
+def mms_second_derivatives(x, y, z, table=None):
+    """d2P/dx2, d2P/dy2, d2P/dz2 of the manufactured fields (each field is a
+    sum of one-variable functions, so every mixed derivative is zero)."""
+    pi = math.pi
+    Dxx, Dyy, Dzz = [], [], []
+    for name in _MMS_ORDER:
+        f0, fx, fy, fz, ax, ay, az = (table or _MMS)[name]
+        Dxx.append(-fx * (ax * pi) ** 2 * np.sin(ax * pi * x))
+        Dyy.append(-fy * (ay * pi) ** 2 * np.cos(ay * pi * y))
+        Dzz.append(-fz * (az * pi) ** 2 * np.sin(az * pi * z))
+    return np.array(Dxx), np.array(Dyy), np.array(Dzz)
+
+
+def viscosity(T, params: dict):
+    """Laminar viscosity and dmu/dT: constant, or Sutherland's law
+    mu = mu_ref (T/T_ref)^(3/2) (T_ref + S)/(T + S)."""
+    mu0 = params["mu"]
+    if not params.get("sutherland", 0):
+        return mu0 * np.ones_like(T), np.zeros_like(T)
+    Tr, S = params["t_ref"], params["s_suth"]
+    mu = mu0 * (T / Tr) ** 1.5 * (Tr + S) / (T + S)
+    return mu, mu * (1.5 / T - 1.0 / (T + S))
+
+
+def mms_viscous_divergence(x, y, z, params: dict, table=None) -> np.ndarray:
+    """div F_v of the manufactured fields (Section 2: tau by Stokes's
+    hypothesis, Theta = tau.u + k grad T, k = mu c_p / Pr,
+    c_p = gamma R/(gamma - 1), T = p/(rho R)).  With every mixed derivative
+    zero, d_j tau_ij = mu (lap u_i + d_i div u / 3) + A_ij d_j mu, A = tau / mu."""
+    g, R, Pr = params["gamma"], params["r_gas"], params["prandtl"]
+    cp = g * R / (g - 1.0)
+    P, Dx, Dy, Dz = mms_primitives(x, y, z, table)
+    D2 = mms_second_derivatives(x, y, z, table)
+    D1 = (Dx, Dy, Dz)
+    rho, p = P[0], P[4]
+    T = p / (rho * R)
+    dT = [(D1[j][4] / rho - p * D1[j][0] / rho ** 2) / R for j in range(3)]
+    d2T = [(D2[j][4] / rho - 2 * D1[j][4] * D1[j][0] / rho ** 2 - p * D2[j][0] / rho ** 2
+            + 2 * p * D1[j][0] ** 2 / rho ** 3) / R for j in range(3)]
+    mu, dmu_dT = viscosity(T, params)
+    dmu = [dmu_dT * dT[j] for j in range(3)]
+    vel = [P[1], P[2], P[3]]
+    G = [[D1[j][1 + i] for j in range(3)] for i in range(3)]       # G[i][j] = d u_i / d x_j
+    div = G[0][0] + G[1][1] + G[2][2]
+    A = [[G[i][j] + G[j][i] - (2.0 / 3.0 if i == j else 0.0) * div for j in range(3)] for i in range(3)]
+    out = np.zeros_like(P)
+    divtau = []
+    for i in range(3):
+        lap = D2[0][1 + i] + D2[1][1 + i] + D2[2][1 + i]
+        t = mu * (lap + D2[i][1 + i] / 3.0) + sum(A[i][j] * dmu[j] for j in range(3))
+        divtau.append(t)
+        out[1 + i] = t
+    k = mu * cp / Pr
+    dk = [cp / Pr * dmu[j] for j in range(3)]
+    out[4] = (sum(divtau[i] * vel[i] for i in range(3))
+              + mu * sum(A[i][j] * G[i][j] for i in range(3) for j in range(3))
+              + k * (d2T[0] + d2T[1] + d2T[2]) + sum(dk[j] * dT[j] for j in range(3)))
+    return out
+
+
+def mms_source(x, y, z, gamma: float = GAMMA, table=None) -> np.ndarray:
     """Source S = div F(Q_exact) of the steady Euler equations for the
     manufactured fields, by the chain rule on the analytic gradients.  This is
     the manufactured PDE's own right-hand side (Section 2: S may come from the
     method of manufactured solutions), a property of the problem, not of the
     discretisation."""
-    P, Dx, Dy, Dz = mms_primitives(x, y, z)
+    P, Dx, Dy, Dz = mms_primitives(x, y, z, table)
     rho, u, v, w, p = P
     vel = (u, v, w)
     q2 = u * u + v * v + w * w
@@ -189,20 +257,58 @@ def mms_3d(n=128, curvilinear: bool = True, amp: float = 0.1, cfl: float = 0.5,
     """3D manufactured-solution block on [0,1]^3 (perturbed-curvilinear when
     ``curvilinear``).  Initial state and all ghost cells (fixed, Dirichlet) hold
     the exact fields at the cell sampling points; the source is the
-    manufactured S at the interior sampling points (per unit volume)."""
+    manufactured S at the interior sampling points (per unit volume), of the
+    Euler equations, or of the laminar Navier-Stokes equations when the
+    parameters set visc = 1."""
     b, padded = _mms_block(n, curvilinear, amp)
     pts = _cell_points(padded)                       # ghosted cell points
     P, _, _, _ = mms_primitives(pts[..., 0], pts[..., 1], pts[..., 2])
     q = prim_to_cons(P)
     g = GHOST
     src = None
+    params = default_params(**param_over)
     if with_source:
         ip = pts[g:g + b.nk, g:g + b.nj, g:g + b.ni]
-        src = [np.ascontiguousarray(mms_source(ip[..., 0], ip[..., 1], ip[..., 2]))]
+        S = mms_source(ip[..., 0], ip[..., 1], ip[..., 2])
+        if params["visc"]:
+            S = S - mms_viscous_divergence(ip[..., 0], ip[..., 1], ip[..., 2], params)
+        src = [np.ascontiguousarray(S)]
     interior = P[:, g:g + b.nk, g:g + b.nj, g:g + b.ni]
     dt = nominal_dt([interior], [(1.0 / b.ni, 1.0 / b.nj, 1.0 / b.nk)], cfl, 3)
-    name = "mms_3d_%s%s" % ("x".join(map(str, (b.ni, b.nj, b.nk))), "_curv" if curvilinear else "")
-    return Problem([b], [], 3, pack_state([b], [q]), src, dt, default_params(**param_over), name)
+    name = "mms_3d_%s%s%s" % ("x".join(map(str, (b.ni, b.nj, b.nk))), "_curv" if curvilinear else "",
+                              "_ns" if params["visc"] else "")
+    return Problem([b], [], 3, pack_state([b], [q]), src, dt, params, name)
+
+
+def mms_periodic_3d(n=64, curvilinear: bool = True, amp: float = 0.1, cfl: float = 0.5,
+                    with_source: bool = True, **param_over) -> Problem:
+    """Manufactured solution with 1-periodic fields (wave numbers 2 pi and
+    4 pi) on the periodic unit cube, perturbed-curvilinear when
+    ``curvilinear`` (the perturbation is periodic too).  Ghost cells come from
+    the periodic connections, so every ghost value and the geometry behind it
+    are those of real neighbour cells.  Initial state = the exact fields at
+    the cell sampling points; source = the manufactured S (Euler, or laminar
+    Navier-Stokes when visc = 1) there."""
+    b, padded = _mms_block(n, curvilinear, amp)
+    pts = _cell_points(padded)
+    P, _, _, _ = mms_primitives(pts[..., 0], pts[..., 1], pts[..., 2], _MMS_PERIODIC)
+    q = prim_to_cons(P)
+    g = GHOST
+    params = default_params(**param_over)
+    src = None
+    ip = pts[g:g + b.nk, g:g + b.nj, g:g + b.ni]
+    if with_source:
+        S = mms_source(ip[..., 0], ip[..., 1], ip[..., 2], table=_MMS_PERIODIC)
+        if params["visc"]:
+            S = S - mms_viscous_divergence(ip[..., 0], ip[..., 1], ip[..., 2], params, _MMS_PERIODIC)
+        src = [np.ascontiguousarray(S)]
+    interior = P[:, g:g + b.nk, g:g + b.nj, g:g + b.ni]
+    dt = nominal_dt([interior], [(1.0 / b.ni, 1.0 / b.nj, 1.0 / b.nk)], cfl, 3)
+    if params["visc"] and params["mu"] > 0:
+        h = 1.0 / max(b.ni, b.nj, b.nk)
+        dt = min(dt, 0.4 * cfl * h * h * float(interior[0].min()) / params["mu"])
+    name = "mms_periodic_%d%s%s" % (b.ni, "_curv" if curvilinear else "", "_ns" if params["visc"] else "")
+    return Problem([b], periodic_connections(0, b), 3, pack_state([b], [q]), src, dt, params, name)
 
 
 def uniform_3d(n=16, curvilinear: bool = True, amp: float = 0.1, seed: Optional[int] = None,

@@ -71,6 +71,10 @@ def lib():
         L.oracle_bc_fill.argtypes = [_dp] + [ctypes.c_int] * 3 + [_dp] * 3 + [ctypes.c_int] * 6 + [_dp, _dp]
         L.oracle_farfield_state.argtypes = [ctypes.c_double] + [_dp] * 4
         L.oracle_wall_flux.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.oracle_edge_fill.argtypes = [ctypes.c_int, _ip, _ip, _lp, ctypes.c_int, ctypes.c_int, _dp]
+        L.oracle_residual_ns.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 7 + [
+            ctypes.c_char_p, _dp]
+        L.oracle_viscous_face.argtypes = [_dp, _dp, _dp, ctypes.c_int, _dp, _dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -97,7 +101,9 @@ def set_threads(n: int) -> None:
 def params_array(params: dict, dim: int) -> np.ndarray:
     return np.array([params["gamma"], params["eps"], params["kappa"], params["limiter"],
                      params["harten"], params["fix_all"], params["va_delta2"], dim,
-                     params.get("flux", 0)], dtype=np.float64)
+                     params.get("flux", 0), params.get("visc", 0), params.get("mu", 0.0),
+                     params.get("prandtl", 0.72), params.get("r_gas", 1.0), params.get("sutherland", 0),
+                     params.get("t_ref", 273.15), params.get("s_suth", 110.4)], dtype=np.float64)
 
 
 # ---------------------------------------------------------------------------
@@ -162,6 +168,18 @@ def wall_flux(p1: float, p2: float, S) -> np.ndarray:
     return out
 
 
+def viscous_face(params: dict, V10, geo2, axis: int, S, dim: int = 3) -> np.ndarray:
+    """Viscous flux times area of one face from its stencil: V10 = primitives
+    (10 x 5) of L, R, L-b, L+b, R-b, R+b, L-c, L+c, R-c, R+c; geo2 = (Omega,
+    Sbar_xi, Sbar_eta, Sbar_zeta) of L and R (2 x 10)."""
+    out = np.zeros(5)
+    pa = params_array(params, dim)
+    lib().oracle_viscous_face(_p(pa), _p(np.ascontiguousarray(V10, dtype=np.float64)),
+                              _p(np.ascontiguousarray(geo2, dtype=np.float64)), int(axis),
+                              _p(np.ascontiguousarray(S, dtype=np.float64)), _p(out))
+    return out
+
+
 def face_opcount(params: dict) -> dict:
     """Operation counts of one face (5 reconstructed components + Roe flux)."""
     rng = np.random.default_rng(0)
@@ -222,7 +240,7 @@ class Oracle:
             maps = [np.zeros(sz, dtype=np.int8) for sz in sizes]
             any_code = False
             for pt in self.bcs:
-                if pt.block != n or pt.kind not in (cases.BC_SLIP_WALL, cases.BC_FARFIELD):
+                if pt.block != n or pt.kind not in (cases.BC_SLIP_WALL, cases.BC_FARFIELD, cases.BC_NOSLIP_WALL):
                     continue
                 ext0 = b.nj if pt.face < 2 else b.ni
                 m = maps[pt.face]
@@ -230,6 +248,72 @@ class Oracle:
                     m[t1 * ext0 + pt.lo[0]:t1 * ext0 + pt.hi[0]] = pt.kind
                 any_code = True
             self.codes.append(np.ascontiguousarray(np.concatenate(maps)) if any_code else None)
+        self.visc = bool(self.params.get("visc", 0))
+        self.geo = self._aux_geometry() if self.visc else None
+
+    # -- viscous geometry -----------------------------------------------------
+    def _aux_geometry(self) -> List[np.ndarray]:
+        """Per block, the auxiliary-volume geometry of every cell of the block
+        padded by one layer: (10, nk+2, nj+2, ni+2) = Omega, Sbar_xi,
+        Sbar_eta, Sbar_zeta (cell-averaged face vectors).  Ghost cells of a
+        connected face take the donor cell's geometry with its face families
+        mapped to this block's axes (sign flipped where an index direction
+        reverses); other ghost cells copy the adjacent interior cell."""
+        geos = []
+        for n, b in enumerate(self.blocks):
+            Sxi, Seta, Szeta, vol = self.metrics[n]
+            G = np.zeros((10, b.nk + 2, b.nj + 2, b.ni + 2))
+            I = (slice(1, b.nk + 1), slice(1, b.nj + 1), slice(1, b.ni + 1))
+            G[(0,) + I] = vol
+            G[(slice(1, 4),) + I] = 0.5 * (Sxi[..., :-1] + Sxi[..., 1:])
+            G[(slice(4, 7),) + I] = 0.5 * (Seta[:, :, :-1, :] + Seta[:, :, 1:, :])
+            G[(slice(7, 10),) + I] = 0.5 * (Szeta[:, :-1] + Szeta[:, 1:])
+            # face ghosts: copies of the adjacent interior cell
+            G[:, 1:-1, 1:-1, 0] = G[:, 1:-1, 1:-1, 1]
+            G[:, 1:-1, 1:-1, -1] = G[:, 1:-1, 1:-1, -2]
+            G[:, 1:-1, 0, 1:-1] = G[:, 1:-1, 1, 1:-1]
+            G[:, 1:-1, -1, 1:-1] = G[:, 1:-1, -2, 1:-1]
+            G[:, 0, 1:-1, 1:-1] = G[:, 1, 1:-1, 1:-1]
+            G[:, -1, 1:-1, 1:-1] = G[:, -2, 1:-1, 1:-1]
+            geos.append(G)
+        for c in self.pb.conns:
+            db, sbk = self.blocks[c.dst_block], self.blocks[c.src_block]
+            da, sa = c.dst_face // 2, c.src_face // 2
+            dext, sext = (db.ni, db.nj, db.nk), (sbk.ni, sbk.nj, sbk.nk)
+            dtan = [x for x in range(3) if x != da]
+            stan = [x for x in range(3) if x != sa]
+            # family of the donor and sign for each of this block's axes
+            fam, sgn = [0, 0, 0], [1.0, 1.0, 1.0]
+            fam[da] = sa
+            sgn[da] = 1.0 if (c.dst_face % 2) != (c.src_face % 2) else -1.0
+            for t in range(2):
+                fam[dtan[t]] = stan[abs(c.transform[t]) - 1]
+                sgn[dtan[t]] = 1.0 if c.transform[t] > 0 else -1.0
+            Gd, Gs = geos[c.dst_block], geos[c.src_block]
+            for bb in range(c.dst_hi[1] - c.dst_lo[1]):
+                for aa in range(c.dst_hi[0] - c.dst_lo[0]):
+                    dc = [0, 0, 0]
+                    dc[dtan[0]], dc[dtan[1]] = c.dst_lo[0] + aa, c.dst_lo[1] + bb
+                    dc[da] = -1 if c.dst_face % 2 == 0 else dext[da]
+                    st = [c.src_lo[0], c.src_lo[1]]
+                    st[abs(c.transform[0]) - 1] += aa if c.transform[0] > 0 else -aa
+                    st[abs(c.transform[1]) - 1] += bb if c.transform[1] > 0 else -bb
+                    sc = [0, 0, 0]
+                    sc[stan[0]], sc[stan[1]] = st[0], st[1]
+                    sc[sa] = 0 if c.src_face % 2 == 0 else sext[sa] - 1
+                    src = Gs[:, sc[2] + 1, sc[1] + 1, sc[0] + 1]
+                    dst = Gd[:, dc[2] + 1, dc[1] + 1, dc[0] + 1]
+                    dst[0] = src[0]
+                    for d in range(3):
+                        dst[1 + 3 * d:4 + 3 * d] = sgn[d] * src[1 + 3 * fam[d]:4 + 3 * fam[d]]
+        return [np.ascontiguousarray(G) for G in geos]
+
+    def edge_fill(self, q: np.ndarray) -> np.ndarray:
+        """Depth-1 edge ghosts (connection extensions, else the mean of the two
+        face-adjacent ghosts), in place."""
+        lib().oracle_edge_fill(len(self.conns), _p(self.conns) if len(self.conns) else None, _p(self.dims),
+                               _p(self.offs), self.dim, len(self.blocks), _p(q))
+        return q
 
     # -- pieces ---------------------------------------------------------------
     def block_view(self, q: np.ndarray, n: int) -> np.ndarray:
@@ -258,8 +342,10 @@ class Oracle:
         return q
 
     def fill_ghosts(self, q: np.ndarray) -> np.ndarray:
-        """Connected-boundary exchange, then the physical boundaries."""
-        return self.apply_bcs(self.exchange(q))
+        """Connected-boundary exchange, then the physical boundaries, then
+        (laminar terms on) the edge ghosts."""
+        q = self.apply_bcs(self.exchange(q))
+        return self.edge_fill(q) if self.visc else q
 
     def residual(self, q: np.ndarray) -> np.ndarray:
         """Residual of every block of the packed state ``q`` as it stands
@@ -270,7 +356,11 @@ class Oracle:
             qb = np.ascontiguousarray(self.block_view(q, n))
             src = None if self.src is None else np.ascontiguousarray(self.src[n], dtype=np.float64)
             Rb = np.zeros(5 * self.ncell[n])
-            if self.codes[n] is not None:
+            if self.visc:
+                codes = None if self.codes[n] is None else self.codes[n].ctypes.data_as(ctypes.c_char_p)
+                lib().oracle_residual_ns(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), _p(vol),
+                                         _p(self.geo[n]), _p(qb), _p(src), codes, _p(Rb))
+            elif self.codes[n] is not None:
                 lib().oracle_residual_bc(_p(self.pa), b.ni, b.nj, b.nk, _p(Sxi), _p(Seta), _p(Szeta), _p(vol),
                                          _p(qb), _p(src), self.codes[n].ctypes.data_as(ctypes.c_char_p), _p(Rb))
             else:
@@ -282,8 +372,8 @@ class Oracle:
     def residual_jvp(self, q: np.ndarray, dq: np.ndarray):
         """(R, dR) with dR = dR/dq . dq by dual numbers (ghosts as they stand;
         no overwritten boundary faces)."""
-        if any(c is not None for c in self.codes):
-            raise NotImplementedError("residual_jvp: wall/farfield face overwrites are not linearised")
+        if any(c is not None for c in self.codes) or self.visc:
+            raise NotImplementedError("residual_jvp: boundary overwrites and viscous terms are not linearised")
         R = np.zeros(int(self.roffs[-1]))
         dR = np.zeros_like(R)
         for n, b in enumerate(self.blocks):

@@ -108,6 +108,11 @@ struct Params {
   double va_delta2;   // van Albada smoothing delta^2
   int dim;            // 2 or 3
   int flux;           // 0 Roe, 1 van Leer flux-vector splitting, 2 Steger-Warming
+  int visc;           // 1: laminar viscous flux (Section 2)
+  double mu;          // viscosity (constant), or mu(t_ref) under Sutherland's law
+  double prandtl, r_gas;
+  int sutherland;
+  double t_ref, s_suth;
 };
 
 Params unpack(const double* p) {
@@ -115,6 +120,8 @@ Params unpack(const double* p) {
   q.gamma = p[0]; q.eps = p[1]; q.kappa = p[2]; q.limiter = (int)p[3];
   q.harten = p[4]; q.fix_all = (int)p[5]; q.va_delta2 = p[6]; q.dim = (int)p[7];
   q.flux = (int)p[8];
+  q.visc = (int)p[9]; q.mu = p[10]; q.prandtl = p[11]; q.r_gas = p[12];
+  q.sutherland = (int)p[13]; q.t_ref = p[14]; q.s_suth = p[15];
   return q;
 }
 
@@ -366,7 +373,8 @@ inline void cross_half(const double* xa, const double* xb, const double* xc, con
 }
 
 // Physical boundary kinds (codes shared with the boundary tables).
-enum { BC_FIXED = 0, BC_SUPERSONIC_INFLOW = 1, BC_EXTRAPOLATE = 2, BC_SLIP_WALL = 3, BC_FARFIELD = 4 };
+enum { BC_FIXED = 0, BC_SUPERSONIC_INFLOW = 1, BC_EXTRAPOLATE = 2, BC_SLIP_WALL = 3, BC_FARFIELD = 4,
+       BC_NOSLIP_WALL = 5 };
 
 // Slip-wall face flux (Section 7.2, V7): pressure only, p_w S.
 template <class T>
@@ -387,6 +395,82 @@ void farfield_flux(const Params& P, const T Vb[5], const double S[3], T out[5]) 
   for (int n = 0; n < 5; ++n) out[n] = out[n] * T(a);
 }
 
+// ---------------------------------------------------------------------------
+// Laminar viscous flux (Section 2): F_v.n = (0, tau.n, Theta.n) with tau by
+// Stokes's hypothesis and Theta = tau.u + k grad T (heat conduction and the
+// work of the viscous stresses), k = mu c_p / Pr, c_p = gamma R/(gamma-1),
+// T = p / (rho R); mu constant or by Sutherland's law.  Face gradients by
+// Green's theorem over the auxiliary volume between the two cell centres
+// (Section 2: "a Green's theorem approach" with a wider stencil).
+// ---------------------------------------------------------------------------
+template <class T>
+T viscosity(const Params& P, T temp) {
+  if (!P.sutherland) return T(P.mu);
+  const T tr = temp / T(P.t_ref);
+  return T(P.mu) * tr * sqrt_(tr) * T(P.t_ref + P.s_suth) / (temp + T(P.s_suth));
+}
+
+// Cell geometry of the auxiliary volumes: per cell of the block padded by one
+// layer, Omega and the cell-averaged face vectors Sbar_d = (S_d,lo + S_d,hi)/2
+// of the three face families; 10 planes of (ni+2)(nj+2)(nk+2) values.
+struct Geo {
+  const double* g;
+  long np;                 // cells per plane
+  int pi, pj;              // padded extents in i, j
+  long at(int i, int j, int k) const { return ((long)(k + 1) * pj + (j + 1)) * pi + (i + 1); }
+};
+
+// Viscous flux times area of the face between cells L and R along axis a
+// (cL, cR: ghosted state indices; sb, sc: ghosted strides of the tangential
+// axes b, c; gL, gR: padded geometry indices), primitives V.
+template <class T>
+void viscous_face(const Params& P, const Blk& B, const std::vector<T>& V, const Geo& G, long cL, long cR, long sb,
+                  long sc, long gL, long gR, int a, int b, int c, const double S[3], T out[5]) {
+  const double R = P.r_gas;
+  auto temp = [&](long x) { return V[4 * B.plane + x] / (V[x] * T(R)); };
+  auto phi = [&](int m, long x) { return m < 3 ? V[(1 + m) * B.plane + x] : temp(x); };
+  // auxiliary volume: Omega_f and the face vectors of its three families
+  const double Om = 0.5 * (G.g[gL] + G.g[gR]);
+  double A[3][3];
+  for (int d = 0; d < 3; ++d)
+    for (int x = 0; x < 3; ++x) A[d][x] = 0.5 * (G.g[(1 + 3 * d + x) * G.np + gL] + G.g[(1 + 3 * d + x) * G.np + gR]);
+  // gradients of u, v, w, T
+  T grad[4][3];
+  for (int m = 0; m < 4; ++m) {
+    const T da = phi(m, cR) - phi(m, cL);
+    const T db = T(0.25) * ((phi(m, cL + sb) - phi(m, cL - sb)) + (phi(m, cR + sb) - phi(m, cR - sb)));
+    T dc = T(0.0);
+    if (P.dim == 3) dc = T(0.25) * ((phi(m, cL + sc) - phi(m, cL - sc)) + (phi(m, cR + sc) - phi(m, cR - sc)));
+    for (int x = 0; x < 3; ++x) {
+      T gx = da * T(A[a][x]) + db * T(A[b][x]);
+      if (P.dim == 3) gx = gx + dc * T(A[c][x]);
+      grad[m][x] = gx / T(Om);
+    }
+  }
+  // face values
+  T uf[3];
+  for (int x = 0; x < 3; ++x) uf[x] = T(0.5) * (V[(1 + x) * B.plane + cL] + V[(1 + x) * B.plane + cR]);
+  const T Tf = T(0.5) * (temp(cL) + temp(cR));
+  const T mu = viscosity(P, Tf);
+  const T kcond = mu * T(P.gamma * R / (P.gamma - 1.0) / P.prandtl);
+  const T div = grad[0][0] + grad[1][1] + grad[2][2];
+  T tau[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) {
+      T t = grad[x][y] + grad[y][x];
+      if (x == y) t = t - T(2.0 / 3.0) * div;
+      tau[x][y] = mu * t;
+    }
+  out[0] = T(0.0);
+  T energy = T(0.0);
+  for (int x = 0; x < 3; ++x) {
+    const T f = tau[x][0] * T(S[0]) + tau[x][1] * T(S[1]) + tau[x][2] * T(S[2]);
+    out[1 + x] = f;
+    energy = energy + f * uf[x];
+  }
+  out[4] = energy + kcond * (grad[3][0] * T(S[0]) + grad[3][1] * T(S[1]) + grad[3][2] * T(S[2]));
+}
+
 // bcode: the six face maps of the block (imin, imax, jmin, jmax, kmin, kmax;
 // each indexed by the two tangential cell indices in (i,j,k) order, first
 // fastest) or nullptr; a slip-wall or farfield code replaces that boundary
@@ -394,7 +478,7 @@ void farfield_flux(const Params& P, const T Vb[5], const double S[3], T out[5]) 
 template <class T>
 void residual_block(const Params& P, const Blk& B, const double* Sxi, const double* Seta,
                     const double* Szeta, const double* vol, const T* q, const double* src, T* R,
-                    const signed char* const* bcode = nullptr) {
+                    const signed char* const* bcode = nullptr, const double* geo = nullptr) {
   const int ni = B.ni, nj = B.nj, nk = B.nk;
   // primitives of every cell, ghosts included
   std::vector<T> V(5 * B.plane);
@@ -426,7 +510,7 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
                   int side) {
     T out[5];
     double S[3] = {Sarr[fidx], Sarr[nfaces + fidx], Sarr[2 * nfaces + fidx]};
-    if (code == BC_SLIP_WALL) {
+    if (code == BC_SLIP_WALL || code == BC_NOSLIP_WALL) {
       const long c1 = side == 0 ? cm2 + 2 * stride : cm2 + stride;
       const long c2 = side == 0 ? cm2 + 3 * stride : cm2;
       wall_flux(V[4 * B.plane + c1], V[4 * B.plane + c2], S, out);
@@ -472,7 +556,46 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
           face(B.at(i, j, k - 2), B.sz, Szeta, n_zeta, f, Fz.data(), code, k == 0 ? 0 : 1);
         }
   }
-  // Eq. (governing), discretely: R = sum over faces of F^ |S| (outward) - S Omega
+  // viscous face fluxes (each face once), when the laminar terms are on
+  std::vector<T> Vx, Vy, Vz;
+  const bool visc = P.visc && geo;
+  if (visc) {
+    Vx.assign(5 * n_xi, T(0.0));
+    Vy.assign(5 * n_eta, T(0.0));
+    if (P.dim == 3) Vz.assign(5 * n_zeta, T(0.0));
+    Geo Gm{geo, (long)(ni + 2) * (nj + 2) * (nk + 2), ni + 2, nj + 2};
+    auto vface = [&](int a, int i, int j, int k, long nfaces, long fidx, const double* Sarr, T* F) {
+      // cells L (one step back along a) and R = (i, j, k)
+      const long sa = a == 0 ? B.sx : (a == 1 ? B.sy : B.sz);
+      const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+      const long sb = b == 0 ? B.sx : B.sy, sc = c == 1 ? B.sy : B.sz;
+      const long cR = B.at(i, j, k), cL = cR - sa;
+      const long gR = Gm.at(i, j, k);
+      const long gL = gR - (a == 0 ? 1 : (a == 1 ? (long)(ni + 2) : (long)(ni + 2) * (nj + 2)));
+      double S[3] = {Sarr[fidx], Sarr[nfaces + fidx], Sarr[2 * nfaces + fidx]};
+      T out[5];
+      viscous_face(P, B, V, Gm, cL, cR, sb, sc, gL, gR, a, b, c, S, out);
+      for (int n = 0; n < 5; ++n) F[n * nfaces + fidx] = out[n];
+    };
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nk; ++k)
+      for (int j = 0; j < nj; ++j)
+        for (int i = 0; i <= ni; ++i) vface(0, i, j, k, n_xi, ((long)k * nj + j) * nfx + i, Sxi, Vx.data());
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nk; ++k)
+      for (int j = 0; j <= nj; ++j)
+        for (int i = 0; i < ni; ++i) vface(1, i, j, k, n_eta, ((long)k * nfy + j) * ni + i, Seta, Vy.data());
+    if (P.dim == 3) {
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k <= nk; ++k)
+        for (int j = 0; j < nj; ++j)
+          for (int i = 0; i < ni; ++i) vface(2, i, j, k, n_zeta, ((long)k * nj + j) * ni + i, Szeta, Vz.data());
+    }
+  }
+
+  // Eq. (governing), discretely: R = sum over faces of (F_i - F_v) |S|
+  // (outward) - S Omega; per cell the inviscid pairs (xi, eta, zeta), then
+  // the viscous pairs, then the source
   const long ncell = (long)ni * nj * nk;
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nk; ++k)
@@ -486,6 +609,11 @@ void residual_block(const Params& P, const Blk& B, const double* Sxi, const doub
           T r = (Fx[n * n_xi + fx + 1] - Fx[n * n_xi + fx]) +
                 (Fy[n * n_eta + fy + ni] - Fy[n * n_eta + fy]);
           if (P.dim == 3) r = r + (Fz[n * n_zeta + fz + (long)ni * nj] - Fz[n * n_zeta + fz]);
+          if (visc) {
+            T rv = (Vx[n * n_xi + fx + 1] - Vx[n * n_xi + fx]) + (Vy[n * n_eta + fy + ni] - Vy[n * n_eta + fy]);
+            if (P.dim == 3) rv = rv + (Vz[n * n_zeta + fz + (long)ni * nj] - Vz[n * n_zeta + fz]);
+            r = r - rv;
+          }
           if (src) r = r - T(src[n * ncell + c] * vol[c]);
           R[n * ncell + c] = r;
         }
@@ -619,6 +747,14 @@ void bc_fill_patch(const Params& P, const Blk& B, const double* Sface, int bf, i
           for (int v = 0; v < 5; ++v) q[v * B.plane + gi] = q[v * B.plane + i1];
         } else if (kind == BC_FARFIELD) {
           for (int v = 0; v < 5; ++v) q[v * B.plane + gi] = qb[v];
+        } else if (kind == BC_NOSLIP_WALL) {
+          // adiabatic no-slip wall: the mirrored cell with its velocity reversed
+          int cm[3] = {c[0], c[1], c[2]};
+          cm[ax] = side == 0 ? d - 1 : ext[ax] - d;
+          const long mi = B.at(cm[0], cm[1], cm[2]);
+          q[gi] = q[mi];
+          for (int x = 1; x <= 3; ++x) q[x * B.plane + gi] = -q[x * B.plane + mi];
+          q[4 * B.plane + gi] = q[4 * B.plane + mi];
         } else if (kind == BC_SLIP_WALL) {
           // mirror of the interior cell at the same depth, normal momentum reflected
           int cm[3] = {c[0], c[1], c[2]};
@@ -634,9 +770,153 @@ void bc_fill_patch(const Params& P, const Blk& B, const double* Sface, int bf, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Edge ghosts (Section 4 of the paper's GPU history: the corner and edge
+// update), needed by the viscous stencil's tangential differences on a
+// block's boundary faces: the cells with two ghost coordinates at depth 1.
+// An edge cell takes the donor's cell when a connection of one of its two
+// faces, extended by one cell along the face, reaches it (connections of the
+// lower-numbered axis first, in table order); otherwise the mean of its two
+// face-adjacent ghost cells.
+// ---------------------------------------------------------------------------
+
+// donor cell of dst tangential coordinates (u0, u1) (patch offsets may fall
+// one cell outside the patch) at depth 1 of connection c; false if c does not
+// belong to dst face df
+bool conn_donor(const int* dims, const int* c, int df, int u0, int u1, int* sb, int* sc) {
+  int dlo0 = c[2], dlo1 = c[3];
+  int sbk = c[6], sf = c[7], slo0 = c[8], slo1 = c[9], t0 = c[10], t1 = c[11];
+  if (c[1] != df) return false;
+  const int a = u0 - dlo0, b = u1 - dlo1;
+  const int sa = sf / 2;
+  int stan[2], m = 0;
+  for (int x = 0; x < 3; ++x)
+    if (x != sa) stan[m++] = x;
+  int st[2] = {slo0, slo1};
+  st[std::abs(t0) - 1] += (t0 > 0 ? a : -a);
+  st[std::abs(t1) - 1] += (t1 > 0 ? b : -b);
+  const int sext[3] = {dims[3 * sbk], dims[3 * sbk + 1], dims[3 * sbk + 2]};
+  sc[stan[0]] = st[0];
+  sc[stan[1]] = st[1];
+  sc[sa] = (sf % 2 == 0) ? 0 : sext[sa] - 1;
+  *sb = sbk;
+  return true;
+}
+
+void edge_fill(int nconn, const int* conns, const int* dims, const long* offs, int dim, double* q, int nblocks) {
+  for (int bk = 0; bk < nblocks; ++bk) {
+    Blk B(dims[3 * bk], dims[3 * bk + 1], dims[3 * bk + 2]);
+    const int ext[3] = {B.ni, B.nj, B.nk};
+    double* qb = q + offs[bk];
+    const int npairs = dim == 3 ? 3 : 1;
+    const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int pr = 0; pr < npairs; ++pr) {
+      const int a = pairs[pr][0], b = pairs[pr][1], cx = 3 - a - b;
+      const int nc = dim == 3 ? ext[cx] : 1;
+      for (int sa = 0; sa < 2; ++sa)
+        for (int sb = 0; sb < 2; ++sb)
+          for (int t = 0; t < nc; ++t) {
+            int e[3];
+            e[a] = sa ? ext[a] : -1;
+            e[b] = sb ? ext[b] : -1;
+            e[cx] = t;
+            bool done = false;
+            // connections of face (a, sa) extended along b, then of (b, sb) along a
+            for (int pass = 0; pass < 2 && !done; ++pass) {
+              const int fa = pass == 0 ? a : b;          // the face's normal axis
+              const int face = 2 * fa + (pass == 0 ? sa : sb);
+              int tan[2], m = 0;
+              for (int x = 0; x < 3; ++x)
+                if (x != fa) tan[m++] = x;
+              const int u0 = e[tan[0]], u1 = e[tan[1]];
+              for (int cn = 0; cn < nconn && !done; ++cn) {
+                const int* c = conns + 12 * cn;
+                if (c[0] != bk || c[1] != face) continue;
+                // the patch extended by one cell along the other edge axis
+                int lo[2] = {c[2], c[3]}, hi[2] = {c[4], c[5]};
+                const int other = pass == 0 ? b : a;
+                for (int x = 0; x < 2; ++x)
+                  if (tan[x] == other) { lo[x] -= 1; hi[x] += 1; }
+                if (u0 < lo[0] || u0 >= hi[0] || u1 < lo[1] || u1 >= hi[1]) continue;
+                int sbk, sc[3];
+                conn_donor(dims, c, face, u0, u1, &sbk, sc);
+                Blk S(dims[3 * sbk], dims[3 * sbk + 1], dims[3 * sbk + 2]);
+                const double* qs = q + offs[sbk];
+                const long di = B.at(e[0], e[1], e[2]), si = S.at(sc[0], sc[1], sc[2]);
+                for (int v = 0; v < 5; ++v) qb[v * B.plane + di] = qs[v * S.plane + si];
+                done = true;
+              }
+            }
+            if (!done) {
+              int f1[3] = {e[0], e[1], e[2]}, f2[3] = {e[0], e[1], e[2]};
+              f1[b] = sb ? ext[b] - 1 : 0;      // ghost of face (a, sa)
+              f2[a] = sa ? ext[a] - 1 : 0;      // ghost of face (b, sb)
+              const long di = B.at(e[0], e[1], e[2]), i1 = B.at(f1[0], f1[1], f1[2]), i2 = B.at(f2[0], f2[1], f2[2]);
+              for (int v = 0; v < 5; ++v)
+                qb[v * B.plane + di] = 0.5 * (qb[v * B.plane + i1] + qb[v * B.plane + i2]);
+            }
+          }
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+// Edge-ghost fill of the packed state (in place), after the connections and
+// the physical boundaries.
+void oracle_edge_fill(int nconn, const int* conns, const int* dims, const long* offs, int dim, int nblocks,
+                      double* q) {
+  edge_fill(nconn, conns, dims, offs, dim, q, nblocks);
+}
+
+// Residual with the laminar viscous terms: geo is the block's padded
+// auxiliary-volume geometry (10 planes of (ni+2)(nj+2)(nk+2): Omega, Sbar_xi,
+// Sbar_eta, Sbar_zeta), codes as for oracle_residual_bc or NULL.
+void oracle_residual_ns(const double* params, int ni, int nj, int nk, const double* Sxi, const double* Seta,
+                        const double* Szeta, const double* vol, const double* geo, const double* q,
+                        const double* src, const signed char* codes, double* R) {
+  Params P = unpack(params);
+  Blk B(ni, nj, nk);
+  const signed char* maps[6];
+  const long sz[6] = {(long)nj * nk, (long)nj * nk, (long)ni * nk, (long)ni * nk, (long)ni * nj, (long)ni * nj};
+  long o = 0;
+  for (int f = 0; f < 6; ++f) { maps[f] = codes ? codes + o : nullptr; o += sz[f]; }
+  residual_block<double>(P, B, Sxi, Seta, Szeta, vol, q, src, R, codes ? maps : nullptr, geo);
+}
+
+// Viscous flux of one face from explicit stencil data, for the closed-form
+// checks: V10 = primitives of L, R, L-b, L+b, R-b, R+b, L-c, L+c, R-c, R+c
+// (10 x 5), geo2 = Omega, Sbar_xi, Sbar_eta, Sbar_zeta of L then R (2 x 10),
+// a = the face's axis, S = its area vector.
+void oracle_viscous_face(const double* params, const double* V10, const double* geo2, int a, const double* S,
+                         double* out) {
+  Params P = unpack(params);
+  // a tiny block holding the 10 cells at the offsets the stencil uses
+  Blk B(5, 5, 5);
+  std::vector<double> V(5 * B.plane, 0.0);
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  int L[3] = {2, 2, 2}, Rc[3] = {2, 2, 2};
+  Rc[a] = 3;
+  auto put = [&](int slot, const int* cc, int db, int dc) {
+    int x[3] = {cc[0], cc[1], cc[2]};
+    x[b] += db;
+    x[c] += dc;
+    const long id = B.at(x[0], x[1], x[2]);
+    for (int n = 0; n < 5; ++n) V[n * B.plane + id] = V10[5 * slot + n];
+  };
+  put(0, L, 0, 0); put(1, Rc, 0, 0);
+  put(2, L, -1, 0); put(3, L, 1, 0); put(4, Rc, -1, 0); put(5, Rc, 1, 0);
+  put(6, L, 0, -1); put(7, L, 0, 1); put(8, Rc, 0, -1); put(9, Rc, 0, 1);
+  std::vector<double> g(20);
+  for (int x = 0; x < 10; ++x) { g[2 * x] = geo2[x]; g[2 * x + 1] = geo2[10 + x]; }
+  Geo G{g.data(), 2, 2, 1};
+  const long sa = a == 0 ? B.sx : (a == 1 ? B.sy : B.sz);
+  const long sb = b == 0 ? B.sx : B.sy, sc = c == 1 ? B.sy : B.sz;
+  const long cL = B.at(L[0], L[1], L[2]);
+  viscous_face(P, B, V, G, cL, cL + sa, sb, sc, 0, 1, a, b, c, S, out);
+}
 
 void oracle_set_threads(int n) {
 #ifdef _OPENMP
