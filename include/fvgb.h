@@ -16,7 +16,12 @@
  *     supersonic inflow, extrapolated outflow, farfield), Section 2 and
  *     Section 7.2 (V2/V3), with the wall and farfield face fluxes overwritten
  *     after the enforcement, Section 7.2 (V7);
- *   - explicit M-step Runge-Kutta time marching, Section 2.
+ *   - explicit M-step Runge-Kutta time marching, Section 2;
+ *   - optionally the laminar viscous flux F_v of Section 2 (Stokes's-hypothesis
+ *     stresses, heat conduction and the work of the stresses), with face
+ *     gradients by Green's theorem over an auxiliary volume (a wider stencil
+ *     that needs the edge ghost cells, Section 2 and the corner/edge update
+ *     of Section 4).
  *
  * Conventions used by every call:
  *   - A block has interior cells i in [0,ni), j in [0,nj), k in [0,nk) and two
@@ -122,13 +127,19 @@ typedef struct {
  *     c_b = (gamma-1)(R+ - R-)/4 with R+ = V_n,i + 2 c_i/(gamma-1),
  *     R- = V_n,f - 2 c_f/(gamma-1), and the entropy p/rho^gamma and the
  *     tangential velocity of the upwind side.  The farfield face flux is
- *     overwritten with the physical flux F(V_b).S. */
+ *     overwritten with the physical flux F(V_b).S.
+ *   NOSLIP_WALL (adiabatic, for the viscous terms): ghost at depth d mirrors
+ *     the interior cell at depth d with its momentum reversed (m_g = -m;
+ *     density and total energy copied, so the temperature is mirrored); the
+ *     inviscid face flux is overwritten as for SLIP_WALL, the viscous flux is
+ *     evaluated from the ghosts. */
 typedef enum {
   FV_BC_FIXED = 0,
   FV_BC_SUPERSONIC_INFLOW = 1,
   FV_BC_EXTRAPOLATE = 2,
   FV_BC_SLIP_WALL = 3,
-  FV_BC_FARFIELD = 4
+  FV_BC_FARFIELD = 4,
+  FV_BC_NOSLIP_WALL = 5
 } fv_bc_kind;
 
 /* One physical boundary patch: face `face` (0..5) of block `block` over the
@@ -160,7 +171,21 @@ typedef struct {
  *     CTA slot); -w = about w tiles per resident CTA slot.  Tiles are handed
  *     to persistent CTAs largest first through a device counter.
  *   flux: fv_flux (Roe by default); van Leer F+- split by the normal Mach
- *     number, Steger-Warming by the eigenvalues; F^ = F+(V_L) + F-(V_R). */
+ *     number, Steger-Warming by the eigenvalues; F^ = F+(V_L) + F-(V_R).
+ *   visc: 1 adds the laminar viscous flux F_v.S = (0, tau.S, Theta.S),
+ *     tau = mu (grad u + grad u^T - 2/3 div u I), Theta = tau.u_f + k grad T,
+ *     k = mu c_p / prandtl, c_p = gamma r_gas / (gamma - 1), T = p/(rho r_gas);
+ *     mu constant (sutherland = 0) or mu (T/t_ref)^1.5 (t_ref + s_suth)/(T + s_suth).
+ *     Face values are the means of the two cells; the face gradient of
+ *     phi in (u, v, w, T) on the face between L and R along axis a is
+ *     [(phi_R - phi_L) A_a + D_b A_b + D_c A_c] / Omega_f with
+ *     D_b = ((phi_L,b+ - phi_L,b-) + (phi_R,b+ - phi_R,b-))/4, A_d the mean of
+ *     the two cells' averaged face vectors of family d and Omega_f the mean
+ *     volume (no c term in 2D).  Ghost cells of a connected face take the
+ *     donor cell's geometry, other ghosts that of the adjacent interior cell;
+ *     the depth-1 edge ghosts take the donor cell of a connection extended by
+ *     one cell along its face, else the mean of their two face-adjacent
+ *     ghosts.  R = sum of the inviscid pairs - sum of the viscous pairs - S Omega. */
 typedef struct {
   double gamma, eps, kappa, harten, va_delta2;
   int limiter, fix_all, dim, n_stages;
@@ -169,11 +194,17 @@ typedef struct {
   int tile;
   int kchunk;
   int flux;
+  int visc;
+  double mu, prandtl, r_gas;
+  int sutherland;
+  double t_ref, s_suth;
 } fv_config;
 
 /* Fill *cfg with the defaults: gamma 1.4, eps 1, kappa -1, van Leer,
  * harten 0.1, fix_all 0, va_delta2 1e-12, dim 3, 4 stages with
- * alpha = (1/4, 1/3, 1/2, 1), FV_PREC_FP64, automatic tiles, Roe flux. */
+ * alpha = (1/4, 1/3, 1/2, 1), FV_PREC_FP64, automatic tiles, Roe flux,
+ * inviscid (visc 0; for visc 1: prandtl 0.72, r_gas 287, t_ref 273.15,
+ * s_suth 110.4, mu to be set). */
 void fv_config_default(fv_config* cfg);
 
 /* Create the solver state on the current CUDA device: validates blocks and
@@ -251,9 +282,10 @@ int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
  * Q^(m) = Q^(0) - alpha_m dt / Omega R.
  * Buffers: stage 1 reads Q^(m-1) = Q^(0) from buffer 0; stage m < n_stages
  * writes buffer 1 when m is odd and buffer 2 when m is even; the last stage
- * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Up to
- * three kernel launches (connections, physical boundaries, fused residual +
- * update). */
+ * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Kernel
+ * launches: connections, physical boundaries, fused residual + update; with
+ * visc also the edge ghosts, the face variables (u, v, w, T) and one viscous
+ * face-flux launch per direction before the fused kernel. */
 int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
 
 /* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage
@@ -286,7 +318,7 @@ int fv_get_launch(fv_handle h, int* out4);
  * including the transpose of the exchange (ghost cotangents added into their
  * donor cells); lam_q0_dev (packed interior field) += lam_out.  qin_dev is
  * not modified.  Fixed ghost cells are constants.  Built for FV_PREC_FP64
- * handles with the Roe flux and no physical boundary patches
+ * handles with the Roe flux, no physical boundary patches and visc = 0
  * (FV_ERR_UNSUPPORTED otherwise). */
 int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
                    double* lam_in_dev, double* lam_q0_dev, void* stream);

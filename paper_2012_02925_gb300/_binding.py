@@ -56,7 +56,9 @@ class fv_config(ctypes.Structure):
                 ("limiter", ctypes.c_int), ("fix_all", ctypes.c_int), ("dim", ctypes.c_int),
                 ("n_stages", ctypes.c_int), ("alpha", ctypes.c_double * 8),
                 ("precision", ctypes.c_int), ("tile", ctypes.c_int), ("kchunk", ctypes.c_int),
-                ("flux", ctypes.c_int)]
+                ("flux", ctypes.c_int), ("visc", ctypes.c_int),
+                ("mu", ctypes.c_double), ("prandtl", ctypes.c_double), ("r_gas", ctypes.c_double),
+                ("sutherland", ctypes.c_int), ("t_ref", ctypes.c_double), ("s_suth", ctypes.c_double)]
 
 
 _lib = None
@@ -166,6 +168,14 @@ class Solver:
         cfg.limiter = int(params.get("limiter", 1))
         cfg.fix_all = int(params.get("fix_all", 0))
         cfg.flux = int(params.get("flux", 0))
+        cfg.visc = int(params.get("visc", 0))
+        if cfg.visc:
+            cfg.mu = float(params["mu"])
+            cfg.prandtl = float(params.get("prandtl", 0.72))
+            cfg.r_gas = float(params.get("r_gas", 287.0))
+            cfg.sutherland = int(params.get("sutherland", 0))
+            cfg.t_ref = float(params.get("t_ref", 273.15))
+            cfg.s_suth = float(params.get("s_suth", 110.4))
         cfg.dim = int(dim)
         alpha = params.get("alpha", (0.25, 1.0 / 3.0, 0.5, 1.0))
         cfg.n_stages = len(alpha)

@@ -53,6 +53,15 @@ struct fv_ctx {
   int nbc = 0;
   long long bc_items = 0;
   signed char* d_bcmap = nullptr;   // overwritten-flux face maps of all blocks
+  // laminar viscous terms
+  long long pad_total = 0;          // cells of all blocks padded by one layer
+  long long nvfaces[3] = {0, 0, 0}; // faces per direction, every block
+  double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total]
+  double* wvar = nullptr;           // face variables (u, v, w, T) [4][pad_total]
+  double* fvis[3] = {nullptr, nullptr, nullptr};  // viscous face fluxes [4][nvfaces[d]]
+  struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
+  EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
+  long long nedges = 0;
   int device = 0, nsm = 0;
   std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
   std::string err;
@@ -231,6 +240,7 @@ __global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvC
 // physical boundaries: work item = (patch, tangential a, b); both ghost
 // layers of that boundary position (Section 2; Section 7.2, V2/V3)
 // ---------------------------------------------------------------------------
+static_assert(FV_BCK_NOSLIP_WALL == FV_BC_NOSLIP_WALL, "boundary kinds");
 static_assert(FV_BCK_SLIP_WALL == FV_BC_SLIP_WALL && FV_BCK_FARFIELD == FV_BC_FARFIELD &&
                   FV_BCK_SUPERSONIC_INFLOW == FV_BC_SUPERSONIC_INFLOW && FV_BCK_EXTRAPOLATE == FV_BC_EXTRAPOLATE,
               "boundary kinds");
@@ -355,7 +365,15 @@ __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBc
 #pragma unroll
     for (int d = 1; d <= FV_GHOST; ++d) {
       const long long gi = at(side ? ext - 1 + d : -d);
-      if (P.kind == FV_BCK_SLIP_WALL) {
+      if (P.kind == FV_BCK_NOSLIP_WALL) {
+        // mirror of the interior cell at the same depth, momentum reversed
+        const long long mi = at(side ? ext - d : d - 1);
+        q[gi] = q[mi];
+        q[gi + B.plane] = -q[mi + B.plane];
+        q[gi + 2 * B.plane] = -q[mi + 2 * B.plane];
+        q[gi + 3 * B.plane] = -q[mi + 3 * B.plane];
+        q[gi + 4 * B.plane] = q[mi + 4 * B.plane];
+      } else if (P.kind == FV_BCK_SLIP_WALL) {
         // mirror of the interior cell at the same depth, normal momentum reflected
         const long long mi = at(side ? ext - d : d - 1);
         const double mx = q[mi + B.plane], my = q[mi + 2 * B.plane], mz = q[mi + 3 * B.plane];
@@ -369,6 +387,73 @@ __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBc
 #pragma unroll
         for (int v = 0; v < 5; ++v) q[gi + v * B.plane] = qb[v];
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// viscous terms: auxiliary-volume geometry (setup) and edge ghosts (per stage)
+// ---------------------------------------------------------------------------
+
+// Omega and the cell-averaged face vectors of every interior cell of a
+// curvilinear block, in its padded box
+__global__ void geo_cells_kernel(const double* nodes, int ni, int nj, int nk, const double* vol, long long pad_off,
+                                 long long P, double* geo) {
+  const long long n = (long long)ni * nj * nk;
+  NodeView N{nodes, ni, nj};
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % ni), j = (int)((c / ni) % nj), k = (int)(c / ((long long)ni * nj));
+    const long long pc = pad_off + ((long long)(k + 1) * (nj + 2) + (j + 1)) * (ni + 2) + (i + 1);
+    geo[pc] = vol[c];
+    for (int dir = 0; dir < 3; ++dir) {
+      const double* p[4];
+      double lo[3], hi[3];
+      face_nodes(N, dir, i, j, k, p);
+      cross_half(p[0], p[1], p[2], p[3], lo);
+      face_nodes(N, dir, i + (dir == 0), j + (dir == 1), k + (dir == 2), p);
+      cross_half(p[0], p[1], p[2], p[3], hi);
+      for (int x = 0; x < 3; ++x) geo[(1 + 3 * dir + x) * P + pc] = 0.5 * (lo[x] + hi[x]);
+    }
+  }
+}
+
+// the same for a Cartesian block (every cell alike)
+__global__ void geo_cart_kernel(FvBlockDev B, long long P, double* geo) {
+  const long long n = (long long)B.ni * B.nj * B.nk;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % B.ni), j = (int)((c / B.ni) % B.nj), k = (int)(c / ((long long)B.ni * B.nj));
+    const long long pc = B.pad_off + ((long long)(k + 1) * (B.nj + 2) + (j + 1)) * (B.ni + 2) + (i + 1);
+    geo[pc] = 1.0 / B.cart_invvol;
+    for (int dir = 0; dir < 3; ++dir)
+      for (int x = 0; x < 3; ++x) geo[(1 + 3 * dir + x) * P + pc] = B.cart_n[dir][x] * B.cart_area[dir];
+  }
+}
+
+// ghost-cell geometry: dst <- src with face family d taken from family
+// fam_d of the source, times sign_d (code: fam0 | fam1 << 2 | fam2 << 4,
+// negative signs in bits 6, 7, 8)
+struct GeoItem { long long dst, src; int code, pad_; };
+
+__global__ void geo_ghost_kernel(const GeoItem* __restrict__ items, long long n, long long P, double* geo) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const GeoItem it = items[x];
+    geo[it.dst] = geo[it.src];
+    for (int d = 0; d < 3; ++d) {
+      const int fam = (it.code >> (2 * d)) & 3;
+      const double sg = (it.code >> (6 + d)) & 1 ? -1.0 : 1.0;
+      for (int c = 0; c < 3; ++c) geo[(1 + 3 * d + c) * P + it.dst] = sg * geo[(1 + 3 * fam + c) * P + it.src];
+    }
+  }
+}
+
+__global__ void edge_fill_kernel(const fv_ctx::EdgeItem* __restrict__ items, long long n, double* q) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const fv_ctx::EdgeItem it = items[x];
+    if (it.s2 < 0) {
+      for (int v = 0; v < 5; ++v) q[it.dst + v * it.dplane] = q[it.s1 + v * it.s1plane];
+    } else {
+      for (int v = 0; v < 5; ++v)
+        q[it.dst + v * it.dplane] = 0.5 * (q[it.s1 + v * it.s1plane] + q[it.s2 + v * it.s2plane]);
     }
   }
 }
@@ -433,8 +518,42 @@ int grid_for(long long n, int threads, int nsm) {
 
 fv_ctx* H(fv_handle h) { return reinterpret_cast<fv_ctx*>(h); }
 
+// laminar viscous terms of state q: face variables, then the face fluxes of
+// every direction (they feed the fused kernel through FvStageArgs::fv)
+int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
+  FvViscArgs v;
+  std::memset(&v, 0, sizeof(v));
+  v.blocks = h->d_blocks;
+  v.nblocks = h->nblocks;
+  v.pad_total = h->pad_total;
+  v.geo = h->geo;
+  v.wvar = h->wvar;
+  v.q = q;
+  v.vp.gamma = h->cfg.gamma;
+  v.vp.mu = h->cfg.mu;
+  v.vp.r_gas = h->cfg.r_gas;
+  v.vp.kfac = h->cfg.gamma * h->cfg.r_gas / ((h->cfg.gamma - 1.0) * h->cfg.prandtl);
+  v.vp.t_ref = h->cfg.t_ref;
+  v.vp.s_suth = h->cfg.s_suth;
+  v.vp.sutherland = h->cfg.sutherland;
+  v.vp.dim = h->cfg.dim;
+  if (fv_visc_vars(v, h->cfg.precision, s)) return cuda_fail(h, cudaGetLastError(), "viscous face variables");
+  for (int d = 0; d < h->cfg.dim; ++d) {
+    v.metric = h->metric[d];
+    v.mstride = h->nfaces[d];
+    v.fv = h->fvis[d];
+    v.vstride = h->nvfaces[d];
+    if (fv_visc_faces(v, d, h->cfg.precision, s)) return cuda_fail(h, cudaGetLastError(), "viscous face fluxes");
+  }
+  return FV_OK;
+}
+
 int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
   int rc;
+  if (h->cfg.visc) {
+    rc = do_visc(h, a.qin, s);
+    if (rc) return rc;
+  }
   switch (h->cfg.precision) {
     case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, h->launch, s); break;
     case FV_PREC_DF64:
@@ -469,6 +588,8 @@ FvStageArgs base_args(fv_ctx* h) {
   a.fp.limiter = h->cfg.limiter;
   a.fp.fix_all = h->cfg.fix_all;
   a.fp.flux = h->cfg.flux;
+  if (h->cfg.visc)
+    for (int d = 0; d < h->cfg.dim; ++d) { a.fv[d] = h->fvis[d]; a.vstride[d] = h->nvfaces[d]; }
   return a;
 }
 
@@ -513,6 +634,10 @@ int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
                                                      (const float*)h->metric[0], (const float*)h->metric[1],
                                                      (const float*)h->metric[2], ms[0], ms[1], ms[2], G, q);
     }
+    CK(h, cudaGetLastError());
+  }
+  if (h->nedges) {
+    edge_fill_kernel<<<grid_for(h->nedges, 256, h->nsm), 256, 0, s>>>(h->d_edges, h->nedges, q);
     CK(h, cudaGetLastError());
   }
   return FV_OK;
@@ -630,6 +755,158 @@ int build_tiles(fv_ctx* h) {
   return FV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// viscous-term tables (host): ghost geometry items and edge-ghost items
+// ---------------------------------------------------------------------------
+long long pad_index(const FvBlockDev& B, int i, int j, int k) {
+  return B.pad_off + ((long long)(k + 1) * (B.nj + 2) + (j + 1)) * (B.ni + 2) + (i + 1);
+}
+long long state_index(const FvBlockDev& B, int i, int j, int k) {
+  return B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
+}
+// tangential axes of a face normal to axis a, in (i, j, k) order
+void tangential(int a, int t[2]) {
+  t[0] = a == 0 ? 1 : 0;
+  t[1] = a == 2 ? 1 : 2;
+}
+// donor cell (depth 1) of dst tangential coordinates (u0, u1) of connection c
+// (u may lie one cell outside the patch)
+void donor_cell(const fv_ctx* h, const fv_connection& c, int u0, int u1, int sc[3]) {
+  const FvBlockDev& S = h->hb[c.src_block];
+  const int sa = c.src_face / 2;
+  int st[2];
+  tangential(sa, st);
+  int v[2] = {c.src_lo[0], c.src_lo[1]};
+  const int a = u0 - c.dst_lo[0], b = u1 - c.dst_lo[1];
+  v[std::abs(c.transform[0]) - 1] += c.transform[0] > 0 ? a : -a;
+  v[std::abs(c.transform[1]) - 1] += c.transform[1] > 0 ? b : -b;
+  const int sext[3] = {S.ni, S.nj, S.nk};
+  sc[st[0]] = v[0];
+  sc[st[1]] = v[1];
+  sc[sa] = (c.src_face & 1) ? sext[sa] - 1 : 0;
+}
+
+int build_visc_tables(fv_ctx* h) {
+  // ghost geometry: copies of the adjacent interior cell, then the donors
+  std::vector<GeoItem> copies, donors;
+  const int ident = 0 | (1 << 2) | (2 << 4);
+  for (const FvBlockDev& B : h->hb) {
+    const int ext[3] = {B.ni, B.nj, B.nk};
+    for (int f = 0; f < 6; ++f) {
+      const int a = f / 2;
+      int t[2];
+      tangential(a, t);
+      for (int u1 = 0; u1 < ext[t[1]]; ++u1)
+        for (int u0 = 0; u0 < ext[t[0]]; ++u0) {
+          int g[3], in[3];
+          g[t[0]] = in[t[0]] = u0;
+          g[t[1]] = in[t[1]] = u1;
+          g[a] = (f & 1) ? ext[a] : -1;
+          in[a] = (f & 1) ? ext[a] - 1 : 0;
+          copies.push_back(GeoItem{pad_index(B, g[0], g[1], g[2]), pad_index(B, in[0], in[1], in[2]), ident, 0});
+        }
+    }
+  }
+  for (const fv_connection& c : h->conns) {
+    const FvBlockDev& D = h->hb[c.dst_block];
+    const FvBlockDev& S = h->hb[c.src_block];
+    const int da = c.dst_face / 2, sa = c.src_face / 2;
+    int dt[2], st[2];
+    tangential(da, dt);
+    tangential(sa, st);
+    int fam[3], neg[3];
+    fam[da] = sa;
+    neg[da] = (c.dst_face & 1) == (c.src_face & 1);   // index direction reverses
+    for (int x = 0; x < 2; ++x) {
+      fam[dt[x]] = st[std::abs(c.transform[x]) - 1];
+      neg[dt[x]] = c.transform[x] < 0;
+    }
+    const int code = fam[0] | (fam[1] << 2) | (fam[2] << 4) | (neg[0] << 6) | (neg[1] << 7) | (neg[2] << 8);
+    const int dext[3] = {D.ni, D.nj, D.nk};
+    for (int u1 = c.dst_lo[1]; u1 < c.dst_hi[1]; ++u1)
+      for (int u0 = c.dst_lo[0]; u0 < c.dst_hi[0]; ++u0) {
+        int g[3], sc[3];
+        g[dt[0]] = u0;
+        g[dt[1]] = u1;
+        g[da] = (c.dst_face & 1) ? dext[da] : -1;
+        donor_cell(h, c, u0, u1, sc);
+        donors.push_back(GeoItem{pad_index(D, g[0], g[1], g[2]), pad_index(S, sc[0], sc[1], sc[2]), code, 0});
+      }
+  }
+  for (const auto* list : {&copies, &donors}) {
+    if (list->empty()) continue;
+    GeoItem* d = nullptr;
+    CK(h, cudaMalloc(&d, sizeof(GeoItem) * list->size()));
+    CK(h, cudaMemcpy(d, list->data(), sizeof(GeoItem) * list->size(), cudaMemcpyHostToDevice));
+    geo_ghost_kernel<<<grid_for((long long)list->size(), 256, h->nsm), 256>>>(d, (long long)list->size(), h->pad_total,
+                                                                          h->geo);
+    CK(h, cudaDeviceSynchronize());
+    cudaFree(d);
+  }
+  // depth-1 edge ghosts: a connection of either face extended by one cell
+  // along the face (faces of the lower axis first, connections in table
+  // order), else the mean of the two face-adjacent ghosts
+  std::vector<fv_ctx::EdgeItem> edges;
+  const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  const int npairs = h->cfg.dim == 3 ? 3 : 1;
+  for (int bk = 0; bk < h->nblocks; ++bk) {
+    const FvBlockDev& B = h->hb[bk];
+    const int ext[3] = {B.ni, B.nj, B.nk};
+    for (int pr = 0; pr < npairs; ++pr) {
+      const int a = pairs[pr][0], b = pairs[pr][1], c3 = 3 - a - b;
+      const int nc = h->cfg.dim == 3 ? ext[c3] : 1;
+      for (int sa = 0; sa < 2; ++sa)
+        for (int sb = 0; sb < 2; ++sb)
+          for (int t = 0; t < nc; ++t) {
+            int e[3];
+            e[a] = sa ? ext[a] : -1;
+            e[b] = sb ? ext[b] : -1;
+            e[c3] = t;
+            fv_ctx::EdgeItem it{state_index(B, e[0], e[1], e[2]), B.plane, 0, 0, -1, 0};
+            bool found = false;
+            for (int pass = 0; pass < 2 && !found; ++pass) {
+              const int fa = pass == 0 ? a : b, other = pass == 0 ? b : a;
+              const int face = 2 * fa + (pass == 0 ? sa : sb);
+              int tn[2];
+              tangential(fa, tn);
+              for (const fv_connection& c : h->conns) {
+                if (c.dst_block != bk || c.dst_face != face) continue;
+                bool inside = true;
+                for (int x = 0; x < 2; ++x) {
+                  const int lo = c.dst_lo[x] - (tn[x] == other), hi = c.dst_hi[x] + (tn[x] == other);
+                  if (e[tn[x]] < lo || e[tn[x]] >= hi) inside = false;
+                }
+                if (!inside) continue;
+                int sc[3];
+                donor_cell(h, c, e[tn[0]], e[tn[1]], sc);
+                const FvBlockDev& S = h->hb[c.src_block];
+                it.s1 = state_index(S, sc[0], sc[1], sc[2]);
+                it.s1plane = S.plane;
+                found = true;
+                break;
+              }
+            }
+            if (!found) {
+              int f1[3] = {e[0], e[1], e[2]}, f2[3] = {e[0], e[1], e[2]};
+              f1[b] = sb ? ext[b] - 1 : 0;
+              f2[a] = sa ? ext[a] - 1 : 0;
+              it.s1 = state_index(B, f1[0], f1[1], f1[2]);
+              it.s1plane = B.plane;
+              it.s2 = state_index(B, f2[0], f2[1], f2[2]);
+              it.s2plane = B.plane;
+            }
+            edges.push_back(it);
+          }
+    }
+  }
+  h->nedges = (long long)edges.size();
+  if (h->nedges) {
+    CK(h, cudaMalloc(&h->d_edges, sizeof(fv_ctx::EdgeItem) * edges.size()));
+    CK(h, cudaMemcpy(h->d_edges, edges.data(), sizeof(fv_ctx::EdgeItem) * edges.size(), cudaMemcpyHostToDevice));
+  }
+  return FV_OK;
+}
+
 int validate(const fv_block_desc* blocks, int nblocks, const fv_connection* conns, int nconn, const fv_config* cfg) {
   if (!blocks || nblocks <= 0) return fail(nullptr, FV_ERR_INVALID_ARG, "no blocks");
   if (!cfg) return fail(nullptr, FV_ERR_INVALID_ARG, "no config");
@@ -639,6 +916,10 @@ int validate(const fv_block_desc* blocks, int nblocks, const fv_connection* conn
   if (cfg->limiter < 0 || cfg->limiter > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown limiter");
   if (cfg->flux < 0 || cfg->flux > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown face flux");
   if (!(cfg->gamma > 1.0)) return fail(nullptr, FV_ERR_INVALID_ARG, "gamma must exceed 1");
+  if (cfg->visc != 0 && cfg->visc != 1) return fail(nullptr, FV_ERR_INVALID_ARG, "visc must be 0 or 1");
+  if (cfg->visc && !(cfg->mu >= 0.0 && cfg->prandtl > 0.0 && cfg->r_gas > 0.0 &&
+                     (!cfg->sutherland || (cfg->t_ref > 0.0 && cfg->s_suth >= 0.0))))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "viscous parameters: need mu >= 0, prandtl > 0, r_gas > 0, t_ref > 0, s_suth >= 0");
   for (int b = 0; b < nblocks; ++b) {
     const fv_block_desc& d = blocks[b];
     if (d.ni < 1 || d.nj < 1 || d.nk < 1 || d.ni > 32000 || d.nj > 32000 || d.nk > 16000)
@@ -715,6 +996,13 @@ void fv_config_default(fv_config* c) {
   c->alpha[2] = 0.5;
   c->alpha[3] = 1.0;
   c->precision = FV_PREC_FP64;
+  c->visc = 0;
+  c->mu = 0.0;
+  c->prandtl = 0.72;
+  c->r_gas = 287.0;
+  c->sutherland = 0;
+  c->t_ref = 273.15;
+  c->s_suth = 110.4;
 }
 
 const char* fv_last_error(fv_handle h) {
@@ -765,6 +1053,19 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     }
     h->hb.push_back(B);
   }
+  if (cfg->visc) {
+    long long po = 0, vo[3] = {0, 0, 0};
+    for (auto& B : h->hb) {
+      B.pad_off = po;
+      po += (long long)(B.ni + 2) * (B.nj + 2) * (B.nk + 2);
+      for (int d = 0; d < 3; ++d) {
+        B.vface_off[d] = vo[d];
+        vo[d] += (long long)(B.ni + (d == 0)) * (B.nj + (d == 1)) * (B.nk + (d == 2));
+      }
+    }
+    h->pad_total = po;
+    for (int d = 0; d < 3; ++d) h->nvfaces[d] = vo[d];
+  }
   h->state_elems = qoff;
   h->ext_state_elems = 0;
   for (auto& B : h->hb) h->ext_state_elems += 5 * ghosted_cells(B.ni, B.nj, B.nk);
@@ -781,6 +1082,12 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
   const int mb = storage_bytes(cfg->precision);
   for (int d = 0; d < 3; ++d)
     if (h->nfaces[d]) CK(hp, cudaMalloc(&h->metric[d], (size_t)mb * 4 * h->nfaces[d]));
+  if (cfg->visc) {
+    CK(hp, cudaMalloc(&h->geo, sizeof(double) * 10 * h->pad_total));
+    CK(hp, cudaMemset(h->geo, 0, sizeof(double) * 10 * h->pad_total));
+    CK(hp, cudaMalloc(&h->wvar, sizeof(double) * 4 * h->pad_total));
+    for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], sizeof(double) * 4 * h->nvfaces[d]));
+  }
   // ---- metrics ----
   double* d_nodes = nullptr;
   for (int b = 0; b < nblocks; ++b) {
@@ -789,6 +1096,7 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     if (B.cartesian) {
       fill_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(h->invvol + B.cell_off, nc, B.cart_invvol);
       fill_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(h->vol + B.cell_off, nc, 1.0 / B.cart_invvol);
+      if (cfg->visc) geo_cart_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(B, h->pad_total, h->geo);
       continue;
     }
     const long long nn = 3LL * (B.ni + 1) * (B.nj + 1) * (B.nk + 1);
@@ -806,6 +1114,9 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
         metrics_faces_kernel<<<g, 256>>>(d_nodes, B.ni, B.nj, B.nk, dir, (float*)h->metric[dir], B.face_off[dir], h->nfaces[dir]);
     }
     volume_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(d_nodes, B.ni, B.nj, B.nk, h->vol + B.cell_off, h->invvol + B.cell_off);
+    if (cfg->visc)
+      geo_cells_kernel<<<grid_for(nc, 256, h->nsm), 256>>>(d_nodes, B.ni, B.nj, B.nk, h->vol + B.cell_off, B.pad_off,
+                                                           h->pad_total, h->geo);
     CK(hp, cudaDeviceSynchronize());
   }
   if (d_nodes) cudaFree(d_nodes);
@@ -832,6 +1143,12 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     CK(hp, cudaMalloc(&h->d_conns, sizeof(FvConnDev) * nconn));
     CK(hp, cudaMemcpy(h->d_conns, cd.data(), sizeof(FvConnDev) * nconn, cudaMemcpyHostToDevice));
   }
+  // ---- viscous-term tables ----
+  if (cfg->visc) {
+    CK(hp, cudaDeviceSynchronize());
+    rc = build_visc_tables(hp);
+    if (rc) { g_create_error = h->err; fv_destroy(reinterpret_cast<fv_handle>(h.release())); return rc; }
+  }
   // ---- tiles ----
   choose_launch(hp);
   rc = build_tiles(hp);
@@ -853,6 +1170,8 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
+  cudaFree(h->geo); cudaFree(h->wvar); cudaFree(h->d_edges);
+  for (int d = 0; d < 3; ++d) cudaFree(h->fvis[d]);
   delete h;
   return FV_OK;
 }
@@ -951,7 +1270,7 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
                     P.hi[0], P.lo[1], P.hi[1], e0, e1);
       return fail(h, FV_ERR_INVALID_ARG, msg);
     }
-    if (P.kind < FV_BC_FIXED || P.kind > FV_BC_FARFIELD) {
+    if (P.kind < FV_BC_FIXED || P.kind > FV_BC_NOSLIP_WALL) {
       std::snprintf(msg, sizeof(msg), "boundary patch %d: unknown kind %d", p, P.kind);
       return fail(h, FV_ERR_INVALID_ARG, msg);
     }
@@ -963,7 +1282,7 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
         return fail(h, FV_ERR_INVALID_ARG, msg);
       }
     }
-    if (P.kind == FV_BC_SLIP_WALL && ext[ax] < 2) {
+    if ((P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_NOSLIP_WALL) && ext[ax] < 2) {
       std::snprintf(msg, sizeof(msg), "boundary patch %d: a slip wall needs two cells along the face normal", p);
       return fail(h, FV_ERR_INVALID_ARG, msg);
     }
@@ -982,7 +1301,8 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
       D.cstate = std::sqrt(g * P.state[4] / r);
     }
     items += (long long)D.L0 * D.L1;
-    if ((P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD) && map_off[P.block] < 0) {
+    if ((P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD || P.kind == FV_BC_NOSLIP_WALL) &&
+        map_off[P.block] < 0) {
       map_off[P.block] = map_total;
       map_total += 2LL * ((long long)B.nj * B.nk + (long long)B.ni * B.nk + (long long)B.ni * B.nj);
     }
@@ -998,7 +1318,8 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
     long long base = map_off[P.block];
     for (int f = 0; f < P.face; ++f) base += sz[f];
     const int ext0 = P.face < 2 ? B.nj : B.ni;
-    const signed char code = (P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD) ? (signed char)P.kind : 0;
+    const signed char code =
+        (P.kind == FV_BC_SLIP_WALL || P.kind == FV_BC_FARFIELD || P.kind == FV_BC_NOSLIP_WALL) ? (signed char)P.kind : 0;
     for (int t1 = P.lo[1]; t1 < P.hi[1]; ++t1)
       for (int t0 = P.lo[0]; t0 < P.hi[0]; ++t0) maps[base + (long long)t1 * ext0 + t0] = code;
   }
@@ -1185,6 +1506,7 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
     return fail(h, FV_ERR_UNSUPPORTED, "the adjoint runs in binary64: create the handle with FV_PREC_FP64");
   if (h->cfg.flux != FV_FLUX_ROE) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint is built for the Roe flux");
   if (h->nbc) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint does not linearise physical boundary patches");
+  if (h->cfg.visc) return fail(h, FV_ERR_UNSUPPORTED, "the adjoint is built for the inviscid residual");
   cudaStream_t s = (cudaStream_t)stream;
   const int nd = h->cfg.dim;
   // per-direction offsets of each block's faces in the contribution scratch

@@ -23,6 +23,8 @@ struct FvBlockDev {
   // nj*nk, nj*nk, ni*nk, ni*nk, ni*nj, ni*nj; first tangential index
   // fastest) back to back, or null when the block has none
   const signed char* bcmap;
+  long long pad_off;            // viscous terms: first cell of the block padded by one layer
+  long long vface_off[3];       // viscous terms: first face per direction (every block)
   double cart_n[3][3];          // Cartesian unit normal of each face family
   double cart_area[3];          // Cartesian face areas
   double cart_invvol;           // Cartesian 1/volume
@@ -42,7 +44,7 @@ struct FvConnDev {
 
 // Physical boundary kinds as the kernels see them (the values of fv_bc_kind).
 constexpr int FV_BCK_FIXED = 0, FV_BCK_SUPERSONIC_INFLOW = 1, FV_BCK_EXTRAPOLATE = 2, FV_BCK_SLIP_WALL = 3,
-              FV_BCK_FARFIELD = 4;
+              FV_BCK_FARFIELD = 4, FV_BCK_NOSLIP_WALL = 5;
 
 // One physical boundary patch; work items (a, b) = tangential cells.
 struct FvBcDev {
@@ -74,6 +76,8 @@ struct FvStageArgs {
   const double* invvol;         // 1/Omega per interior cell
   const double* srcvol;         // S*Omega, [block][5][cells], or null
   const float2* srcvol2;        // the same as double-float (hi, lo) pairs, or null
+  const double* fv[3];          // viscous face fluxes per direction, [4][faces] (momentum, energy), or null
+  long long vstride[3];         // faces per direction of fv
   double* rout;                 // residual output or null
   int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
   long long ncell_total;
@@ -126,3 +130,31 @@ int fv_adjoint_gather(const FvBlockDev& B, const double* cx, const double* cy, c
 int fv_adjoint_transpose(const FvBlockDev* d_blocks, const FvConnDev& c, double* lamg, cudaStream_t s);
 int fv_adjoint_finish(const FvBlockDev& B, const double* lamg, const double* lam_out, double* lam_in, double* lam_q0,
                       cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Laminar viscous terms (fv_visc.cu)
+// ---------------------------------------------------------------------------
+struct FvViscParams {
+  double gamma, mu, r_gas, kfac;   // kfac = gamma r_gas / ((gamma - 1) Pr): k = mu kfac
+  double t_ref, s_suth;
+  int sutherland, dim;
+};
+
+// Padded-cell geometry of the auxiliary volumes: 10 planes of pad_total cells
+// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta); face variables: 4 planes (u, v, w, T).
+struct FvViscArgs {
+  const FvBlockDev* blocks;
+  int nblocks;
+  long long pad_total;
+  const double* geo;
+  double* wvar;
+  const double* q;                 // state buffer (ghosts filled)
+  const void* metric;              // this direction's face metrics (storage type of the form)
+  long long mstride;
+  double* fv;                      // this direction's viscous fluxes [4][vstride]
+  long long vstride;
+  FvViscParams vp;
+};
+
+int fv_visc_vars(const FvViscArgs& a, int precision, cudaStream_t s);          // face variables
+int fv_visc_faces(const FvViscArgs& a, int dir, int precision, cudaStream_t s); // fluxes of one direction

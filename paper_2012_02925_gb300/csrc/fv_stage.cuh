@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         nz = MetricStore<T>::ld(m, f + 2 * ms); A = MetricStore<T>::ld(m, f + 3 * ms);
       }
       T out[5];
-      if (code == FV_BCK_SLIP_WALL) {
+      if (code == FV_BCK_SLIP_WALL || code == FV_BCK_NOSLIP_WALL) {
         // nearest interior cells: s2, s3 on a min face, s1, s0 on a max face
         wall_face_flux(C, (side ? s1 : s2)[4 * PL], (side ? s0 : s3)[4 * PL], nx, ny, nz, A, out);
       } else if (code == FV_BCK_FARFIELD) {
@@ -341,6 +341,11 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
           const long long ncell_b = (long long)ni * nj * nk;
           AT R[5];
           const long long src_off = 5 * B.cell_off + cell;
+          // viscous face fluxes of this cell's six faces (laminar terms on)
+          const long long vx = B.vface_off[0] + ((long long)k * nj + j) * (ni + 1) + i;
+          const long long vy = B.vface_off[1] + ((long long)k * (nj + 1) + j) * ni + i;
+          const long long vz = B.vface_off[2] + ((long long)k * nj + j) * ni + i;
+          const long long vzs = (long long)ni * nj;
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
             const T x1 = Fx[n * NXI + y * (TX + 1) + x + 1], x0 = Fx[n * NXI + y * (TX + 1) + x];
@@ -358,6 +363,24 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
                 lo = FADD(FADD(lo, rz.lo), h2.lo);
                 h.hi = h2.hi;
               }
+              if (args.fv[0] && n > 0) {
+                // the viscous pairs (binary32 values stored in binary64: exact)
+                const double* f0 = args.fv[0] + (n - 1) * args.vstride[0];
+                const double* f1 = args.fv[1] + (n - 1) * args.vstride[1];
+                const df64 vxp = two_sum(fv_d2f_rn(f0[vx + 1]), -fv_d2f_rn(f0[vx]));
+                const df64 vyp = two_sum(fv_d2f_rn(f1[vy + ni]), -fv_d2f_rn(f1[vy]));
+                df64 t = two_sum(h.hi, -vxp.hi);
+                lo = FADD(FSUB(lo, vxp.lo), t.lo);
+                t = two_sum(t.hi, -vyp.hi);
+                lo = FADD(FSUB(lo, vyp.lo), t.lo);
+                if (DIM3) {
+                  const double* f2 = args.fv[2] + (n - 1) * args.vstride[2];
+                  const df64 vzp = two_sum(fv_d2f_rn(f2[vz + vzs]), -fv_d2f_rn(f2[vz]));
+                  t = two_sum(t.hi, -vzp.hi);
+                  lo = FADD(FSUB(lo, vzp.lo), t.lo);
+                }
+                h.hi = t.hi;
+              }
               if (args.srcvol2) {
                 const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);
                 const df64 t = two_sum(h.hi, -sv.x);
@@ -370,6 +393,17 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
               if (DIM3)
                 r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
                                      Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
+              if (args.fv[0] && n > 0) {
+                const double* f0 = args.fv[0] + (n - 1) * args.vstride[0];
+                const double* f1 = args.fv[1] + (n - 1) * args.vstride[1];
+                AT rv = (Acc<T>::from_d(f0[vx + 1]) - Acc<T>::from_d(f0[vx])) +
+                        (Acc<T>::from_d(f1[vy + ni]) - Acc<T>::from_d(f1[vy]));
+                if (DIM3) {
+                  const double* f2 = args.fv[2] + (n - 1) * args.vstride[2];
+                  rv = rv + (Acc<T>::from_d(f2[vz + vzs]) - Acc<T>::from_d(f2[vz]));
+                }
+                r = r - rv;
+              }
               if constexpr (std::is_same<AT, df64>::value) {
                 if (args.srcvol2) {
                   const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);

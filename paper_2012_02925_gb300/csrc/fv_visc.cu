@@ -1,0 +1,201 @@
+// Laminar viscous terms (Section 2): F_v.S = (0, tau.S, Theta.S) with
+// Stokes's-hypothesis stresses tau = mu (grad u + grad u^T - 2/3 div u I),
+// Theta = tau.u_f + k grad T, k = mu c_p / Pr, T = p / (rho R), and face
+// gradients by Green's theorem over the auxiliary volume between the two
+// cell centres (Section 2: the viscous flux needs a wider stencil than the
+// inviscid one).
+//
+// Two kernels per stage, each in the arithmetic of the form (binary64,
+// double-float, binary32): the face variables (u, v, w, T) of every cell of
+// the blocks padded by one layer (ghosts and edge ghosts included), then one
+// thread per face of one direction gathering the ten cells of its stencil and
+// the auxiliary-volume geometry of its two cells.  The fluxes go to a
+// per-face array that the fused stage kernel differences per cell.
+#include "fv_arith.cuh"
+#include "fv_internal.h"
+
+namespace {
+
+template <class T> struct VMetric;
+template <> struct VMetric<double> {
+  using type = double;
+  static __device__ __forceinline__ double ld(const double* m, long long i) { return __ldg(m + i); }
+};
+template <> struct VMetric<df64> {
+  using type = float2;
+  static __device__ __forceinline__ df64 ld(const float2* m, long long i) {
+    const float2 v = __ldg(m + i);
+    return mk(v.x, v.y);
+  }
+};
+template <> struct VMetric<float> {
+  using type = float;
+  static __device__ __forceinline__ float ld(const float* m, long long i) { return __ldg(m + i); }
+};
+
+// last block whose offset (pad_off, or vface_off[dir] when dir >= 0) is <= x
+__device__ __forceinline__ int find_block(const FvBlockDev* __restrict__ B, int n, long long x, int dir) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const long long o = dir < 0 ? B[mid].pad_off : B[mid].vface_off[dir];
+    if (o <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// (u, v, w, T) of every padded cell; cells that were never filled (the
+// corners of the ghost frame, density 0) get zeros - no stencil reads them
+template <class T>
+__global__ void visc_vars_kernel(const FvViscArgs a) {
+  using S = Sc<T>;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < a.pad_total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const FvBlockDev& B = a.blocks[find_block(a.blocks, a.nblocks, x, -1)];
+    const long long loc = x - B.pad_off;
+    const int pi = B.ni + 2, pj = B.nj + 2;
+    const int i = (int)(loc % pi) - 1, j = (int)((loc / pi) % pj) - 1, k = (int)(loc / ((long long)pi * pj)) - 1;
+    const long long qi = B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
+    const double r = a.q[qi];
+    if (!(r > 0.0)) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a.wvar[m * a.pad_total + x] = 0.0;
+      continue;
+    }
+    const T rho = S::from_d(r);
+    const T ri = S::rcp(rho);
+    const T u = S::from_d(a.q[qi + B.plane]) * ri;
+    const T v = S::from_d(a.q[qi + 2 * B.plane]) * ri;
+    const T w = S::from_d(a.q[qi + 3 * B.plane]) * ri;
+    const T p = S::c(a.vp.gamma - 1.0) * (S::from_d(a.q[qi + 4 * B.plane]) - S::c(0.5) * rho * (u * u + v * v + w * w));
+    const T temp = p * ri * S::c(1.0 / a.vp.r_gas);
+    a.wvar[x] = S::to_d(u);
+    a.wvar[a.pad_total + x] = S::to_d(v);
+    a.wvar[2 * a.pad_total + x] = S::to_d(w);
+    a.wvar[3 * a.pad_total + x] = S::to_d(temp);
+  }
+}
+
+template <class T>
+__global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
+  using S = Sc<T>;
+  using MT = typename VMetric<T>::type;
+  const MT* metric = reinterpret_cast<const MT*>(a.metric);
+  const long long P = a.pad_total;
+  const int b_ax = dir == 0 ? 1 : 0, c_ax = dir == 2 ? 1 : 2;
+  const bool three = a.vp.dim == 3;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < a.vstride;
+       f += (long long)gridDim.x * blockDim.x) {
+    const FvBlockDev& B = a.blocks[find_block(a.blocks, a.nblocks, f, dir)];
+    const long long loc = f - B.vface_off[dir];
+    const int ei = B.ni + (dir == 0), ej = B.nj + (dir == 1);
+    const int i = (int)(loc % ei), j = (int)((loc / ei) % ej), k = (int)(loc / ((long long)ei * ej));
+    const long long pi = B.ni + 2, pij = pi * (B.nj + 2);
+    const long long pR = B.pad_off + (k + 1) * pij + (long long)(j + 1) * pi + (i + 1);
+    const long long sa = dir == 0 ? 1 : (dir == 1 ? pi : pij);
+    const long long sb = b_ax == 0 ? 1 : pi, sc = c_ax == 1 ? pi : pij;
+    const long long pL = pR - sa;
+    // the face's area vector
+    T Sx, Sy, Sz;
+    if (B.cartesian) {
+      const T A = S::from_d(B.cart_area[dir]);
+      Sx = S::from_d(B.cart_n[dir][0]) * A;
+      Sy = S::from_d(B.cart_n[dir][1]) * A;
+      Sz = S::from_d(B.cart_n[dir][2]) * A;
+    } else {
+      const long long fi = B.face_off[dir] + loc;
+      const T A = VMetric<T>::ld(metric, fi + 3 * a.mstride);
+      Sx = VMetric<T>::ld(metric, fi) * A;
+      Sy = VMetric<T>::ld(metric, fi + a.mstride) * A;
+      Sz = VMetric<T>::ld(metric, fi + 2 * a.mstride) * A;
+    }
+    // auxiliary volume: mean volume and mean averaged face vectors of L and R
+    const T half = S::c(0.5), quarter = S::c(0.25);
+    const T iOm = S::rcp(half * (S::from_d(a.geo[pL]) + S::from_d(a.geo[pR])));
+    // families of the face's own axis (a) and of the tangential axes b, c
+    T Aa[3], Ab[3], Ac[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const double* ga = a.geo + (long long)(1 + 3 * dir + x) * P;
+      const double* gb = a.geo + (long long)(1 + 3 * b_ax + x) * P;
+      const double* gc = a.geo + (long long)(1 + 3 * c_ax + x) * P;
+      Aa[x] = half * (S::from_d(ga[pL]) + S::from_d(ga[pR]));
+      Ab[x] = half * (S::from_d(gb[pL]) + S::from_d(gb[pR]));
+      Ac[x] = half * (S::from_d(gc[pL]) + S::from_d(gc[pR]));
+    }
+    // gradients of u, v, w, T
+    T grad[4][3];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double* W = a.wvar + m * P;
+      const T da = S::from_d(W[pR]) - S::from_d(W[pL]);
+      const T db = quarter * ((S::from_d(W[pL + sb]) - S::from_d(W[pL - sb])) +
+                              (S::from_d(W[pR + sb]) - S::from_d(W[pR - sb])));
+      T dc = S::c(0.0);
+      if (three)
+        dc = quarter * ((S::from_d(W[pL + sc]) - S::from_d(W[pL - sc])) +
+                        (S::from_d(W[pR + sc]) - S::from_d(W[pR - sc])));
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        T g = da * Aa[x] + db * Ab[x];
+        if (three) g = g + dc * Ac[x];
+        grad[m][x] = g * iOm;
+      }
+    }
+    // face values, viscosity, conductivity
+    T uf[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) uf[x] = half * (S::from_d(a.wvar[x * P + pL]) + S::from_d(a.wvar[x * P + pR]));
+    const T Tf = half * (S::from_d(a.wvar[3 * P + pL]) + S::from_d(a.wvar[3 * P + pR]));
+    T mu = S::c(a.vp.mu);
+    if (a.vp.sutherland) {
+      const T tr = Tf * S::c(1.0 / a.vp.t_ref);
+      mu = mu * tr * S::sqrt(tr) * S::c(a.vp.t_ref + a.vp.s_suth) * S::rcp(Tf + S::c(a.vp.s_suth));
+    }
+    const T kc = mu * S::c(a.vp.kfac);
+    const T div = grad[0][0] + grad[1][1] + grad[2][2];
+    const T Sv[3] = {Sx, Sy, Sz};
+    T energy = S::c(0.0);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      T fx = S::c(0.0);
+#pragma unroll
+      for (int y = 0; y < 3; ++y) {
+        T t = grad[x][y] + grad[y][x];
+        if (x == y) t = t - S::c(2.0 / 3.0) * div;
+        fx = fx + mu * t * Sv[y];
+      }
+      a.fv[x * a.vstride + f] = S::to_d(fx);
+      energy = energy + fx * uf[x];
+    }
+    energy = energy + kc * (grad[3][0] * Sx + grad[3][1] * Sy + grad[3][2] * Sz);
+    a.fv[3 * a.vstride + f] = S::to_d(energy);
+  }
+}
+
+int grid_of(long long n, int threads) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long g = (n + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > (long long)nsm * 16 ? (long long)nsm * 16 : g));
+}
+
+}  // namespace
+
+int fv_visc_vars(const FvViscArgs& a, int precision, cudaStream_t s) {
+  const int t = 256, g = grid_of(a.pad_total, t);
+  if (precision == 0) visc_vars_kernel<double><<<g, t, 0, s>>>(a);
+  else if (precision == 1) visc_vars_kernel<df64><<<g, t, 0, s>>>(a);
+  else visc_vars_kernel<float><<<g, t, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int fv_visc_faces(const FvViscArgs& a, int dir, int precision, cudaStream_t s) {
+  if (a.vstride == 0) return 0;
+  const int t = 128, g = grid_of(a.vstride, t);
+  if (precision == 0) visc_faces_kernel<double><<<g, t, 0, s>>>(a, dir);
+  else if (precision == 1) visc_faces_kernel<df64><<<g, t, 0, s>>>(a, dir);
+  else visc_faces_kernel<float><<<g, t, 0, s>>>(a, dir);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
