@@ -48,8 +48,17 @@ CELL_OPS = 58
 DF64_COST = {"add": 11, "mul": 7, "div": 27, "sqrt": 25, "abs": 2}
 
 
-def alu_ops_per_cell(dim: int = 3) -> int:
-    return dim * sum(FACE_OPS.values()) + CELL_OPS
+# one viscous face (the oracle's own count: face gradients of u, v, w, T,
+# stresses, heat flux, flux; constant viscosity) and, per cell, the viscous
+# pair differences of the 4 momentum/energy components
+VISC_FACE_OPS = {"add": 82, "mul": 89, "div": 24, "sqrt": 0, "abs": 0}
+
+
+def alu_ops_per_cell(dim: int = 3, visc: bool = False) -> int:
+    n = dim * sum(FACE_OPS.values()) + CELL_OPS
+    if visc:
+        n += dim * sum(VISC_FACE_OPS.values()) + 8 * dim
+    return n
 
 
 def alu_peak(precision: str) -> float:
@@ -67,6 +76,8 @@ def workload(name: str):
     Steger-Warming face flux instead of Roe."""
     if "+" in name:
         base, suf = name.split("+", 1)
+        if suf == "ns":
+            return workload_ns(base)
         pb = workload(base)
         pb.params["flux"] = {"vl": 1, "sw": 2}[suf]
         pb.name += "_" + {"vl": "vanleer_fvs", "sw": "steger_warming"}[suf]
@@ -88,6 +99,22 @@ def workload(name: str):
     raise SystemExit("unknown workload " + name)
 
 
+def workload_ns(base: str):
+    """Laminar Navier-Stokes versions: the manufactured 128^3 block with its
+    viscous source (mu = 0.05), or the extruded O-grid with adiabatic no-slip
+    walls and air's Sutherland viscosity (SI units)."""
+    if base.startswith("mms"):
+        n = 128 if base == "mms128" else int(base[3:])
+        return cases.mms_3d(n, curvilinear=True, visc=1, mu=0.05)
+    pb = workload(base)
+    pb.params.update(visc=1, mu=1.716e-5, sutherland=1, t_ref=273.15, s_suth=110.4, r_gas=287.0)
+    pb.bcs = [cases.BCPatch(p.block, p.face, p.lo, p.hi,
+                            cases.BC_NOSLIP_WALL if p.kind == cases.BC_SLIP_WALL else p.kind, p.state)
+              for p in pb.bcs]
+    pb.name += "_ns"
+    return pb
+
+
 def algorithmic_bytes(pb, stage: int, curvilinear: bool) -> float:
     """Bytes a cell-update must move at least: read Q^(m-1) (40 B), read Q^(0)
     for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics 24 B per
@@ -100,6 +127,8 @@ def algorithmic_bytes(pb, stage: int, curvilinear: bool) -> float:
         per += 24.0 * pb.dim + 8.0
     if pb.source is not None:
         per += 40.0
+    if pb.params.get("visc", 0):
+        per += 80.0          # the auxiliary-volume geometry (Omega + 3 face vectors) read once
     ghosts = 0
     for c in pb.conns:
         ghosts += 2 * (c.dst_hi[0] - c.dst_lo[0]) * (c.dst_hi[1] - c.dst_lo[1])
@@ -261,7 +290,7 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
     else:
         # FP64-accurate forms are bound by arithmetic: algorithmic FP64
         # operations per launch / launch time against the derived peak
-        ops = alu_ops_per_cell(pb.dim) * pb.ncells
+        ops = alu_ops_per_cell(pb.dim, bool(pb.params.get("visc", 0))) * pb.ncells
         achieved = ops / (sum(kt) / M) / 1e9
         peak = alu_peak(precision) / 1e9
         r.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s (FP64 ops)",
@@ -533,7 +562,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
-    ap.add_argument("--variant-workloads", default="mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid")
+    ap.add_argument("--variant-workloads",
+                    default="mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid,mms128+ns,ogrid+ns")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

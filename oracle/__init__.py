@@ -75,6 +75,7 @@ def lib():
         L.oracle_residual_ns.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 7 + [
             ctypes.c_char_p, _dp]
         L.oracle_viscous_face.argtypes = [_dp, _dp, _dp, ctypes.c_int, _dp, _dp]
+        L.oracle_viscous_opcount.argtypes = [_dp, _lp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -178,6 +179,13 @@ def viscous_face(params: dict, V10, geo2, axis: int, S, dim: int = 3) -> np.ndar
                               _p(np.ascontiguousarray(geo2, dtype=np.float64)), int(axis),
                               _p(np.ascontiguousarray(S, dtype=np.float64)), _p(out))
     return out
+
+
+def viscous_opcount(params: dict) -> dict:
+    """Operation counts of one viscous face (gradients, stresses, flux)."""
+    out = np.zeros(6, dtype=np.int64)
+    lib().oracle_viscous_opcount(_p(params_array(params, 3)), _p(out))
+    return dict(zip(("add", "mul", "div", "sqrt", "abs", "cmp"), map(int, out)))
 
 
 def face_opcount(params: dict) -> dict:

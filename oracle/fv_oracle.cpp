@@ -886,6 +886,24 @@ void oracle_residual_ns(const double* params, int ni, int nj, int nk, const doub
   residual_block<double>(P, B, Sxi, Seta, Szeta, vol, q, src, R, codes ? maps : nullptr, geo);
 }
 
+// Operation counts of one viscous face (op-counting scalar), as the oracle
+// states it: {add, mul, div, sqrt, abs, cmp}.
+void oracle_viscous_opcount(const double* params, long* out) {
+  Params P = unpack(params);
+  P.dim = 3;
+  Blk B(5, 5, 5);
+  std::vector<Cnt> V(5 * B.plane, Cnt(1.0));
+  std::vector<double> g(20, 1.0);
+  Geo G{g.data(), 2, 2, 1};
+  const double S[3] = {1.0, 0.1, 0.2};
+  const long cL = B.at(2, 2, 2);
+  Cnt o[5];
+  g_ops = OpCount{0, 0, 0, 0, 0, 0};
+  viscous_face<Cnt>(P, B, V, G, cL, cL + B.sx, B.sy, B.sz, 0, 1, 0, 1, 2, S, o);
+  out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div;
+  out[3] = g_ops.sqrt; out[4] = g_ops.abs_; out[5] = g_ops.cmp;
+}
+
 // Viscous flux of one face from explicit stencil data, for the closed-form
 // checks: V10 = primitives of L, R, L-b, L+b, R-b, R+b, L-c, L+c, R-c, R+c
 // (10 x 5), geo2 = Omega, Sbar_xi, Sbar_eta, Sbar_zeta of L then R (2 x 10),

@@ -16,3 +16,9 @@ def test_alu_peaks_are_derived_from_unit_counts():
     assert bench.alu_peak("fp64") == 1.25e12
     p = bench.alu_peak("df64")
     assert 3.0e12 < p < 4.5e12
+
+
+def test_viscous_face_op_count_matches_oracle():
+    c = oracle.viscous_opcount(default_params(visc=1, mu=0.05))
+    for k, v in bench.VISC_FACE_OPS.items():
+        assert c[k] == v, (k, c[k], v)
