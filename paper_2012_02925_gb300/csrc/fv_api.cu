@@ -56,9 +56,10 @@ struct fv_ctx {
   // laminar viscous terms
   long long pad_total = 0;          // cells of all blocks padded by one layer
   long long nvfaces[3] = {0, 0, 0}; // faces per direction, every block
-  double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total]
-  double* wvar = nullptr;           // face variables (u, v, w, T) [4][pad_total]
-  double* fvis[3] = {nullptr, nullptr, nullptr};  // viscous face fluxes [4][nvfaces[d]]
+  double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total], binary64 (setup)
+  void* geo_t = nullptr;            // the same in the form's storage type (== geo for binary64)
+  void* wvar = nullptr;             // face variables (u, v, w, T) [4][pad_total], storage type
+  void* fvis[3] = {nullptr, nullptr, nullptr};    // viscous face fluxes [4][nvfaces[d]], storage type
   struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
   EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
   long long nedges = 0;
@@ -429,6 +430,13 @@ __global__ void geo_cart_kernel(FvBlockDev B, long long P, double* geo) {
   }
 }
 
+// binary64 -> the storage type of a form
+template <class MT>
+__global__ void convert_kernel(const double* in, MT* out, long long n) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+    store_metric(out, x, in[x]);
+}
+
 // ghost-cell geometry: dst <- src with face family d taken from family
 // fam_d of the source, times sign_d (code: fam0 | fam1 << 2 | fam2 << 4,
 // negative signs in bits 6, 7, 8)
@@ -526,7 +534,7 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
   v.blocks = h->d_blocks;
   v.nblocks = h->nblocks;
   v.pad_total = h->pad_total;
-  v.geo = h->geo;
+  v.geo = h->geo_t;
   v.wvar = h->wvar;
   v.q = q;
   v.vp.gamma = h->cfg.gamma;
@@ -1085,8 +1093,8 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
   if (cfg->visc) {
     CK(hp, cudaMalloc(&h->geo, sizeof(double) * 10 * h->pad_total));
     CK(hp, cudaMemset(h->geo, 0, sizeof(double) * 10 * h->pad_total));
-    CK(hp, cudaMalloc(&h->wvar, sizeof(double) * 4 * h->pad_total));
-    for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], sizeof(double) * 4 * h->nvfaces[d]));
+    CK(hp, cudaMalloc(&h->wvar, (size_t)mb * 4 * h->pad_total));
+    for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], (size_t)mb * 4 * h->nvfaces[d]));
   }
   // ---- metrics ----
   double* d_nodes = nullptr;
@@ -1148,6 +1156,19 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     CK(hp, cudaDeviceSynchronize());
     rc = build_visc_tables(hp);
     if (rc) { g_create_error = h->err; fv_destroy(reinterpret_cast<fv_handle>(h.release())); return rc; }
+    if (cfg->precision == FV_PREC_FP64) {
+      h->geo_t = h->geo;
+    } else {
+      const long long n = 10 * h->pad_total;
+      CK(hp, cudaMalloc(&h->geo_t, (size_t)mb * n));
+      if (cfg->precision == FV_PREC_DF64)
+        convert_kernel<<<grid_for(n, 256, h->nsm), 256>>>(h->geo, (float2*)h->geo_t, n);
+      else
+        convert_kernel<<<grid_for(n, 256, h->nsm), 256>>>(h->geo, (float*)h->geo_t, n);
+      CK(hp, cudaDeviceSynchronize());
+      cudaFree(h->geo);
+      h->geo = nullptr;
+    }
   }
   // ---- tiles ----
   choose_launch(hp);
@@ -1170,6 +1191,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
+  if (h->geo_t != h->geo) cudaFree(h->geo_t);
   cudaFree(h->geo); cudaFree(h->wvar); cudaFree(h->d_edges);
   for (int d = 0; d < 3; ++d) cudaFree(h->fvis[d]);
   delete h;

@@ -76,7 +76,8 @@ struct FvStageArgs {
   const double* invvol;         // 1/Omega per interior cell
   const double* srcvol;         // S*Omega, [block][5][cells], or null
   const float2* srcvol2;        // the same as double-float (hi, lo) pairs, or null
-  const double* fv[3];          // viscous face fluxes per direction, [4][faces] (momentum, energy), or null
+  const void* fv[3];            // viscous face fluxes per direction, [4][faces] (momentum, energy), in the
+                                // form's storage type (binary64, binary32 pairs, binary32), or null
   long long vstride[3];         // faces per direction of fv
   double* rout;                 // residual output or null
   int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
@@ -141,17 +142,20 @@ struct FvViscParams {
 };
 
 // Padded-cell geometry of the auxiliary volumes: 10 planes of pad_total cells
-// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta); face variables: 4 planes (u, v, w, T).
+// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta); face variables: 4 planes (u, v, w, T);
+// both, and the fluxes, in the storage type of the form (binary64 for the
+// binary64 form, (hi, lo) binary32 pairs for double-float, binary32 for the
+// binary32-flux form), so that the kernels convert nothing.
 struct FvViscArgs {
   const FvBlockDev* blocks;
   int nblocks;
   long long pad_total;
-  const double* geo;
-  double* wvar;
+  const void* geo;
+  void* wvar;
   const double* q;                 // state buffer (ghosts filled)
-  const void* metric;              // this direction's face metrics (storage type of the form)
+  const void* metric;              // this direction's face metrics
   long long mstride;
-  double* fv;                      // this direction's viscous fluxes [4][vstride]
+  void* fv;                        // this direction's viscous fluxes [4][vstride]
   long long vstride;
   FvViscParams vp;
 };

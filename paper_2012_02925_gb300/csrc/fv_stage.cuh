@@ -364,18 +364,18 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
                 h.hi = h2.hi;
               }
               if (args.fv[0] && n > 0) {
-                // the viscous pairs (binary32 values stored in binary64: exact)
-                const double* f0 = args.fv[0] + (n - 1) * args.vstride[0];
-                const double* f1 = args.fv[1] + (n - 1) * args.vstride[1];
-                const df64 vxp = two_sum(fv_d2f_rn(f0[vx + 1]), -fv_d2f_rn(f0[vx]));
-                const df64 vyp = two_sum(fv_d2f_rn(f1[vy + ni]), -fv_d2f_rn(f1[vy]));
+                // the viscous pairs (binary32 fluxes)
+                const float* f0 = reinterpret_cast<const float*>(args.fv[0]) + (n - 1) * args.vstride[0];
+                const float* f1 = reinterpret_cast<const float*>(args.fv[1]) + (n - 1) * args.vstride[1];
+                const df64 vxp = two_sum(f0[vx + 1], -f0[vx]);
+                const df64 vyp = two_sum(f1[vy + ni], -f1[vy]);
                 df64 t = two_sum(h.hi, -vxp.hi);
                 lo = FADD(FSUB(lo, vxp.lo), t.lo);
                 t = two_sum(t.hi, -vyp.hi);
                 lo = FADD(FSUB(lo, vyp.lo), t.lo);
                 if (DIM3) {
-                  const double* f2 = args.fv[2] + (n - 1) * args.vstride[2];
-                  const df64 vzp = two_sum(fv_d2f_rn(f2[vz + vzs]), -fv_d2f_rn(f2[vz]));
+                  const float* f2 = reinterpret_cast<const float*>(args.fv[2]) + (n - 1) * args.vstride[2];
+                  const df64 vzp = two_sum(f2[vz + vzs], -f2[vz]);
                   t = two_sum(t.hi, -vzp.hi);
                   lo = FADD(FSUB(lo, vzp.lo), t.lo);
                 }
@@ -394,13 +394,14 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
                 r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
                                      Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
               if (args.fv[0] && n > 0) {
-                const double* f0 = args.fv[0] + (n - 1) * args.vstride[0];
-                const double* f1 = args.fv[1] + (n - 1) * args.vstride[1];
-                AT rv = (Acc<T>::from_d(f0[vx + 1]) - Acc<T>::from_d(f0[vx])) +
-                        (Acc<T>::from_d(f1[vy + ni]) - Acc<T>::from_d(f1[vy]));
+                // the viscous pairs, stored like the metrics of this form
+                const MT* f0 = reinterpret_cast<const MT*>(args.fv[0]) + (n - 1) * args.vstride[0];
+                const MT* f1 = reinterpret_cast<const MT*>(args.fv[1]) + (n - 1) * args.vstride[1];
+                AT rv = (MetricStore<T>::ld(f0, vx + 1) - MetricStore<T>::ld(f0, vx)) +
+                        (MetricStore<T>::ld(f1, vy + ni) - MetricStore<T>::ld(f1, vy));
                 if (DIM3) {
-                  const double* f2 = args.fv[2] + (n - 1) * args.vstride[2];
-                  rv = rv + (Acc<T>::from_d(f2[vz + vzs]) - Acc<T>::from_d(f2[vz]));
+                  const MT* f2 = reinterpret_cast<const MT*>(args.fv[2]) + (n - 1) * args.vstride[2];
+                  rv = rv + (MetricStore<T>::ld(f2, vz + vzs) - MetricStore<T>::ld(f2, vz));
                 }
                 r = r - rv;
               }

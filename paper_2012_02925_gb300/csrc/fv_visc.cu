@@ -16,10 +16,13 @@
 
 namespace {
 
+// storage type of each arithmetic form (metrics, geometry, face variables,
+// fluxes) with its load and store
 template <class T> struct VMetric;
 template <> struct VMetric<double> {
   using type = double;
   static __device__ __forceinline__ double ld(const double* m, long long i) { return __ldg(m + i); }
+  static __device__ __forceinline__ void st(double* m, long long i, double v) { m[i] = v; }
 };
 template <> struct VMetric<df64> {
   using type = float2;
@@ -27,10 +30,12 @@ template <> struct VMetric<df64> {
     const float2 v = __ldg(m + i);
     return mk(v.x, v.y);
   }
+  static __device__ __forceinline__ void st(float2* m, long long i, df64 v) { m[i] = make_float2(v.hi, v.lo); }
 };
 template <> struct VMetric<float> {
   using type = float;
   static __device__ __forceinline__ float ld(const float* m, long long i) { return __ldg(m + i); }
+  static __device__ __forceinline__ void st(float* m, long long i, float v) { m[i] = v; }
 };
 
 // last block whose offset (pad_off, or vface_off[dir] when dir >= 0) is <= x
@@ -49,6 +54,8 @@ __device__ __forceinline__ int find_block(const FvBlockDev* __restrict__ B, int 
 template <class T>
 __global__ void visc_vars_kernel(const FvViscArgs a) {
   using S = Sc<T>;
+  using V = VMetric<T>;
+  typename V::type* wv = reinterpret_cast<typename V::type*>(a.wvar);
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < a.pad_total;
        x += (long long)gridDim.x * blockDim.x) {
     const FvBlockDev& B = a.blocks[find_block(a.blocks, a.nblocks, x, -1)];
@@ -59,7 +66,7 @@ __global__ void visc_vars_kernel(const FvViscArgs a) {
     const double r = a.q[qi];
     if (!(r > 0.0)) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) a.wvar[m * a.pad_total + x] = 0.0;
+      for (int m = 0; m < 4; ++m) V::st(wv, m * a.pad_total + x, S::c(0.0));
       continue;
     }
     const T rho = S::from_d(r);
@@ -69,18 +76,22 @@ __global__ void visc_vars_kernel(const FvViscArgs a) {
     const T w = S::from_d(a.q[qi + 3 * B.plane]) * ri;
     const T p = S::c(a.vp.gamma - 1.0) * (S::from_d(a.q[qi + 4 * B.plane]) - S::c(0.5) * rho * (u * u + v * v + w * w));
     const T temp = p * ri * S::c(1.0 / a.vp.r_gas);
-    a.wvar[x] = S::to_d(u);
-    a.wvar[a.pad_total + x] = S::to_d(v);
-    a.wvar[2 * a.pad_total + x] = S::to_d(w);
-    a.wvar[3 * a.pad_total + x] = S::to_d(temp);
+    V::st(wv, x, u);
+    V::st(wv, a.pad_total + x, v);
+    V::st(wv, 2 * a.pad_total + x, w);
+    V::st(wv, 3 * a.pad_total + x, temp);
   }
 }
 
 template <class T>
 __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
   using S = Sc<T>;
-  using MT = typename VMetric<T>::type;
+  using V = VMetric<T>;
+  using MT = typename V::type;
   const MT* metric = reinterpret_cast<const MT*>(a.metric);
+  const MT* geo = reinterpret_cast<const MT*>(a.geo);
+  const MT* wv = reinterpret_cast<const MT*>(a.wvar);
+  MT* fv = reinterpret_cast<MT*>(a.fv);
   const long long P = a.pad_total;
   const int b_ax = dir == 0 ? 1 : 0, c_ax = dir == 2 ? 1 : 2;
   const bool three = a.vp.dim == 3;
@@ -111,30 +122,27 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
     }
     // auxiliary volume: mean volume and mean averaged face vectors of L and R
     const T half = S::c(0.5), quarter = S::c(0.25);
-    const T iOm = S::rcp(half * (S::from_d(a.geo[pL]) + S::from_d(a.geo[pR])));
+    const T iOm = S::rcp(half * (V::ld(geo, pL) + V::ld(geo, pR)));
     // families of the face's own axis (a) and of the tangential axes b, c
     T Aa[3], Ab[3], Ac[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      const double* ga = a.geo + (long long)(1 + 3 * dir + x) * P;
-      const double* gb = a.geo + (long long)(1 + 3 * b_ax + x) * P;
-      const double* gc = a.geo + (long long)(1 + 3 * c_ax + x) * P;
-      Aa[x] = half * (S::from_d(ga[pL]) + S::from_d(ga[pR]));
-      Ab[x] = half * (S::from_d(gb[pL]) + S::from_d(gb[pR]));
-      Ac[x] = half * (S::from_d(gc[pL]) + S::from_d(gc[pR]));
+      const long long oa = (long long)(1 + 3 * dir + x) * P, ob = (long long)(1 + 3 * b_ax + x) * P;
+      const long long oc = (long long)(1 + 3 * c_ax + x) * P;
+      Aa[x] = half * (V::ld(geo, oa + pL) + V::ld(geo, oa + pR));
+      Ab[x] = half * (V::ld(geo, ob + pL) + V::ld(geo, ob + pR));
+      Ac[x] = half * (V::ld(geo, oc + pL) + V::ld(geo, oc + pR));
     }
     // gradients of u, v, w, T
     T grad[4][3];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const double* W = a.wvar + m * P;
-      const T da = S::from_d(W[pR]) - S::from_d(W[pL]);
-      const T db = quarter * ((S::from_d(W[pL + sb]) - S::from_d(W[pL - sb])) +
-                              (S::from_d(W[pR + sb]) - S::from_d(W[pR - sb])));
+      const MT* W = wv + m * P;
+      const T da = V::ld(W, pR) - V::ld(W, pL);
+      const T db = quarter * ((V::ld(W, pL + sb) - V::ld(W, pL - sb)) + (V::ld(W, pR + sb) - V::ld(W, pR - sb)));
       T dc = S::c(0.0);
       if (three)
-        dc = quarter * ((S::from_d(W[pL + sc]) - S::from_d(W[pL - sc])) +
-                        (S::from_d(W[pR + sc]) - S::from_d(W[pR - sc])));
+        dc = quarter * ((V::ld(W, pL + sc) - V::ld(W, pL - sc)) + (V::ld(W, pR + sc) - V::ld(W, pR - sc)));
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         T g = da * Aa[x] + db * Ab[x];
@@ -145,8 +153,8 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
     // face values, viscosity, conductivity
     T uf[3];
 #pragma unroll
-    for (int x = 0; x < 3; ++x) uf[x] = half * (S::from_d(a.wvar[x * P + pL]) + S::from_d(a.wvar[x * P + pR]));
-    const T Tf = half * (S::from_d(a.wvar[3 * P + pL]) + S::from_d(a.wvar[3 * P + pR]));
+    for (int x = 0; x < 3; ++x) uf[x] = half * (V::ld(wv, x * P + pL) + V::ld(wv, x * P + pR));
+    const T Tf = half * (V::ld(wv, 3 * P + pL) + V::ld(wv, 3 * P + pR));
     T mu = S::c(a.vp.mu);
     if (a.vp.sutherland) {
       const T tr = Tf * S::c(1.0 / a.vp.t_ref);
@@ -165,11 +173,11 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
         if (x == y) t = t - S::c(2.0 / 3.0) * div;
         fx = fx + mu * t * Sv[y];
       }
-      a.fv[x * a.vstride + f] = S::to_d(fx);
+      V::st(fv, x * a.vstride + f, fx);
       energy = energy + fx * uf[x];
     }
     energy = energy + kc * (grad[3][0] * Sx + grad[3][1] * Sy + grad[3][2] * Sz);
-    a.fv[3 * a.vstride + f] = S::to_d(energy);
+    V::st(fv, 3 * a.vstride + f, energy);
   }
 }
 
