@@ -56,9 +56,9 @@ struct fv_ctx {
   // laminar viscous terms
   long long pad_total = 0;          // cells of all blocks padded by one layer
   long long nvfaces[3] = {0, 0, 0}; // faces per direction, every block
-  double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total], binary64 (setup)
-  void* geo_t = nullptr;            // the same in the form's storage type (== geo for binary64)
-  void* wvar = nullptr;             // face variables (u, v, w, T) [4][pad_total], storage type
+  double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total], binary64 (setup only)
+  void* geo_t = nullptr;            // the same as per-cell records [pad_total][12], storage type
+  void* wvar = nullptr;             // face variables (u, v, w, T) [pad_total][4], storage type
   void* fvis[3] = {nullptr, nullptr, nullptr};    // viscous face fluxes [4][nvfaces[d]], storage type
   struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
   EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
@@ -430,11 +430,15 @@ __global__ void geo_cart_kernel(FvBlockDev B, long long P, double* geo) {
   }
 }
 
-// binary64 -> the storage type of a form
+// geometry planes [10][P] in binary64 -> per-cell records [P][12] in the
+// storage type of a form (the last two entries of a record are padding)
 template <class MT>
-__global__ void convert_kernel(const double* in, MT* out, long long n) {
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
-    store_metric(out, x, in[x]);
+__global__ void geo_records_kernel(const double* in, MT* out, long long P) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < P; x += (long long)gridDim.x * blockDim.x) {
+    for (int c = 0; c < 10; ++c) store_metric(out, 12 * x + c, in[c * P + x]);
+    store_metric(out, 12 * x + 10, 0.0);
+    store_metric(out, 12 * x + 11, 0.0);
+  }
 }
 
 // ghost-cell geometry: dst <- src with face family d taken from family
@@ -1156,15 +1160,15 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     CK(hp, cudaDeviceSynchronize());
     rc = build_visc_tables(hp);
     if (rc) { g_create_error = h->err; fv_destroy(reinterpret_cast<fv_handle>(h.release())); return rc; }
-    if (cfg->precision == FV_PREC_FP64) {
-      h->geo_t = h->geo;
-    } else {
-      const long long n = 10 * h->pad_total;
-      CK(hp, cudaMalloc(&h->geo_t, (size_t)mb * n));
-      if (cfg->precision == FV_PREC_DF64)
-        convert_kernel<<<grid_for(n, 256, h->nsm), 256>>>(h->geo, (float2*)h->geo_t, n);
+    {
+      const long long P = h->pad_total;
+      CK(hp, cudaMalloc(&h->geo_t, (size_t)mb * 12 * P));
+      if (cfg->precision == FV_PREC_FP64)
+        geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (double*)h->geo_t, P);
+      else if (cfg->precision == FV_PREC_DF64)
+        geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (float2*)h->geo_t, P);
       else
-        convert_kernel<<<grid_for(n, 256, h->nsm), 256>>>(h->geo, (float*)h->geo_t, n);
+        geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (float*)h->geo_t, P);
       CK(hp, cudaDeviceSynchronize());
       cudaFree(h->geo);
       h->geo = nullptr;
@@ -1191,7 +1195,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
-  if (h->geo_t != h->geo) cudaFree(h->geo_t);
+  cudaFree(h->geo_t);
   cudaFree(h->geo); cudaFree(h->wvar); cudaFree(h->d_edges);
   for (int d = 0; d < 3; ++d) cudaFree(h->fvis[d]);
   delete h;

@@ -141,11 +141,12 @@ struct FvViscParams {
   int sutherland, dim;
 };
 
-// Padded-cell geometry of the auxiliary volumes: 10 planes of pad_total cells
-// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta); face variables: 4 planes (u, v, w, T);
-// both, and the fluxes, in the storage type of the form (binary64 for the
-// binary64 form, (hi, lo) binary32 pairs for double-float, binary32 for the
-// binary32-flux form), so that the kernels convert nothing.
+// Padded-cell geometry of the auxiliary volumes: a 12-entry record per cell
+// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, 2 pads); face variables: a 4-entry
+// record per cell (u, v, w, T); both, and the fluxes, in the storage type of
+// the form (binary64 for the binary64 form, (hi, lo) binary32 pairs for
+// double-float, binary32 for the binary32-flux form), so that the kernels
+// convert nothing and read a cell with 16-byte loads.
 struct FvViscArgs {
   const FvBlockDev* blocks;
   int nblocks;

@@ -38,6 +38,67 @@ template <> struct VMetric<float> {
   static __device__ __forceinline__ void st(float* m, long long i, float v) { m[i] = v; }
 };
 
+// Per-cell records: the face variables (u, v, w, T) and the geometry
+// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, 2 pads) of a padded cell lie
+// together, 4 and 12 values of the storage type, read with 16-byte loads.
+template <class T> struct VRec;
+template <> struct VRec<double> {
+  static __device__ __forceinline__ void ld4(const double* p, long long c, double o[4]) {
+    const double2* q = reinterpret_cast<const double2*>(p + 4 * c);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  static __device__ __forceinline__ void st4(double* p, long long c, const double v[4]) {
+    double2* q = reinterpret_cast<double2*>(p + 4 * c);
+    q[0] = make_double2(v[0], v[1]);
+    q[1] = make_double2(v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ld10(const double* p, long long c, double o[10]) {
+    const double2* q = reinterpret_cast<const double2*>(p + 12 * c);
+#pragma unroll
+    for (int x = 0; x < 5; ++x) {
+      const double2 a = __ldg(q + x);
+      o[2 * x] = a.x; o[2 * x + 1] = a.y;
+    }
+  }
+};
+template <> struct VRec<df64> {
+  static __device__ __forceinline__ void ld4(const float2* p, long long c, df64 o[4]) {
+    const float4* q = reinterpret_cast<const float4*>(p + 4 * c);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    o[0] = mk(a.x, a.y); o[1] = mk(a.z, a.w); o[2] = mk(b.x, b.y); o[3] = mk(b.z, b.w);
+  }
+  static __device__ __forceinline__ void st4(float2* p, long long c, const df64 v[4]) {
+    float4* q = reinterpret_cast<float4*>(p + 4 * c);
+    q[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    q[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+  }
+  static __device__ __forceinline__ void ld10(const float2* p, long long c, df64 o[10]) {
+    const float4* q = reinterpret_cast<const float4*>(p + 12 * c);
+#pragma unroll
+    for (int x = 0; x < 5; ++x) {
+      const float4 a = __ldg(q + x);
+      o[2 * x] = mk(a.x, a.y); o[2 * x + 1] = mk(a.z, a.w);
+    }
+  }
+};
+template <> struct VRec<float> {
+  static __device__ __forceinline__ void ld4(const float* p, long long c, float o[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p + 4 * c));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+  static __device__ __forceinline__ void st4(float* p, long long c, const float v[4]) {
+    *reinterpret_cast<float4*>(p + 4 * c) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ld10(const float* p, long long c, float o[10]) {
+    const float4* q = reinterpret_cast<const float4*>(p + 12 * c);
+    const float4 a = __ldg(q), b = __ldg(q + 1), d = __ldg(q + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    o[8] = d.x; o[9] = d.y;
+  }
+};
+
 // last block whose offset (pad_off, or vface_off[dir] when dir >= 0) is <= x
 __device__ __forceinline__ int find_block(const FvBlockDev* __restrict__ B, int n, long long x, int dir) {
   int lo = 0, hi = n - 1;
@@ -65,8 +126,8 @@ __global__ void visc_vars_kernel(const FvViscArgs a) {
     const long long qi = B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
     const double r = a.q[qi];
     if (!(r > 0.0)) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) V::st(wv, m * a.pad_total + x, S::c(0.0));
+      const T z[4] = {S::c(0.0), S::c(0.0), S::c(0.0), S::c(0.0)};
+      VRec<T>::st4(wv, x, z);
       continue;
     }
     const T rho = S::from_d(r);
@@ -76,10 +137,8 @@ __global__ void visc_vars_kernel(const FvViscArgs a) {
     const T w = S::from_d(a.q[qi + 3 * B.plane]) * ri;
     const T p = S::c(a.vp.gamma - 1.0) * (S::from_d(a.q[qi + 4 * B.plane]) - S::c(0.5) * rho * (u * u + v * v + w * w));
     const T temp = p * ri * S::c(1.0 / a.vp.r_gas);
-    V::st(wv, x, u);
-    V::st(wv, a.pad_total + x, v);
-    V::st(wv, 2 * a.pad_total + x, w);
-    V::st(wv, 3 * a.pad_total + x, temp);
+    const T rec[4] = {u, v, w, temp};
+    VRec<T>::st4(wv, x, rec);
   }
 }
 
@@ -89,8 +148,8 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
   using V = VMetric<T>;
   using MT = typename V::type;
   const MT* metric = reinterpret_cast<const MT*>(a.metric);
-  const MT* geo = reinterpret_cast<const MT*>(a.geo);
-  const MT* wv = reinterpret_cast<const MT*>(a.wvar);
+  const MT* geo = reinterpret_cast<const MT*>(a.geo);    // [pad cells][12]
+  const MT* wv = reinterpret_cast<const MT*>(a.wvar);    // [pad cells][4]
   MT* fv = reinterpret_cast<MT*>(a.fv);
   const long long P = a.pad_total;
   const int b_ax = dir == 0 ? 1 : 0, c_ax = dir == 2 ? 1 : 2;
@@ -122,27 +181,41 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
     }
     // auxiliary volume: mean volume and mean averaged face vectors of L and R
     const T half = S::c(0.5), quarter = S::c(0.25);
-    const T iOm = S::rcp(half * (V::ld(geo, pL) + V::ld(geo, pR)));
+    T gl[10], gr[10];
+    VRec<T>::ld10(geo, pL, gl);
+    VRec<T>::ld10(geo, pR, gr);
+    const T iOm = S::rcp(half * (gl[0] + gr[0]));
     // families of the face's own axis (a) and of the tangential axes b, c
     T Aa[3], Ab[3], Ac[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      const long long oa = (long long)(1 + 3 * dir + x) * P, ob = (long long)(1 + 3 * b_ax + x) * P;
-      const long long oc = (long long)(1 + 3 * c_ax + x) * P;
-      Aa[x] = half * (V::ld(geo, oa + pL) + V::ld(geo, oa + pR));
-      Ab[x] = half * (V::ld(geo, ob + pL) + V::ld(geo, ob + pR));
-      Ac[x] = half * (V::ld(geo, oc + pL) + V::ld(geo, oc + pR));
+      Aa[x] = half * (dir == 0 ? gl[1 + x] + gr[1 + x] : (dir == 1 ? gl[4 + x] + gr[4 + x] : gl[7 + x] + gr[7 + x]));
+      Ab[x] = half * (b_ax == 0 ? gl[1 + x] + gr[1 + x] : gl[4 + x] + gr[4 + x]);
+      Ac[x] = half * (c_ax == 1 ? gl[4 + x] + gr[4 + x] : gl[7 + x] + gr[7 + x]);
+    }
+    // the stencil: L, R and their neighbours along b (and c)
+    T wL[4], wR[4], wLbm[4], wLbp[4], wRbm[4], wRbp[4];
+    VRec<T>::ld4(wv, pL, wL);
+    VRec<T>::ld4(wv, pR, wR);
+    VRec<T>::ld4(wv, pL - sb, wLbm);
+    VRec<T>::ld4(wv, pL + sb, wLbp);
+    VRec<T>::ld4(wv, pR - sb, wRbm);
+    VRec<T>::ld4(wv, pR + sb, wRbp);
+    T wLcm[4], wLcp[4], wRcm[4], wRcp[4];
+    if (three) {
+      VRec<T>::ld4(wv, pL - sc, wLcm);
+      VRec<T>::ld4(wv, pL + sc, wLcp);
+      VRec<T>::ld4(wv, pR - sc, wRcm);
+      VRec<T>::ld4(wv, pR + sc, wRcp);
     }
     // gradients of u, v, w, T
     T grad[4][3];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const MT* W = wv + m * P;
-      const T da = V::ld(W, pR) - V::ld(W, pL);
-      const T db = quarter * ((V::ld(W, pL + sb) - V::ld(W, pL - sb)) + (V::ld(W, pR + sb) - V::ld(W, pR - sb)));
+      const T da = wR[m] - wL[m];
+      const T db = quarter * ((wLbp[m] - wLbm[m]) + (wRbp[m] - wRbm[m]));
       T dc = S::c(0.0);
-      if (three)
-        dc = quarter * ((V::ld(W, pL + sc) - V::ld(W, pL - sc)) + (V::ld(W, pR + sc) - V::ld(W, pR - sc)));
+      if (three) dc = quarter * ((wLcp[m] - wLcm[m]) + (wRcp[m] - wRcm[m]));
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         T g = da * Aa[x] + db * Ab[x];
@@ -153,8 +226,8 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
     // face values, viscosity, conductivity
     T uf[3];
 #pragma unroll
-    for (int x = 0; x < 3; ++x) uf[x] = half * (V::ld(wv, x * P + pL) + V::ld(wv, x * P + pR));
-    const T Tf = half * (V::ld(wv, 3 * P + pL) + V::ld(wv, 3 * P + pR));
+    for (int x = 0; x < 3; ++x) uf[x] = half * (wL[x] + wR[x]);
+    const T Tf = half * (wL[3] + wR[3]);
     T mu = S::c(a.vp.mu);
     if (a.vp.sutherland) {
       const T tr = Tf * S::c(1.0 / a.vp.t_ref);
