@@ -59,7 +59,7 @@ __global__ void adj_face_kernel(const FvBlockDev B, int dir, const double* __res
       nx = B.cart_n[dir][0]; ny = B.cart_n[dir][1]; nz = B.cart_n[dir][2]; A = B.cart_area[dir];
     } else {
       const long long fi = B.face_off[dir] + f;
-      nx = metric[fi]; ny = metric[fi + mstride]; nz = metric[fi + 2 * mstride]; A = metric[fi + 3 * mstride];
+      nx = metric[4 * fi]; ny = metric[4 * fi + 1]; nz = metric[4 * fi + 2]; A = metric[4 * fi + 3];
     }
     double qbar[4][5] = {}, F[5];
     face_vjp(P, q, nx, ny, nz, A, Fb, qbar, F);

@@ -143,10 +143,11 @@ __global__ void metrics_faces_kernel(const double* nodes, int ni, int nj, int nk
     double S[3];
     cross_half(p[0], p[1], p[2], p[3], S);
     const double A = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-    store_metric(out, off + f, S[0] / A);
-    store_metric(out, off + f + mstride, S[1] / A);
-    store_metric(out, off + f + 2 * mstride, S[2] / A);
-    store_metric(out, off + f + 3 * mstride, A);
+    // one record per face: (n_x, n_y, n_z, |S|)
+    store_metric(out, 4 * (off + f), S[0] / A);
+    store_metric(out, 4 * (off + f) + 1, S[1] / A);
+    store_metric(out, 4 * (off + f) + 2, S[2] / A);
+    store_metric(out, 4 * (off + f) + 3, A);
   }
 }
 
@@ -339,7 +340,7 @@ __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBc
                                                : ((long long)tf * B.nj + tj) * B.ni + ti));
       const MT* m = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
       const long long ms = ax == 0 ? ms0 : (ax == 1 ? ms1 : ms2);
-      n0 = metric_d(m, fi); n1 = metric_d(m, fi + ms); n2 = metric_d(m, fi + 2 * ms);
+      n0 = metric_d(m, 4 * fi); n1 = metric_d(m, 4 * fi + 1); n2 = metric_d(m, 4 * fi + 2);
     }
     const long long i1 = at(side ? ext - 1 : 0);   // first interior cell
     double qb[5];

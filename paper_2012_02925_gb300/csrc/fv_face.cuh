@@ -7,6 +7,7 @@
 //    Psi^{+/-}; each limiter value multiplies the difference that is the
 //    denominator of its ratio, so a limited term is Psi(a/b) b.
 #pragma once
+#include <type_traits>
 #include "fv_arith.cuh"
 #include "fv_internal.h"
 
@@ -140,7 +141,8 @@ __device__ __forceinline__ void muscl(const CC& C, T vm1, T v0, T vp1, T vp2, T&
   }
 }
 
-// Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d
+// Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d (a branch: the fix is
+// rare, near sonic points; a select costing both sides always was slower)
 template <class T, class CC>
 __device__ __forceinline__ T entropy_fixed(const CC& C, T lam, T delta) {
   if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * (C.half * Sc<T>::rcp(delta));

@@ -71,8 +71,8 @@ struct FvStageArgs {
   const double* qin;            // Q^(m-1)
   const double* q0;             // Q^(0)
   double* qout;                 // Q^(m)
-  const void* metric[3];        // per direction: nx, ny, nz, area planes
-  long long mstride[3];         // per direction: faces in all blocks (plane length)
+  const void* metric[3];        // per direction: one (n_x, n_y, n_z, |S|) record per face
+  long long mstride[3];         // per direction: faces in all blocks
   const double* invvol;         // 1/Omega per interior cell
   const double* srcvol;         // S*Omega, [block][5][cells], or null
   const float2* srcvol2;        // the same as double-float (hi, lo) pairs, or null

@@ -21,9 +21,17 @@
 #include "fv_face.cuh"
 
 template <class T> struct MetricStore;
+// Face metrics are one (n_x, n_y, n_z, |S|) record per face, read with
+// 16-byte loads (ld4); ld reads one value (the viscous face fluxes).
 template <> struct MetricStore<double> {
   using type = double;
   static __device__ __forceinline__ double ld(const double* p, long long i) { return __ldg(p + i); }
+  static __device__ __forceinline__ void ld4(const double* p, long long f, double& a, double& b, double& c,
+                                             double& d) {
+    const double2* q = reinterpret_cast<const double2*>(p + 4 * f);
+    const double2 x = __ldg(q), y = __ldg(q + 1);
+    a = x.x; b = x.y; c = y.x; d = y.y;
+  }
 };
 template <> struct MetricStore<df64> {
   using type = float2;
@@ -31,10 +39,19 @@ template <> struct MetricStore<df64> {
     float2 v = __ldg(p + i);
     return mk(v.x, v.y);
   }
+  static __device__ __forceinline__ void ld4(const float2* p, long long f, df64& a, df64& b, df64& c, df64& d) {
+    const float4* q = reinterpret_cast<const float4*>(p + 4 * f);
+    const float4 x = __ldg(q), y = __ldg(q + 1);
+    a = mk(x.x, x.y); b = mk(x.z, x.w); c = mk(y.x, y.y); d = mk(y.z, y.w);
+  }
 };
 template <> struct MetricStore<float> {
   using type = float;
   static __device__ __forceinline__ float ld(const float* p, long long i) { return __ldg(p + i); }
+  static __device__ __forceinline__ void ld4(const float* p, long long f, float& a, float& b, float& c, float& d) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p + 4 * f));
+    a = x.x; b = x.y; c = x.z; d = x.w;
+  }
 };
 
 // accumulation type: binary32 face fluxes are summed in double-float
@@ -103,7 +120,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
   const MT* mxi = reinterpret_cast<const MT*>(args.metric[0]);
   const MT* meta = reinterpret_cast<const MT*>(args.metric[1]);
   const MT* mzeta = reinterpret_cast<const MT*>(args.metric[2]);
-  const long long msx = args.mstride[0], msy = args.mstride[1], msz = args.mstride[2];
 
   // Tiles 0..gridDim-1 go to the CTAs in order; later ones are handed out
   // dynamically (largest first, as the table is sorted) through a counter
@@ -187,9 +203,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         nz = S::from_d(B.cart_n[dir][2]); A = S::from_d(B.cart_area[dir]);
       } else {
         const MT* m = dir == 0 ? mxi : (dir == 1 ? meta : mzeta);
-        const long long ms = dir == 0 ? msx : (dir == 1 ? msy : msz);
-        nx = MetricStore<T>::ld(m, f); ny = MetricStore<T>::ld(m, f + ms);
-        nz = MetricStore<T>::ld(m, f + 2 * ms); A = MetricStore<T>::ld(m, f + 3 * ms);
+        MetricStore<T>::ld4(m, f, nx, ny, nz, A);
       }
       T out[5];
       if (code == FV_BCK_SLIP_WALL || code == FV_BCK_NOSLIP_WALL) {

@@ -173,11 +173,11 @@ __global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
       Sy = S::from_d(B.cart_n[dir][1]) * A;
       Sz = S::from_d(B.cart_n[dir][2]) * A;
     } else {
-      const long long fi = B.face_off[dir] + loc;
-      const T A = VMetric<T>::ld(metric, fi + 3 * a.mstride);
+      const long long fi = 4 * (B.face_off[dir] + loc);     // (n_x, n_y, n_z, |S|) record
+      const T A = VMetric<T>::ld(metric, fi + 3);
       Sx = VMetric<T>::ld(metric, fi) * A;
-      Sy = VMetric<T>::ld(metric, fi + a.mstride) * A;
-      Sz = VMetric<T>::ld(metric, fi + 2 * a.mstride) * A;
+      Sy = VMetric<T>::ld(metric, fi + 1) * A;
+      Sz = VMetric<T>::ld(metric, fi + 2) * A;
     }
     // auxiliary volume: mean volume and mean averaged face vectors of L and R
     const T half = S::c(0.5), quarter = S::c(0.25);
