@@ -92,7 +92,7 @@ __device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]
   V[1] = u;
   V[2] = v;
   V[3] = w;
-  V[4] = C.gm1 * (q[4] - C.half * q[0] * (u * u + v * v + w * w));
+  V[4] = C.gm1 * (q[4] - Sc<T>::halve(q[0]) * (u * u + v * v + w * w));
 }
 
 // Half the van Leer limited slope, Psi(a/b) b / 2 with Psi(r) = (r + |r|)/(1 + |r|).
@@ -105,7 +105,7 @@ template <class T>
 __device__ __forceinline__ T vanleer_half(T a, T b) {
   using S = Sc<T>;
   const T p = a * b, s = a + b;
-  const T h = p * S::rcp(s);
+  const T h = S::div(p, s);
   return S::sel(S::pos(p) && S::above(S::abs(s), 1e-30f), h, S::c(0.0));
 }
 
@@ -145,7 +145,7 @@ __device__ __forceinline__ void muscl(const CC& C, T vm1, T v0, T vp1, T vp2, T&
 // rare, near sonic points; a select costing both sides always was slower)
 template <class T, class CC>
 __device__ __forceinline__ T entropy_fixed(const CC& C, T lam, T delta) {
-  if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * (C.half * Sc<T>::rcp(delta));
+  if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * Sc<T>::halve(Sc<T>::rcp(delta));
   return lam;
 }
 
@@ -160,8 +160,8 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   const T VnL = nx * uL + ny * vL + nz * wL;
   const T VnR = nx * uR + ny * vR + nz * wR;
   const T riL = S::rcp(rL), riR = S::rcp(rR);
-  const T hL = C.g_gm1 * pL * riL + C.half * (uL * uL + vL * vL + wL * wL);
-  const T hR = C.g_gm1 * pR * riR + C.half * (uR * uR + vR * vR + wR * wR);
+  const T hL = C.g_gm1 * pL * riL + S::halve(uL * uL + vL * vL + wL * wL);
+  const T hR = C.g_gm1 * pR * riR + S::halve(uR * uR + vR * vR + wR * wR);
   const T mL = rL * VnL, mR = rR * VnR;
 
   // Roe averages: R = sqrt(rho_R/rho_L), rho~ = rho_L R
@@ -172,7 +172,7 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   const T vt = (vL + Rt * vR) * w1;
   const T wt = (wL + Rt * wR) * w1;
   const T ht = (hL + Rt * hR) * w1;
-  const T q2h = C.half * (ut * ut + vt * vt + wt * wt);
+  const T q2h = S::halve(ut * ut + vt * vt + wt * wt);
   const T c2 = C.gm1 * (ht - q2h);
   const T ct = S::sqrt(c2);
   const T ic2 = S::rcp(c2);
@@ -189,7 +189,7 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
     if (C.k_fixall()) l2 = entropy_fixed(C, l2, delta);
   }
   const T rcd = rt * ct * dVn;
-  const T hic2 = C.half * ic2;
+  const T hic2 = S::halve(ic2);
   const T a1 = l1 * (dp - rcd) * hic2;
   const T a5 = l5 * (dp + rcd) * hic2;
   const T a2 = l2 * (dr - dp * ic2);
@@ -203,7 +203,7 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   T D3 = a15 * wt + d51 * nz + a2 * wt + a3 * (dw - nz * dVn);
   T D4 = a15 * ht + d51 * Vnt + a2 * q2h + a3 * (ut * du + vt * dv + wt * dw - Vnt * dVn);
 
-  const T hA = C.half * A;
+  const T hA = S::halve(A);
   out[0] = ((mL + mR) - D0) * hA;
   out[1] = ((mL * uL + mR * uR + nx * (pL + pR)) - D1) * hA;
   out[2] = ((mL * vL + mR * vR + ny * (pL + pR)) - D2) * hA;
