@@ -563,17 +563,20 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
 
 int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
   int rc;
-  if (h->cfg.visc) {
+  const FvLaunch& l = h->launch;
+  if (h->cfg.visc && !l.visc) {
+    // binary64 and double-float: the viscous fluxes by the separate kernels
     rc = do_visc(h, a.qin, s);
     if (rc) return rc;
   }
   switch (h->cfg.precision) {
-    case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, h->launch, s); break;
+    case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, l, s); break;
     case FV_PREC_DF64:
-      rc = h->launch.fast ? fv_launch_stage_df64_fast(a, h->launch, s) : fv_launch_stage_df64(a, h->launch, s);
+      rc = l.fast ? fv_launch_stage_df64_fast(a, l, s) : fv_launch_stage_df64(a, l, s);
       break;
     default:
-      rc = h->launch.fast ? fv_launch_stage_fp32_fast(a, h->launch, s) : fv_launch_stage_fp32(a, h->launch, s);
+      if (l.visc) rc = l.fast ? fv_launch_stage_fp32_fast_visc(a, l, s) : fv_launch_stage_fp32_visc(a, l, s);
+      else rc = l.fast ? fv_launch_stage_fp32_fast(a, l, s) : fv_launch_stage_fp32(a, l, s);
       break;
   }
   if (rc == -2) return fail(h, FV_ERR_UNSUPPORTED, "tile shape not compiled");
@@ -601,8 +604,20 @@ FvStageArgs base_args(fv_ctx* h) {
   a.fp.limiter = h->cfg.limiter;
   a.fp.fix_all = h->cfg.fix_all;
   a.fp.flux = h->cfg.flux;
-  if (h->cfg.visc)
+  if (h->cfg.visc && h->launch.visc) {
+    // binary32: viscous terms fused into the stage kernel
+    a.geo = h->geo_t;
+    a.vp.gamma = h->cfg.gamma;
+    a.vp.mu = h->cfg.mu;
+    a.vp.r_gas = h->cfg.r_gas;
+    a.vp.kfac = h->cfg.gamma * h->cfg.r_gas / ((h->cfg.gamma - 1.0) * h->cfg.prandtl);
+    a.vp.t_ref = h->cfg.t_ref;
+    a.vp.s_suth = h->cfg.s_suth;
+    a.vp.sutherland = h->cfg.sutherland;
+    a.vp.dim = h->cfg.dim;
+  } else if (h->cfg.visc) {
     for (int d = 0; d < h->cfg.dim; ++d) { a.fv[d] = h->fvis[d]; a.vstride[d] = h->nvfaces[d]; }
+  }
   return a;
 }
 
@@ -708,6 +723,10 @@ void choose_launch(fv_ctx* h) {
   l.ty = FV_SHAPE_TABLE[shape - 1][1];
   l.threads = FV_SHAPE_TABLE[shape - 1][2];
   l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.eps, c.kappa, c.harten, c.fix_all);
+  // the binary32 form fuses the viscous faces into the stage kernel (its T on
+  // the fly costs a MUFU reciprocal); for binary64 and double-float the
+  // separate kernels measured faster
+  l.visc = c.visc && c.precision == FV_PREC_FP32FLUX;
   h->launch = l;
 }
 
@@ -717,6 +736,9 @@ int query_occupancy(fv_ctx* h, size_t* smem) {
     case FV_PREC_DF64:
       return h->launch.fast ? fv_stage_occupancy_df64_fast(h->launch, smem) : fv_stage_occupancy_df64(h->launch, smem);
     default:
+      if (h->launch.visc)
+        return h->launch.fast ? fv_stage_occupancy_fp32_fast_visc(h->launch, smem)
+                              : fv_stage_occupancy_fp32_visc(h->launch, smem);
       return h->launch.fast ? fv_stage_occupancy_fp32_fast(h->launch, smem) : fv_stage_occupancy_fp32(h->launch, smem);
   }
 }
@@ -1098,8 +1120,10 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
   if (cfg->visc) {
     CK(hp, cudaMalloc(&h->geo, sizeof(double) * 10 * h->pad_total));
     CK(hp, cudaMemset(h->geo, 0, sizeof(double) * 10 * h->pad_total));
-    CK(hp, cudaMalloc(&h->wvar, (size_t)mb * 4 * h->pad_total));
-    for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], (size_t)mb * 4 * h->nvfaces[d]));
+    if (cfg->precision != FV_PREC_FP32FLUX) {
+      CK(hp, cudaMalloc(&h->wvar, (size_t)mb * 4 * h->pad_total));
+      for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], (size_t)mb * 4 * h->nvfaces[d]));
+    }
   }
   // ---- metrics ----
   double* d_nodes = nullptr;

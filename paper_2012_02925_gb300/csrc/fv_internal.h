@@ -55,6 +55,12 @@ struct FvBcDev {
   double cstate;                // its speed of sound
 };
 
+struct FvViscParams {
+  double gamma, mu, r_gas, kfac;   // kfac = gamma r_gas / ((gamma - 1) Pr): k = mu kfac
+  double t_ref, s_suth;
+  int sutherland, dim;
+};
+
 struct FvFaceParams {
   double gamma, eps, kappa, harten, va_delta2;
   int limiter, fix_all, flux;
@@ -79,6 +85,9 @@ struct FvStageArgs {
   const void* fv[3];            // viscous face fluxes per direction, [4][faces] (momentum, energy), in the
                                 // form's storage type (binary64, binary32 pairs, binary32), or null
   long long vstride[3];         // faces per direction of fv
+  FvViscParams vp;              // the binary32 form's fused viscous terms (VISC kernels)
+  const void* geo;              // and their 12-entry (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, pads) geometry record
+                                // per cell of every block padded by one layer, binary32
   double* rout;                 // residual output or null
   int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
   long long ncell_total;
@@ -93,6 +102,7 @@ struct FvLaunch {
   int grid;                     // CTAs (persistent)
   int three_d;
   int fast;                     // the kernel with the default scheme compiled in
+  int visc;                     // the kernel with the laminar viscous terms fused in (binary32 form)
 };
 
 // The default scheme (Roe flux, van Leer limiter, eps = 1, kappa = -1,
@@ -115,6 +125,13 @@ int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem_bytes);
+// the binary32 form with the laminar viscous terms fused into the face loop
+// (fv_stage_fp32[_fast]_visc.cu); the other forms evaluate them in separate
+// kernels (fv_visc.cu) and read the per-face fluxes in the cell sums
+int fv_launch_stage_fp32_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_fp32_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_stage_occupancy_fp32_visc(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_fp32_fast_visc(const FvLaunch& l, size_t* smem_bytes);
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
 constexpr int FV_NUM_SHAPES = 8;
@@ -135,11 +152,7 @@ int fv_adjoint_finish(const FvBlockDev& B, const double* lamg, const double* lam
 // ---------------------------------------------------------------------------
 // Laminar viscous terms (fv_visc.cu)
 // ---------------------------------------------------------------------------
-struct FvViscParams {
-  double gamma, mu, r_gas, kfac;   // kfac = gamma r_gas / ((gamma - 1) Pr): k = mu kfac
-  double t_ref, s_suth;
-  int sutherland, dim;
-};
+
 
 // Padded-cell geometry of the auxiliary volumes: a 12-entry record per cell
 // (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, 2 pads); face variables: a 4-entry

@@ -19,6 +19,7 @@
 #include <cuda_pipeline.h>
 #include <type_traits>
 #include "fv_face.cuh"
+#include "fv_viscface.cuh"
 
 template <class T> struct MetricStore;
 // Face metrics are one (n_x, n_y, n_z, |S|) record per face, read with
@@ -96,7 +97,7 @@ constexpr int stage_min_ctas() {
   return sizeof(T) == 4 ? (NT <= 128 ? 8 : 4) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
 }
 
-template <class T, int TX, int TY, int NT, bool DIM3, bool PF, bool FAST>
+template <class T, int TX, int TY, int NT, bool DIM3, bool PF, bool FAST, bool VISC>
 __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel(const FvStageArgs args) {
   using S = Sc<T>;
   using CC = typename std::conditional<FAST, FaceCFast<T>, FaceC<T>>::type;
@@ -117,6 +118,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
 
   const int tid = threadIdx.x;
   const CC C = CC::from(make_face_consts<T>(args.fp));
+  const ViscC<T> VK = make_visc_consts<T>(args.vp);
+  const typename VGeo<T>::type* geo = reinterpret_cast<const typename VGeo<T>::type*>(args.geo);
   const MT* mxi = reinterpret_cast<const MT*>(args.metric[0]);
   const MT* meta = reinterpret_cast<const MT*>(args.metric[1]);
   const MT* mzeta = reinterpret_cast<const MT*>(args.metric[2]);
@@ -195,8 +198,14 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
     // direction `dir` and face index f, storing the 5 fluxes at dst[n * dstr].
     // code: 0, or the boundary kind whose flux overwrites this face (slip
     // wall, farfield); side: 0 on the block's min face, 1 on its max face
+    // vis: the viscous stencil (VISC only): tangential neighbours of L = s1
+    // and R = s2, and the padded-cell index of R (L is one step back)
+    struct VisArgs {
+      const T *Lbm, *Lbp, *Rbm, *Rbp, *Lcm, *Lcp, *Rcm, *Rcp;
+      long long gR, gstep;
+    };
     auto do_face = [&](const T* s0, const T* s1, const T* s2, const T* s3, int dir, long long f, T* dst,
-                       int dstr, int code, int side) {
+                       int dstr, int code, int side, const VisArgs& vis) {
       T nx, ny, nz, A;
       if (cart) {
         nx = S::from_d(B.cart_n[dir][0]); ny = S::from_d(B.cart_n[dir][1]);
@@ -217,6 +226,16 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
         normal_face_flux(C, Vb, nx, ny, nz, A, out);
       } else {
         face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
+      }
+      if constexpr (VISC) {
+        // F_i - F_v: the cell sums below then carry the viscous pairs too
+        T gl[10], gr[10], fvv[4];
+        VGeo<T>::ld10(geo, vis.gR - vis.gstep, gl);
+        VGeo<T>::ld10(geo, vis.gR, gr);
+        viscous_face_flux(VK, s1, s2, vis.Lbm, vis.Lbp, vis.Rbm, vis.Rbp, vis.Lcm, vis.Lcp, vis.Rcm, vis.Rcp, PL,
+                          DIM3, gl, gr, dir, dir == 0 ? 1 : 0, dir == 2 ? 1 : 2, nx * A, ny * A, nz * A, fvv);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) out[1 + n] = out[1 + n] - fvv[n];
       }
 #pragma unroll
       for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
@@ -341,7 +360,33 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
             }
           }
         }
-        do_face(s0, s1, s2, s3, d, f, dp, dstr, code, side);
+        VisArgs vis;
+        if constexpr (VISC) {
+          // cell R of the face in block coordinates, and its tangential
+          // neighbours (and L's) in the plane ring
+          int ri, rj, rk;
+          if (d == 0) {
+            const int fy = dst / (TX + 1);
+            ri = i0 + dst - fy * (TX + 1); rj = j0 + fy; rk = k;
+          } else {
+            const int fy = dst / TX;
+            ri = i0 + dst - fy * TX; rj = j0 + fy; rk = d == 2 ? k + 1 : k;
+          }
+          const long long pi = ni + 2, pij = pi * (nj + 2);
+          vis.gR = B.pad_off + (rk + 1) * pij + (long long)(rj + 1) * pi + (ri + 1);
+          vis.gstep = d == 0 ? 1 : (d == 1 ? pi : pij);
+          const int sb = d == 0 ? W : 1;
+          vis.Lbm = s1 - sb; vis.Lbp = s1 + sb; vis.Rbm = s2 - sb; vis.Rbp = s2 + sb;
+          if (d == 2) {
+            vis.Lcm = s1 - W; vis.Lcp = s1 + W; vis.Rcm = s2 - W; vis.Rcp = s2 + W;
+          } else {
+            const long long oL = s1 - P, oR = s2 - P;
+            const T* Pm = Vs + ((k - 1) & 3) * 5 * PL;
+            const T* Pp = Vs + ((k + 1) & 3) * 5 * PL;
+            vis.Lcm = Pm + oL; vis.Lcp = Pp + oL; vis.Rcm = Pm + oR; vis.Rcp = Pp + oR;
+          }
+        }
+        do_face(s0, s1, s2, s3, d, f, dp, dstr, code, side, vis);
       }
       __syncthreads();
       if (DIM3 && k < k0) continue;
@@ -376,24 +421,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
                 const df64 h2 = two_sum(h.hi, rz.hi);
                 lo = FADD(FADD(lo, rz.lo), h2.lo);
                 h.hi = h2.hi;
-              }
-              if (args.fv[0] && n > 0) {
-                // the viscous pairs (binary32 fluxes)
-                const float* f0 = reinterpret_cast<const float*>(args.fv[0]) + (n - 1) * args.vstride[0];
-                const float* f1 = reinterpret_cast<const float*>(args.fv[1]) + (n - 1) * args.vstride[1];
-                const df64 vxp = two_sum(f0[vx + 1], -f0[vx]);
-                const df64 vyp = two_sum(f1[vy + ni], -f1[vy]);
-                df64 t = two_sum(h.hi, -vxp.hi);
-                lo = FADD(FSUB(lo, vxp.lo), t.lo);
-                t = two_sum(t.hi, -vyp.hi);
-                lo = FADD(FSUB(lo, vyp.lo), t.lo);
-                if (DIM3) {
-                  const float* f2 = reinterpret_cast<const float*>(args.fv[2]) + (n - 1) * args.vstride[2];
-                  const df64 vzp = two_sum(f2[vz + vzs], -f2[vz]);
-                  t = two_sum(t.hi, -vzp.hi);
-                  lo = FADD(FSUB(lo, vzp.lo), t.lo);
-                }
-                h.hi = t.hi;
               }
               if (args.srcvol2) {
                 const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);
@@ -478,27 +505,27 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
 
 // The dynamic shared-memory limit is raised once by occupancy_t (at handle
 // creation), so a launch is a plain enqueue that stream capture accepts.
-template <class T, int TX, int TY, int NT, bool PF, bool FAST>
+template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC>
 static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
   const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0, PF);
   if (l.three_d) {
-    fv_stage_kernel<T, TX, TY, NT, true, PF, FAST><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC><<<l.grid, NT, smem, s>>>(a);
   } else {
-    fv_stage_kernel<T, TX, TY, NT, false, false, FAST><<<l.grid, NT, smem, s>>>(a);
+    fv_stage_kernel<T, TX, TY, NT, false, false, FAST, VISC><<<l.grid, NT, smem, s>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <class T, int TX, int TY, int NT, bool PF, bool FAST>
+template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC>
 static int occupancy_t(bool three_d, size_t* smem_out) {
   const size_t smem = StageSmem<T, TX, TY>::bytes(three_d, PF);
   int n = 0;
   if (three_d) {
-    auto k = fv_stage_kernel<T, TX, TY, NT, true, PF, FAST>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   } else {
-    auto k = fv_stage_kernel<T, TX, TY, NT, false, false, FAST>;
+    auto k = fv_stage_kernel<T, TX, TY, NT, false, false, FAST, VISC>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem);
   }
@@ -522,27 +549,27 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
 
 // FAST selects the compile-time default scheme (FaceCFast); each form's
 // translation units instantiate one value of it.
-template <class T, bool FAST>
+template <class T, bool FAST, bool VISC>
 int fv_dispatch_launch(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
   constexpr bool allow_pf = std::is_same<T, float>::value;
 #define FV_LAUNCH_CASE(ID, TX, TY, NT, PF)                                     \
   if (l.shape == ID) {                                                          \
     if (PF && !allow_pf) return -2;                                             \
-    return launch_stage_t<T, TX, TY, NT, PF && allow_pf, FAST>(a, l, s);        \
+    return launch_stage_t<T, TX, TY, NT, PF && allow_pf, FAST, VISC>(a, l, s);  \
   }
   FV_SHAPES(FV_LAUNCH_CASE)
 #undef FV_LAUNCH_CASE
   return -2;
 }
 
-template <class T, bool FAST>
+template <class T, bool FAST, bool VISC>
 int fv_dispatch_occupancy(const FvLaunch& l, size_t* smem) {
   constexpr bool allow_pf = std::is_same<T, float>::value;
   const bool d3 = l.three_d != 0;
 #define FV_OCC_CASE(ID, TX, TY, NT, PF)                                         \
   if (l.shape == ID) {                                                          \
     if (PF && !allow_pf) return 0;                                              \
-    return occupancy_t<T, TX, TY, NT, PF && allow_pf, FAST>(d3, smem);          \
+    return occupancy_t<T, TX, TY, NT, PF && allow_pf, FAST, VISC>(d3, smem);    \
   }
   FV_SHAPES(FV_OCC_CASE)
 #undef FV_OCC_CASE

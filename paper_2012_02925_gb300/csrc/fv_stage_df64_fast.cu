@@ -2,6 +2,6 @@
 #include "fv_stage.cuh"
 
 int fv_launch_stage_df64_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<df64, true>(a, l, s);
+  return fv_dispatch_launch<df64, true, false>(a, l, s);
 }
-int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<df64, true>(l, smem); }
+int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<df64, true, false>(l, smem); }

@@ -2,6 +2,6 @@
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp32_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<float, true>(a, l, s);
+  return fv_dispatch_launch<float, true, false>(a, l, s);
 }
-int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<float, true>(l, smem); }
+int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<float, true, false>(l, smem); }

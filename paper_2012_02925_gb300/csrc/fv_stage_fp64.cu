@@ -2,6 +2,6 @@
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<double, false>(a, l, s);
+  return fv_dispatch_launch<double, false, false>(a, l, s);
 }
-int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<double, false>(l, smem); }
+int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<double, false, false>(l, smem); }
