@@ -159,23 +159,37 @@ class ClockSampler:
         self._t = None
 
     def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                if out.returncode == 0:
-                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        # one long-lived nvidia-smi in loop mode (a sample every 100 ms); a
+        # process per sample would take longer than the timed region
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                        "--format=csv,noheader,nounits", "-lms", "100"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        for line in self._p.stdout:
+            row = [x.strip() for x in line.strip().split(",")]
+            if len(row) >= 7:
+                self.rows.append(row)
+            if self._stop.is_set():
+                break
 
     def __enter__(self):
+        self._p = None
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
+        time.sleep(0.3)     # let the first sample land before the region starts
         return self
 
     def __exit__(self, *a):
+        time.sleep(0.15)    # one more sample at the end of the region
         self._stop.set()
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
         if self._t:
             self._t.join(timeout=10)
 
@@ -342,10 +356,10 @@ def run_gpu(args):
     value = cell_updates / elapsed / 1e9
     pk, peak_kind = peaks()
     traffic = load_traffic()
-    stage_times, ex_time = time_stage_kernels(s, pb, max(3, args.steps // 2))
+    stage_times, ex_time = time_stage_kernels(s, pb, min(20, max(3, args.steps // 2)))
     roof = roofline(pb, args.precision, stage_times, ex_time, curv, pk, peak_kind, traffic)
     # end to end through the public API with host buffers
-    e2e = run_e2e(s, pb, max(3, args.steps // 4))
+    e2e = run_e2e(s, pb, min(40, max(3, args.steps // 4)))
     launches_per_step = M * (2 if pb.conns else 1)
     result = {
         "metric": "Gcell-updates/s per RK stage",
@@ -470,7 +484,7 @@ def run_variants(args, pk, peak_kind, traffic):
             curv = pb.blocks[0].nodes is not None
             big = pb.ncells > 3e7
             s = make_solver(pb, prec, reps=1 if big else 3)
-            steps = 3 if big else max(3, args.steps // 2)
+            steps = 3 if big else min(10, max(3, args.steps // 2))
             el = time_steps(s, pb, steps, 3)
             st, ex = time_stage_kernels(s, pb, 3)
             out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
@@ -554,7 +568,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # 200 steps of the 128^3 block: a timed region of ~0.7 s, long enough for
+    # several clock samples
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fvgb", choices=["fvgb", "reference"])
     ap.add_argument("--workload", default="mms128")
