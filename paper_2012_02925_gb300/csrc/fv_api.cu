@@ -57,8 +57,10 @@ struct fv_ctx {
   long long pad_total = 0;          // cells of all blocks padded by one layer
   long long nvfaces[3] = {0, 0, 0}; // faces per direction, every block
   double* geo = nullptr;            // auxiliary-volume geometry [10][pad_total], binary64 (setup only)
-  void* geo_t = nullptr;            // the same as per-cell records [pad_total][12], storage type
-  void* wvar = nullptr;             // face variables (u, v, w, T) [pad_total][4], storage type
+  void* geo_t = nullptr;            // binary32 form: the same as per-cell records [pad_total][12]
+  void* fgeo[3] = {nullptr, nullptr, nullptr};    // other forms: face records (G_a, G_b, G_c, S) [nvfaces[d]][12]
+  FvViscTile* d_vtiles = nullptr;   // work units of the viscous face kernel
+  int nvtiles = 0;
   void* fvis[3] = {nullptr, nullptr, nullptr};    // viscous face fluxes [4][nvfaces[d]], storage type
   struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
   EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
@@ -304,8 +306,8 @@ __device__ __forceinline__ void bc_farfield(const BcGas& G, const double Vi[5], 
 
 template <class MT>
 __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBcDev* __restrict__ bcs, int nbc,
-                               long long nitems, const MT* m0, const MT* m1, const MT* m2, long long ms0,
-                               long long ms1, long long ms2, BcGas G, double* q) {
+                               long long nitems, const MT* m0, const MT* m1, const MT* m2, BcGas G,
+                               double* q) {
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
        it += (long long)gridDim.x * blockDim.x) {
     int lo = 0, hi = nbc - 1;
@@ -339,7 +341,6 @@ __global__ void bc_fill_kernel(const FvBlockDev* __restrict__ blocks, const FvBc
                                     : (ax == 1 ? ((long long)tk * (B.nj + 1) + tf) * B.ni + ti
                                                : ((long long)tf * B.nj + tj) * B.ni + ti));
       const MT* m = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-      const long long ms = ax == 0 ? ms0 : (ax == 1 ? ms1 : ms2);
       n0 = metric_d(m, 4 * fi); n1 = metric_d(m, 4 * fi + 1); n2 = metric_d(m, 4 * fi + 2);
     }
     const long long i1 = at(side ? ext - 1 : 0);   // first interior cell
@@ -442,6 +443,42 @@ __global__ void geo_records_kernel(const double* in, MT* out, long long P) {
   }
 }
 
+// per-face gradient geometry of one block and direction (binary64 in, the
+// storage type out): G_d = (Sbar_d(L) + Sbar_d(R)) / 2 / Omega_f for the
+// face's own family a and the tangential families b, c, Omega_f =
+// (Omega_L + Omega_R) / 2, then the face's area vector S = n |S|
+template <class MT>
+__global__ void face_geometry_kernel(FvBlockDev B, int dir, const double* geo, long long P, const MT* metric,
+                                     MT* out) {
+  const int ei = B.ni + (dir == 0), ej = B.nj + (dir == 1), ek = B.nk + (dir == 2);
+  const long long n = (long long)ei * ej * ek;
+  const long long pi = B.ni + 2, pij = pi * (B.nj + 2);
+  const long long sa = dir == 0 ? 1 : (dir == 1 ? pi : pij);
+  const int fam[3] = {dir, dir == 0 ? 1 : 0, dir == 2 ? 1 : 2};
+  for (long long loc = blockIdx.x * (long long)blockDim.x + threadIdx.x; loc < n;
+       loc += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(loc % ei), j = (int)((loc / ei) % ej), k = (int)(loc / ((long long)ei * ej));
+    const long long pR = B.pad_off + (k + 1) * pij + (long long)(j + 1) * pi + (i + 1), pL = pR - sa;
+    const long long o = 12 * (B.vface_off[dir] + loc);
+    const double om = 0.5 * (geo[pL] + geo[pR]);
+    for (int d = 0; d < 3; ++d)
+      for (int x = 0; x < 3; ++x) {
+        const long long r = (long long)(1 + 3 * fam[d] + x) * P;
+        store_metric(out, o + 3 * d + x, 0.5 * (geo[r + pL] + geo[r + pR]) / om);
+      }
+    for (int x = 0; x < 3; ++x) {
+      double S;
+      if (B.cartesian) {
+        S = B.cart_n[dir][x] * B.cart_area[dir];
+      } else {
+        const long long m = 4 * (B.face_off[dir] + loc);
+        S = metric_d(metric, m + x) * metric_d(metric, m + 3);
+      }
+      store_metric(out, o + 9 + x, S);
+    }
+  }
+}
+
 // ghost-cell geometry: dst <- src with face family d taken from family
 // fam_d of the source, times sign_d (code: fam0 | fam1 << 2 | fam2 << 4,
 // negative signs in bits 6, 7, 8)
@@ -537,11 +574,14 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
   FvViscArgs v;
   std::memset(&v, 0, sizeof(v));
   v.blocks = h->d_blocks;
-  v.nblocks = h->nblocks;
-  v.pad_total = h->pad_total;
-  v.geo = h->geo_t;
-  v.wvar = h->wvar;
+  v.tiles = h->d_vtiles;
+  v.ntiles = h->nvtiles;
   v.q = q;
+  for (int d = 0; d < h->cfg.dim; ++d) {
+    v.fgeo[d] = h->fgeo[d];
+    v.fv[d] = h->fvis[d];
+    v.vstride[d] = h->nvfaces[d];
+  }
   v.vp.gamma = h->cfg.gamma;
   v.vp.mu = h->cfg.mu;
   v.vp.r_gas = h->cfg.r_gas;
@@ -550,14 +590,8 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
   v.vp.s_suth = h->cfg.s_suth;
   v.vp.sutherland = h->cfg.sutherland;
   v.vp.dim = h->cfg.dim;
-  if (fv_visc_vars(v, h->cfg.precision, s)) return cuda_fail(h, cudaGetLastError(), "viscous face variables");
-  for (int d = 0; d < h->cfg.dim; ++d) {
-    v.metric = h->metric[d];
-    v.mstride = h->nfaces[d];
-    v.fv = h->fvis[d];
-    v.vstride = h->nvfaces[d];
-    if (fv_visc_faces(v, d, h->cfg.precision, s)) return cuda_fail(h, cudaGetLastError(), "viscous face fluxes");
-  }
+  if (fv_visc_faces(v, h->cfg.precision == FV_PREC_FP64 ? 0 : 1, s))
+    return cuda_fail(h, cudaGetLastError(), "viscous face fluxes");
   return FV_OK;
 }
 
@@ -652,15 +686,15 @@ int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
     if (h->cfg.precision == FV_PREC_FP64) {
       bc_fill_kernel<double><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                       (const double*)h->metric[0], (const double*)h->metric[1],
-                                                      (const double*)h->metric[2], ms[0], ms[1], ms[2], G, q);
+                                                      (const double*)h->metric[2], G, q);
     } else if (h->cfg.precision == FV_PREC_DF64) {
       bc_fill_kernel<float2><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                       (const float2*)h->metric[0], (const float2*)h->metric[1],
-                                                      (const float2*)h->metric[2], ms[0], ms[1], ms[2], G, q);
+                                                      (const float2*)h->metric[2], G, q);
     } else {
       bc_fill_kernel<float><<<grid, threads, 0, s>>>(h->d_blocks, h->d_bcs, h->nbc, h->bc_items,
                                                      (const float*)h->metric[0], (const float*)h->metric[1],
-                                                     (const float*)h->metric[2], ms[0], ms[1], ms[2], G, q);
+                                                     (const float*)h->metric[2], G, q);
     }
     CK(h, cudaGetLastError());
   }
@@ -687,6 +721,19 @@ int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
 // copy between the packed ghosted layout and the internal layout (identical
 // when pitch == ni+4)
 int copy_state(fv_ctx* h, const double* src, double* dst, bool to_internal, cudaStream_t s) {
+  // rows of the internal layout are unpadded, so the packed and internal
+  // layouts coincide: one flat copy (a pitched copy of ~1 KB rows runs far
+  // below the host link's bandwidth when one side is host memory)
+  bool flat = h->state_elems == h->ext_state_elems;
+  long long off = 0;
+  for (const FvBlockDev& b : h->hb) {
+    flat = flat && b.pitch == b.ni + 2 * FV_GHOST && b.qoff == off;
+    off += 5 * ghosted_cells(b.ni, b.nj, b.nk);
+  }
+  if (flat) {
+    CK(h, cudaMemcpyAsync(dst, src, sizeof(double) * h->ext_state_elems, cudaMemcpyDefault, s));
+    return FV_OK;
+  }
   long long ext = 0;
   for (const FvBlockDev& b : h->hb) {
     const long long cells = ghosted_cells(b.ni, b.nj, b.nk);
@@ -1121,8 +1168,10 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     CK(hp, cudaMalloc(&h->geo, sizeof(double) * 10 * h->pad_total));
     CK(hp, cudaMemset(h->geo, 0, sizeof(double) * 10 * h->pad_total));
     if (cfg->precision != FV_PREC_FP32FLUX) {
-      CK(hp, cudaMalloc(&h->wvar, (size_t)mb * 4 * h->pad_total));
-      for (int d = 0; d < cfg->dim; ++d) CK(hp, cudaMalloc(&h->fvis[d], (size_t)mb * 4 * h->nvfaces[d]));
+      for (int d = 0; d < cfg->dim; ++d) {
+        CK(hp, cudaMalloc(&h->fvis[d], (size_t)mb * 4 * h->nvfaces[d]));
+        CK(hp, cudaMalloc(&h->fgeo[d], (size_t)mb * 12 * h->nvfaces[d]));
+      }
     }
   }
   // ---- metrics ----
@@ -1187,13 +1236,34 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     if (rc) { g_create_error = h->err; fv_destroy(reinterpret_cast<fv_handle>(h.release())); return rc; }
     {
       const long long P = h->pad_total;
-      CK(hp, cudaMalloc(&h->geo_t, (size_t)mb * 12 * P));
-      if (cfg->precision == FV_PREC_FP64)
-        geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (double*)h->geo_t, P);
-      else if (cfg->precision == FV_PREC_DF64)
-        geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (float2*)h->geo_t, P);
-      else
+      if (cfg->precision == FV_PREC_FP32FLUX) {
+        CK(hp, cudaMalloc(&h->geo_t, (size_t)mb * 12 * P));
         geo_records_kernel<<<grid_for(P, 256, h->nsm), 256>>>(h->geo, (float*)h->geo_t, P);
+      } else {
+        for (int d = 0; d < cfg->dim; ++d)
+          for (const FvBlockDev& B : h->hb) {
+            const long long nf = (long long)(B.ni + (d == 0)) * (B.nj + (d == 1)) * (B.nk + (d == 2));
+            const int g = grid_for(nf, 256, h->nsm);
+            if (cfg->precision == FV_PREC_FP64)
+              face_geometry_kernel<<<g, 256>>>(B, d, h->geo, P, (const double*)h->metric[d], (double*)h->fgeo[d]);
+            else
+              face_geometry_kernel<<<g, 256>>>(B, d, h->geo, P, (const float2*)h->metric[d], (float2*)h->fgeo[d]);
+          }
+        // the viscous face kernel's work units: 32 x 8 face positions
+        // (i = 0..ni, j = 0..nj) of a block, FV_VISC_KC positions along k
+        // (k = 0..nk; one plane in 2D)
+        std::vector<FvViscTile> vt;
+        for (int b = 0; b < nblocks; ++b) {
+          const FvBlockDev& B = h->hb[b];
+          const int kpos = cfg->dim == 3 ? B.nk + 1 : 1;
+          for (int k0 = 0; k0 < kpos; k0 += FV_VISC_KC)
+            for (int j0 = 0; j0 <= B.nj; j0 += FV_VISC_TY)
+              for (int i0 = 0; i0 <= B.ni; i0 += FV_VISC_TX) vt.push_back(FvViscTile{b, i0, j0, k0});
+        }
+        h->nvtiles = (int)vt.size();
+        CK(hp, cudaMalloc(&h->d_vtiles, sizeof(FvViscTile) * vt.size()));
+        CK(hp, cudaMemcpy(h->d_vtiles, vt.data(), sizeof(FvViscTile) * vt.size(), cudaMemcpyHostToDevice));
+      }
       CK(hp, cudaDeviceSynchronize());
       cudaFree(h->geo);
       h->geo = nullptr;
@@ -1221,8 +1291,8 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
   cudaFree(h->geo_t);
-  cudaFree(h->geo); cudaFree(h->wvar); cudaFree(h->d_edges);
-  for (int d = 0; d < 3; ++d) cudaFree(h->fvis[d]);
+  cudaFree(h->geo); cudaFree(h->d_vtiles); cudaFree(h->d_edges);
+  for (int d = 0; d < 3; ++d) { cudaFree(h->fvis[d]); cudaFree(h->fgeo[d]); }
   delete h;
   return FV_OK;
 }

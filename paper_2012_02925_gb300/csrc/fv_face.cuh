@@ -92,7 +92,7 @@ __device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]
   V[1] = u;
   V[2] = v;
   V[3] = w;
-  V[4] = C.gm1 * (q[4] - Sc<T>::halve(q[0]) * (u * u + v * v + w * w));
+  V[4] = C.gm1 * (q[4] - Sc<T>::halve(q[0]) * Sc<T>::dot3(u, u, v, v, w, w));
 }
 
 // Half the van Leer limited slope, Psi(a/b) b / 2 with Psi(r) = (r + |r|)/(1 + |r|).
@@ -157,11 +157,11 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   using S = Sc<T>;
   const T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
   const T rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
-  const T VnL = nx * uL + ny * vL + nz * wL;
-  const T VnR = nx * uR + ny * vR + nz * wR;
+  const T VnL = S::dot3(nx, uL, ny, vL, nz, wL);
+  const T VnR = S::dot3(nx, uR, ny, vR, nz, wR);
   const T riL = S::rcp(rL), riR = S::rcp(rR);
-  const T hL = C.g_gm1 * pL * riL + S::halve(uL * uL + vL * vL + wL * wL);
-  const T hR = C.g_gm1 * pR * riR + S::halve(uR * uR + vR * vR + wR * wR);
+  const T hL = C.g_gm1 * pL * riL + S::halve(S::dot3(uL, uL, vL, vL, wL, wL));
+  const T hR = C.g_gm1 * pR * riR + S::halve(S::dot3(uR, uR, vR, vR, wR, wR));
   const T mL = rL * VnL, mR = rR * VnR;
 
   // Roe averages: R = sqrt(rho_R/rho_L), rho~ = rho_L R
@@ -172,11 +172,11 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   const T vt = (vL + Rt * vR) * w1;
   const T wt = (wL + Rt * wR) * w1;
   const T ht = (hL + Rt * hR) * w1;
-  const T q2h = S::halve(ut * ut + vt * vt + wt * wt);
+  const T q2h = S::halve(S::dot3(ut, ut, vt, vt, wt, wt));
   const T c2 = C.gm1 * (ht - q2h);
   const T ct = S::sqrt(c2);
   const T ic2 = S::rcp(c2);
-  const T Vnt = nx * ut + ny * vt + nz * wt;
+  const T Vnt = S::dot3(nx, ut, ny, vt, nz, wt);
 
   const T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
   const T dVn = VnR - VnL;
@@ -198,17 +198,18 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
 
   // dissipation |dF1| + |dF234| + |dF5|
   T D0 = a15 + a2;
-  T D1 = a15 * ut + d51 * nx + a2 * ut + a3 * (du - nx * dVn);
-  T D2 = a15 * vt + d51 * ny + a2 * vt + a3 * (dv - ny * dVn);
-  T D3 = a15 * wt + d51 * nz + a2 * wt + a3 * (dw - nz * dVn);
-  T D4 = a15 * ht + d51 * Vnt + a2 * q2h + a3 * (ut * du + vt * dv + wt * dw - Vnt * dVn);
+  T D1 = S::dot4(a15, ut, d51, nx, a2, ut, a3, du - nx * dVn);
+  T D2 = S::dot4(a15, vt, d51, ny, a2, vt, a3, dv - ny * dVn);
+  T D3 = S::dot4(a15, wt, d51, nz, a2, wt, a3, dw - nz * dVn);
+  T D4 = S::dot4(a15, ht, d51, Vnt, a2, q2h, a3, S::dot4(ut, du, vt, dv, wt, dw, -Vnt, dVn));
 
   const T hA = S::halve(A);
+  const T pLR = pL + pR;
   out[0] = ((mL + mR) - D0) * hA;
-  out[1] = ((mL * uL + mR * uR + nx * (pL + pR)) - D1) * hA;
-  out[2] = ((mL * vL + mR * vR + ny * (pL + pR)) - D2) * hA;
-  out[3] = ((mL * wL + mR * wR + nz * (pL + pR)) - D3) * hA;
-  out[4] = ((mL * hL + mR * hR) - D4) * hA;
+  out[1] = (S::dot3(mL, uL, mR, uR, nx, pLR) - D1) * hA;
+  out[2] = (S::dot3(mL, vL, mR, vR, ny, pLR) - D2) * hA;
+  out[3] = (S::dot3(mL, wL, mR, wR, nz, pLR) - D3) * hA;
+  out[4] = (S::dot2(mL, hL, mR, hR) - D4) * hA;
 }
 
 // ---------------------------------------------------------------------------

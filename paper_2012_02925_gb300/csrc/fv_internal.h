@@ -154,25 +154,35 @@ int fv_adjoint_finish(const FvBlockDev& B, const double* lamg, const double* lam
 // ---------------------------------------------------------------------------
 
 
-// Padded-cell geometry of the auxiliary volumes: a 12-entry record per cell
-// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, 2 pads); face variables: a 4-entry
-// record per cell (u, v, w, T); both, and the fluxes, in the storage type of
-// the form (binary64 for the binary64 form, (hi, lo) binary32 pairs for
-// double-float, binary32 for the binary32-flux form), so that the kernels
-// convert nothing and read a cell with 16-byte loads.
+// Padded-cell geometry of the auxiliary volumes for the binary32 form's
+// fused path: a 12-entry record per cell (Omega, Sbar_xi, Sbar_eta,
+// Sbar_zeta, 2 pads) in binary32, read with 16-byte loads.
+//
+// The binary64 and double-float forms use the separate kernel below.  Its
+// static geometry is one 12-entry record per face of each direction:
+// G_a, G_b, G_c (the auxiliary volume's face vectors of the face's own
+// family a and of the two tangential families, each divided by the
+// auxiliary volume) and the face's area vector S, in the form's storage type
+// (binary64, or (hi, lo) binary32 pairs for double-float).
+
+// One unit of work of the viscous face kernel: face positions
+// i0..i0+31 x j0..j0+7 of a block, marched over k0..k0+7 (one plane in 2D).
+struct FvViscTile {
+  int block, i0, j0, k0;
+};
+constexpr int FV_VISC_TX = 32, FV_VISC_TY = 8, FV_VISC_KC = 8;
+
 struct FvViscArgs {
   const FvBlockDev* blocks;
-  int nblocks;
-  long long pad_total;
-  const void* geo;
-  void* wvar;
-  const double* q;                 // state buffer (ghosts filled)
-  const void* metric;              // this direction's face metrics
-  long long mstride;
-  void* fv;                        // this direction's viscous fluxes [4][vstride]
-  long long vstride;
+  const FvViscTile* tiles;
+  int ntiles;
+  const double* q;                 // state buffer (ghosts, edge ghosts filled)
+  const void* fgeo[3];             // per direction: the face geometry records
+  void* fv[3];                     // per direction: viscous fluxes [4][vstride]
+  long long vstride[3];
   FvViscParams vp;
 };
 
-int fv_visc_vars(const FvViscArgs& a, int precision, cudaStream_t s);          // face variables
-int fv_visc_faces(const FvViscArgs& a, int dir, int precision, cudaStream_t s); // fluxes of one direction
+// F_v.S of every face of every direction (binary64: precision 0,
+// double-float: 1)
+int fv_visc_faces(const FvViscArgs& a, int precision, cudaStream_t s);

@@ -1,282 +1,264 @@
-// Laminar viscous terms (Section 2): F_v.S = (0, tau.S, Theta.S) with
-// Stokes's-hypothesis stresses tau = mu (grad u + grad u^T - 2/3 div u I),
-// Theta = tau.u_f + k grad T, k = mu c_p / Pr, T = p / (rho R), and face
-// gradients by Green's theorem over the auxiliary volume between the two
-// cell centres (Section 2: the viscous flux needs a wider stencil than the
-// inviscid one).
+// Laminar viscous terms (Section 2) for the binary64 and double-float forms:
+// F_v.S = (0, tau.S, Theta.S) with Stokes's-hypothesis stresses
+// tau = mu (grad u + grad u^T - 2/3 div u I), Theta = tau.u_f + k grad T,
+// k = mu c_p / Pr, T = p / (rho R), and face gradients by Green's theorem
+// over the auxiliary volume between the two cell centres (Section 2: the
+// viscous flux needs a wider stencil than the inviscid one):
+//   grad phi = (phi_R - phi_L) G_a + D_b G_b + D_c G_c,
+//   D_b = ((phi_L,b+ - phi_L,b-) + (phi_R,b+ - phi_R,b-)) / 4,
+// G_d = the mean of the two cells' averaged face vectors of family d divided
+// by their mean volume (a static per-face record built with the metrics).
 //
-// Two kernels per stage, each in the arithmetic of the form (binary64,
-// double-float, binary32): the face variables (u, v, w, T) of every cell of
-// the blocks padded by one layer (ghosts and edge ghosts included), then one
-// thread per face of one direction gathering the ten cells of its stencil and
-// the auxiliary-volume geometry of its two cells.  The fluxes go to a
-// per-face array that the fused stage kernel differences per cell.
+// One kernel per stage computes every face of every direction.  A CTA owns
+// 32 x 8 face positions of a block and marches them along k through a ring
+// of three padded-cell planes in shared memory holding (u, v, w, T) of each
+// cell, computed once per plane from the conserved state; each thread then
+// evaluates the xi, eta and zeta faces at its position (the faces on the
+// low sides of its cell, plus the high-side faces of the block's last cells)
+// from the ring.  The conserved state of the next plane is copied
+// asynchronously into a staging plane while the faces are computed.  The fluxes go to per-face arrays that the fused stage
+// kernel differences per cell.
+#include <cuda_pipeline.h>
+
 #include "fv_arith.cuh"
 #include "fv_internal.h"
 
 namespace {
 
-// storage type of each arithmetic form (metrics, geometry, face variables,
-// fluxes) with its load and store
-template <class T> struct VMetric;
-template <> struct VMetric<double> {
+// storage type of each arithmetic form with its loads and stores
+template <class T> struct VT;
+template <> struct VT<double> {
   using type = double;
-  static __device__ __forceinline__ double ld(const double* m, long long i) { return __ldg(m + i); }
-  static __device__ __forceinline__ void st(double* m, long long i, double v) { m[i] = v; }
-};
-template <> struct VMetric<df64> {
-  using type = float2;
-  static __device__ __forceinline__ df64 ld(const float2* m, long long i) {
-    const float2 v = __ldg(m + i);
-    return mk(v.x, v.y);
-  }
-  static __device__ __forceinline__ void st(float2* m, long long i, df64 v) { m[i] = make_float2(v.hi, v.lo); }
-};
-template <> struct VMetric<float> {
-  using type = float;
-  static __device__ __forceinline__ float ld(const float* m, long long i) { return __ldg(m + i); }
-  static __device__ __forceinline__ void st(float* m, long long i, float v) { m[i] = v; }
-};
-
-// Per-cell records: the face variables (u, v, w, T) and the geometry
-// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, 2 pads) of a padded cell lie
-// together, 4 and 12 values of the storage type, read with 16-byte loads.
-template <class T> struct VRec;
-template <> struct VRec<double> {
-  static __device__ __forceinline__ void ld4(const double* p, long long c, double o[4]) {
-    const double2* q = reinterpret_cast<const double2*>(p + 4 * c);
-    const double2 a = __ldg(q), b = __ldg(q + 1);
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-  }
-  static __device__ __forceinline__ void st4(double* p, long long c, const double v[4]) {
-    double2* q = reinterpret_cast<double2*>(p + 4 * c);
-    q[0] = make_double2(v[0], v[1]);
-    q[1] = make_double2(v[2], v[3]);
-  }
-  static __device__ __forceinline__ void ld10(const double* p, long long c, double o[10]) {
-    const double2* q = reinterpret_cast<const double2*>(p + 12 * c);
+  static __device__ __forceinline__ double get(double v) { return v; }
+  static __device__ __forceinline__ double put(double v) { return v; }
+  static __device__ __forceinline__ void ld12(const double* p, long long f, double o[12]) {
+    const double2* q = reinterpret_cast<const double2*>(p + 12 * f);
 #pragma unroll
-    for (int x = 0; x < 5; ++x) {
+    for (int x = 0; x < 6; ++x) {
       const double2 a = __ldg(q + x);
-      o[2 * x] = a.x; o[2 * x + 1] = a.y;
+      o[2 * x] = a.x;
+      o[2 * x + 1] = a.y;
     }
   }
 };
-template <> struct VRec<df64> {
-  static __device__ __forceinline__ void ld4(const float2* p, long long c, df64 o[4]) {
-    const float4* q = reinterpret_cast<const float4*>(p + 4 * c);
-    const float4 a = __ldg(q), b = __ldg(q + 1);
-    o[0] = mk(a.x, a.y); o[1] = mk(a.z, a.w); o[2] = mk(b.x, b.y); o[3] = mk(b.z, b.w);
-  }
-  static __device__ __forceinline__ void st4(float2* p, long long c, const df64 v[4]) {
-    float4* q = reinterpret_cast<float4*>(p + 4 * c);
-    q[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
-    q[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
-  }
-  static __device__ __forceinline__ void ld10(const float2* p, long long c, df64 o[10]) {
-    const float4* q = reinterpret_cast<const float4*>(p + 12 * c);
+template <> struct VT<df64> {
+  using type = float2;
+  static __device__ __forceinline__ df64 get(float2 v) { return mk(v.x, v.y); }
+  static __device__ __forceinline__ float2 put(df64 v) { return make_float2(v.hi, v.lo); }
+  static __device__ __forceinline__ void ld12(const float2* p, long long f, df64 o[12]) {
+    const float4* q = reinterpret_cast<const float4*>(p + 12 * f);
 #pragma unroll
-    for (int x = 0; x < 5; ++x) {
+    for (int x = 0; x < 6; ++x) {
       const float4 a = __ldg(q + x);
-      o[2 * x] = mk(a.x, a.y); o[2 * x + 1] = mk(a.z, a.w);
+      o[2 * x] = mk(a.x, a.y);
+      o[2 * x + 1] = mk(a.z, a.w);
     }
   }
 };
-template <> struct VRec<float> {
-  static __device__ __forceinline__ void ld4(const float* p, long long c, float o[4]) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(p + 4 * c));
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-  }
-  static __device__ __forceinline__ void st4(float* p, long long c, const float v[4]) {
-    *reinterpret_cast<float4*>(p + 4 * c) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-  static __device__ __forceinline__ void ld10(const float* p, long long c, float o[10]) {
-    const float4* q = reinterpret_cast<const float4*>(p + 12 * c);
-    const float4 a = __ldg(q), b = __ldg(q + 1), d = __ldg(q + 2);
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-    o[8] = d.x; o[9] = d.y;
-  }
+
+constexpr int TX = FV_VISC_TX, TY = FV_VISC_TY, KC = FV_VISC_KC;
+constexpr int W = TX + 2, H = TY + 2;
+
+// the viscous constants in the arithmetic of the form
+template <class T>
+struct ViscK {
+  T mu, kfac, itref, tref_s, s_suth;
 };
 
-// last block whose offset (pad_off, or vface_off[dir] when dir >= 0) is <= x
-__device__ __forceinline__ int find_block(const FvBlockDev* __restrict__ B, int n, long long x, int dir) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    const long long o = dir < 0 ? B[mid].pad_off : B[mid].vface_off[dir];
-    if (o <= x) lo = mid; else hi = mid - 1;
+// F_v.S of one face from the differences of (u, v, w, T) along the face's
+// own axis (da) and the tangential axes (db, dc), the face values of the
+// velocity (uf) and of T (Tf), and the face's geometry record g
+// (G_a, G_b, G_c, S).  tau is symmetric: its six distinct entries are formed
+// once and mu multiplies tau.S, not each entry; the sums of products are
+// compensated dot products in double-float.
+template <class T, bool THREE>
+__device__ __forceinline__ void face_flux(const ViscK<T>& K, int suth, const T da[4], const T db[4], const T dc[4],
+                                          const T uf[3], T Tf, const T g[12], T fv[4]) {
+  using S = Sc<T>;
+  T grad[4][3];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+      grad[m][x] = THREE ? S::dot3(da[m], g[x], db[m], g[3 + x], dc[m], g[6 + x]) : S::dot2(da[m], g[x], db[m], g[3 + x]);
+  T mu = K.mu;
+  if (suth) {
+    const T tr = Tf * K.itref;
+    mu = mu * tr * S::sqrt(tr) * K.tref_s * S::rcp(Tf + K.s_suth);
   }
-  return lo;
+  const T d23 = S::c(2.0 / 3.0) * (grad[0][0] + grad[1][1] + grad[2][2]);
+  const T t00 = S::twice(grad[0][0]) - d23, t11 = S::twice(grad[1][1]) - d23, t22 = S::twice(grad[2][2]) - d23;
+  const T t01 = grad[0][1] + grad[1][0], t02 = grad[0][2] + grad[2][0], t12 = grad[1][2] + grad[2][1];
+  fv[0] = mu * S::dot3(t00, g[9], t01, g[10], t02, g[11]);
+  fv[1] = mu * S::dot3(t01, g[9], t11, g[10], t12, g[11]);
+  fv[2] = mu * S::dot3(t02, g[9], t12, g[10], t22, g[11]);
+  fv[3] = S::dot4(fv[0], uf[0], fv[1], uf[1], fv[2], uf[2], mu * K.kfac,
+                  S::dot3(grad[3][0], g[9], grad[3][1], g[10], grad[3][2], g[11]));
 }
 
-// (u, v, w, T) of every padded cell; cells that were never filled (the
-// corners of the ghost frame, density 0) get zeros - no stencil reads them
-template <class T>
-__global__ void visc_vars_kernel(const FvViscArgs a) {
+template <class T, bool THREE>
+__global__ void __launch_bounds__(TX * TY, 2) visc_faces_kernel(const FvViscArgs a) {
   using S = Sc<T>;
-  using V = VMetric<T>;
-  typename V::type* wv = reinterpret_cast<typename V::type*>(a.wvar);
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < a.pad_total;
-       x += (long long)gridDim.x * blockDim.x) {
-    const FvBlockDev& B = a.blocks[find_block(a.blocks, a.nblocks, x, -1)];
-    const long long loc = x - B.pad_off;
-    const int pi = B.ni + 2, pj = B.nj + 2;
-    const int i = (int)(loc % pi) - 1, j = (int)((loc / pi) % pj) - 1, k = (int)(loc / ((long long)pi * pj)) - 1;
-    const long long qi = B.qoff + (long long)(k + 2) * B.kstride + (long long)(j + 2) * B.jstride + (i + 2);
-    const double r = a.q[qi];
-    if (!(r > 0.0)) {
-      const T z[4] = {S::c(0.0), S::c(0.0), S::c(0.0), S::c(0.0)};
-      VRec<T>::st4(wv, x, z);
-      continue;
-    }
-    const T rho = S::from_d(r);
-    const T ri = S::rcp(rho);
-    const T u = S::from_d(a.q[qi + B.plane]) * ri;
-    const T v = S::from_d(a.q[qi + 2 * B.plane]) * ri;
-    const T w = S::from_d(a.q[qi + 3 * B.plane]) * ri;
-    const T p = S::c(a.vp.gamma - 1.0) * (S::from_d(a.q[qi + 4 * B.plane]) - S::c(0.5) * rho * (u * u + v * v + w * w));
-    const T temp = p * ri * S::c(1.0 / a.vp.r_gas);
-    const T rec[4] = {u, v, w, temp};
-    VRec<T>::st4(wv, x, rec);
-  }
-}
-
-template <class T>
-__global__ void visc_faces_kernel(const FvViscArgs a, const int dir) {
-  using S = Sc<T>;
-  using V = VMetric<T>;
+  using V = VT<T>;
   using MT = typename V::type;
-  const MT* metric = reinterpret_cast<const MT*>(a.metric);
-  const MT* geo = reinterpret_cast<const MT*>(a.geo);    // [pad cells][12]
-  const MT* wv = reinterpret_cast<const MT*>(a.wvar);    // [pad cells][4]
-  MT* fv = reinterpret_cast<MT*>(a.fv);
-  const long long P = a.pad_total;
-  const int b_ax = dir == 0 ? 1 : 0, c_ax = dir == 2 ? 1 : 2;
-  const bool three = a.vp.dim == 3;
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < a.vstride;
-       f += (long long)gridDim.x * blockDim.x) {
-    const FvBlockDev& B = a.blocks[find_block(a.blocks, a.nblocks, f, dir)];
-    const long long loc = f - B.vface_off[dir];
-    const int ei = B.ni + (dir == 0), ej = B.nj + (dir == 1);
-    const int i = (int)(loc % ei), j = (int)((loc / ei) % ej), k = (int)(loc / ((long long)ei * ej));
-    const long long pi = B.ni + 2, pij = pi * (B.nj + 2);
-    const long long pR = B.pad_off + (k + 1) * pij + (long long)(j + 1) * pi + (i + 1);
-    const long long sa = dir == 0 ? 1 : (dir == 1 ? pi : pij);
-    const long long sb = b_ax == 0 ? 1 : pi, sc = c_ax == 1 ? pi : pij;
-    const long long pL = pR - sa;
-    // the face's area vector
-    T Sx, Sy, Sz;
-    if (B.cartesian) {
-      const T A = S::from_d(B.cart_area[dir]);
-      Sx = S::from_d(B.cart_n[dir][0]) * A;
-      Sy = S::from_d(B.cart_n[dir][1]) * A;
-      Sz = S::from_d(B.cart_n[dir][2]) * A;
-    } else {
-      const long long fi = 4 * (B.face_off[dir] + loc);     // (n_x, n_y, n_z, |S|) record
-      const T A = VMetric<T>::ld(metric, fi + 3);
-      Sx = VMetric<T>::ld(metric, fi) * A;
-      Sy = VMetric<T>::ld(metric, fi + 1) * A;
-      Sz = VMetric<T>::ld(metric, fi + 2) * A;
-    }
-    // auxiliary volume: mean volume and mean averaged face vectors of L and R
-    const T half = S::c(0.5), quarter = S::c(0.25);
-    T gl[10], gr[10];
-    VRec<T>::ld10(geo, pL, gl);
-    VRec<T>::ld10(geo, pR, gr);
-    const T iOm = S::rcp(half * (gl[0] + gr[0]));
-    // families of the face's own axis (a) and of the tangential axes b, c
-    T Aa[3], Ab[3], Ac[3];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      Aa[x] = half * (dir == 0 ? gl[1 + x] + gr[1 + x] : (dir == 1 ? gl[4 + x] + gr[4 + x] : gl[7 + x] + gr[7 + x]));
-      Ab[x] = half * (b_ax == 0 ? gl[1 + x] + gr[1 + x] : gl[4 + x] + gr[4 + x]);
-      Ac[x] = half * (c_ax == 1 ? gl[4 + x] + gr[4 + x] : gl[7 + x] + gr[7 + x]);
-    }
-    // the stencil: L, R and their neighbours along b (and c)
-    T wL[4], wR[4], wLbm[4], wLbp[4], wRbm[4], wRbp[4];
-    VRec<T>::ld4(wv, pL, wL);
-    VRec<T>::ld4(wv, pR, wR);
-    VRec<T>::ld4(wv, pL - sb, wLbm);
-    VRec<T>::ld4(wv, pL + sb, wLbp);
-    VRec<T>::ld4(wv, pR - sb, wRbm);
-    VRec<T>::ld4(wv, pR + sb, wRbp);
-    T wLcm[4], wLcp[4], wRcm[4], wRcp[4];
-    if (three) {
-      VRec<T>::ld4(wv, pL - sc, wLcm);
-      VRec<T>::ld4(wv, pL + sc, wLcp);
-      VRec<T>::ld4(wv, pR - sc, wRcm);
-      VRec<T>::ld4(wv, pR + sc, wRcp);
-    }
-    // gradients of u, v, w, T
-    T grad[4][3];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const T da = wR[m] - wL[m];
-      const T db = quarter * ((wLbp[m] - wLbm[m]) + (wRbp[m] - wRbm[m]));
-      T dc = S::c(0.0);
-      if (three) dc = quarter * ((wLcp[m] - wLcm[m]) + (wRcp[m] - wRcm[m]));
-#pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        T g = da * Aa[x] + db * Ab[x];
-        if (three) g = g + dc * Ac[x];
-        grad[m][x] = g * iOm;
-      }
-    }
-    // face values, viscosity, conductivity
-    T uf[3];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) uf[x] = half * (wL[x] + wR[x]);
-    const T Tf = half * (wL[3] + wR[3]);
-    T mu = S::c(a.vp.mu);
-    if (a.vp.sutherland) {
-      const T tr = Tf * S::c(1.0 / a.vp.t_ref);
-      mu = mu * tr * S::sqrt(tr) * S::c(a.vp.t_ref + a.vp.s_suth) * S::rcp(Tf + S::c(a.vp.s_suth));
-    }
-    const T kc = mu * S::c(a.vp.kfac);
-    const T div = grad[0][0] + grad[1][1] + grad[2][2];
-    const T Sv[3] = {Sx, Sy, Sz};
-    T energy = S::c(0.0);
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      T fx = S::c(0.0);
-#pragma unroll
-      for (int y = 0; y < 3; ++y) {
-        T t = grad[x][y] + grad[y][x];
-        if (x == y) t = t - S::c(2.0 / 3.0) * div;
-        fx = fx + mu * t * Sv[y];
-      }
-      V::st(fv, x * a.vstride + f, fx);
-      energy = energy + fx * uf[x];
-    }
-    energy = energy + kc * (grad[3][0] * Sx + grad[3][1] * Sy + grad[3][2] * Sz);
-    V::st(fv, 3 * a.vstride + f, energy);
-  }
-}
+  constexpr int NP = THREE ? 3 : 1;
+  __shared__ MT ring[NP][4][H][W];
+  __shared__ double stg[THREE ? 5 : 1][THREE ? H * W : 1];   // staged state of the next plane
 
-int grid_of(long long n, int threads) {
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long g = (n + threads - 1) / threads;
-  return (int)(g < 1 ? 1 : (g > (long long)nsm * 16 ? (long long)nsm * 16 : g));
+  const FvViscTile tile = a.tiles[blockIdx.x];
+  const FvBlockDev& B = a.blocks[tile.block];
+  const int ni = B.ni, nj = B.nj, nk = B.nk;
+  const long long qoff = B.qoff, jst = B.jstride, kst = B.kstride, pl = B.plane;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int i = tile.i0 + tx, j = tile.j0 + ty;
+  const int k0 = tile.k0, k1 = THREE ? min(tile.k0 + KC, nk + 1) : 1;
+  const double* __restrict__ q = a.q;
+  const T gm1 = S::c(a.vp.gamma - 1.0), iR = S::c(1.0 / a.vp.r_gas), zero = S::c(0.0);
+  ViscK<T> K;
+  K.mu = S::c(a.vp.mu);
+  K.kfac = S::c(a.vp.kfac);
+  K.itref = S::c(1.0 / a.vp.t_ref);
+  K.tref_s = S::c(a.vp.t_ref + a.vp.s_suth);
+  K.s_suth = S::c(a.vp.s_suth);
+  const int suth = a.vp.sutherland;
+
+  // plane kk's cells handled by this thread: e = tid + r * TX * TY; the
+  // cell's state index, or -1 outside the padded block
+  constexpr int NE = (W * H + TX * TY - 1) / (TX * TY);
+  auto cell_of = [&](int e, int kk) -> long long {
+    const int x = e % W, y = e / W;
+    const int ci = tile.i0 - 1 + x, cj = tile.j0 - 1 + y;
+    if (e >= W * H || kk < -1 || kk > nk || ci > ni || cj > nj) return -1;
+    return qoff + (long long)(kk + 2) * kst + (long long)(cj + 2) * jst + (ci + 2);
+  };
+  // (u, v, w, T) of one cell from its conserved state into ring slot sl;
+  // the never-filled corners of the ghost frame (density 0) and cells
+  // outside the padded block get zeros: no face reads them
+  auto put_vars = [&](int sl, int e, bool in, double r, double m1, double m2, double m3, double en) {
+    T u = zero, v = zero, w = zero, t = zero;
+    if (in && r > 0.0) {
+      const T rho = S::from_d(r);
+      const T ri = S::rcp(rho);
+      u = S::from_d(m1) * ri;
+      v = S::from_d(m2) * ri;
+      w = S::from_d(m3) * ri;
+      const T p = gm1 * (S::from_d(en) - S::c(0.5) * rho * (u * u + v * v + w * w));
+      t = p * ri * iR;
+    }
+    MT* d = &ring[sl][0][0][0] + e;
+    d[0] = V::put(u);
+    d[H * W] = V::put(v);
+    d[2 * H * W] = V::put(w);
+    d[3 * H * W] = V::put(t);
+  };
+  auto load_plane = [&](int sl, int kk) {
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      const int e = tid + r * TX * TY;
+      if (e >= W * H) break;
+      const long long c = cell_of(e, kk);
+      if (c >= 0) put_vars(sl, e, true, q[c], q[c + pl], q[c + 2 * pl], q[c + 3 * pl], q[c + 4 * pl]);
+      else put_vars(sl, e, false, 0.0, 0.0, 0.0, 0.0, 0.0);
+    }
+  };
+  // the same in two halves: the asynchronous copy of the state into the
+  // staging plane, then (after the faces) the conversion of the cells this
+  // thread copied
+  auto prefetch_plane = [&](int kk) {
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      const int e = tid + r * TX * TY;
+      const long long c = cell_of(e, kk);
+      if (c < 0) continue;
+#pragma unroll
+      for (int n = 0; n < 5; ++n) __pipeline_memcpy_async(&stg[n][e], q + c + n * pl, sizeof(double));
+    }
+    __pipeline_commit();
+  };
+  auto convert_plane = [&](int sl, int kk) {
+    __pipeline_wait_prior(0);
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      const int e = tid + r * TX * TY;
+      if (e >= W * H) break;
+      const bool in = cell_of(e, kk) >= 0;
+      put_vars(sl, e, in, in ? stg[0][e] : 0.0, in ? stg[1][e] : 0.0, in ? stg[2][e] : 0.0, in ? stg[3][e] : 0.0,
+               in ? stg[4][e] : 0.0);
+    }
+  };
+
+  if (THREE) {
+    for (int kk = k0 - 1; kk <= k0 + 1; ++kk) load_plane((kk + 1) % 3, kk);
+  } else {
+    load_plane(0, 0);
+  }
+  __syncthreads();
+
+  constexpr int VS = H * W, SL = 4 * VS;     // variable and ring-slot strides
+  for (int k = k0; k < k1; ++k) {
+    const int sm = THREE ? k % 3 : 0, s0 = THREE ? (k + 1) % 3 : 0, sp = THREE ? (k + 2) % 3 : 0;
+    const bool more = THREE && k + 1 < k1;
+    if (more) prefetch_plane(k + 2);      // overlaps the faces below
+    // this position's cell (variable 0) and the offsets of the planes k-1
+    // and k+1 from it
+    const MT* C = &ring[s0][0][ty + 1][tx + 1];
+    const int dkm = (sm - s0) * SL, dkp = (sp - s0) * SL;
+    // the xi, eta and zeta faces at this position through one copy of the
+    // face code (three inlined copies overflow the instruction cache)
+#pragma unroll 1
+    for (int dir = 0; dir < (THREE ? 3 : 2); ++dir) {
+      const bool valid = dir == 0 ? (i <= ni && j < nj && k < nk)
+                                  : (dir == 1 ? (i < ni && j <= nj && k < nk) : (i < ni && j < nj && k <= nk));
+      if (!valid) continue;
+      // L (offset oL) and the tangential neighbours: xi face b = eta,
+      // c = zeta; eta face b = xi, c = zeta; zeta face b = xi, c = eta
+      const int oL = dir == 0 ? -1 : (dir == 1 ? -W : dkm);
+      const int obp = dir == 0 ? W : 1, obm = -obp;
+      const int ocp = dir == 2 ? W : dkp, ocm = dir == 2 ? -W : dkm;
+      const int ei = ni + (dir == 0), ej = nj + (dir == 1);
+      const long long f = B.vface_off[dir] + (long long)i + (long long)ei * (j + (long long)ej * k);
+      T g[12];
+      V::ld12(reinterpret_cast<const MT*>(a.fgeo[dir]), f, g);
+      T da[4], db[4], dc[4], uf[3], Tf;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const MT* c = C + m * VS;
+        const T pL = V::get(c[oL]), pR = V::get(c[0]);
+        da[m] = pR - pL;
+        db[m] = S::quarter((V::get(c[oL + obp]) - V::get(c[oL + obm])) + (V::get(c[obp]) - V::get(c[obm])));
+        dc[m] = zero;
+        if (THREE)
+          dc[m] = S::quarter((V::get(c[oL + ocp]) - V::get(c[oL + ocm])) + (V::get(c[ocp]) - V::get(c[ocm])));
+        if (m < 3) uf[m] = S::halve(pL + pR);
+        else Tf = S::halve(pL + pR);
+      }
+      T fv[4];
+      face_flux<T, THREE>(K, suth, da, db, dc, uf, Tf, g, fv);
+      MT* out = reinterpret_cast<MT*>(a.fv[dir]);
+      const long long vs = a.vstride[dir];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) out[x * vs + f] = V::put(fv[x]);
+    }
+    if (more) {
+      __syncthreads();
+      convert_plane(sm, k + 2);   // plane k-1's slot takes plane k+2
+      __syncthreads();
+    }
+  }
 }
 
 }  // namespace
 
-int fv_visc_vars(const FvViscArgs& a, int precision, cudaStream_t s) {
-  const int t = 256, g = grid_of(a.pad_total, t);
-  if (precision == 0) visc_vars_kernel<double><<<g, t, 0, s>>>(a);
-  else if (precision == 1) visc_vars_kernel<df64><<<g, t, 0, s>>>(a);
-  else visc_vars_kernel<float><<<g, t, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-int fv_visc_faces(const FvViscArgs& a, int dir, int precision, cudaStream_t s) {
-  if (a.vstride == 0) return 0;
-  const int t = 128, g = grid_of(a.vstride, t);
-  if (precision == 0) visc_faces_kernel<double><<<g, t, 0, s>>>(a, dir);
-  else if (precision == 1) visc_faces_kernel<df64><<<g, t, 0, s>>>(a, dir);
-  else visc_faces_kernel<float><<<g, t, 0, s>>>(a, dir);
+int fv_visc_faces(const FvViscArgs& a, int precision, cudaStream_t s) {
+  if (a.ntiles == 0) return 0;
+  const dim3 block(TX, TY);
+  const bool three = a.vp.dim == 3;
+  if (precision == 0) {
+    if (three) visc_faces_kernel<double, true><<<a.ntiles, block, 0, s>>>(a);
+    else visc_faces_kernel<double, false><<<a.ntiles, block, 0, s>>>(a);
+  } else {
+    if (three) visc_faces_kernel<df64, true><<<a.ntiles, block, 0, s>>>(a);
+    else visc_faces_kernel<df64, false><<<a.ntiles, block, 0, s>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
