@@ -284,8 +284,9 @@ int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
  * writes buffer 1 when m is odd and buffer 2 when m is even; the last stage
  * writes buffer 0 in place; stage m > 1 reads what stage m-1 wrote.  Kernel
  * launches: connections, physical boundaries, fused residual + update; with
- * visc also the edge ghosts, the face variables (u, v, w, T) and one viscous
- * face-flux launch per direction before the fused kernel. */
+ * visc also the edge ghosts and (binary64, double-float) the viscous face
+ * kernel before the fused kernel; stage 1 with the residual monitor on (see
+ * fv_set_monitor) also its two reduction kernels. */
 int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
 
 /* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage
@@ -297,6 +298,25 @@ int fv_rk_step(fv_handle h, double dt, int use_graph, void* stream);
  * and Linf = max |R| in out_host[5..9] (host pointer, 10 doubles).
  * Synchronises `stream`.  Returns FV_ERR_NONFINITE when any R is NaN/Inf. */
 int fv_residual_norms(fv_handle h, int buffer, double* out_host, void* stream);
+
+/* Residual monitor (the residual histories of Sections 8.1-8.3, recorded
+ * without a separate residual evaluation).  on != 0: from now on every RK
+ * stage 1 (fv_rk_stage(h, 1, ...), the first stage of fv_rk_step) also
+ * stores the residual it computes, R(Q^(0)) - the residual of the state the
+ * step starts from, the one fv_residual_norms(h, 0, ...) would give before
+ * the step - and reduces it to the norms fv_monitor_norms returns.  The
+ * first call with on != 0 allocates the monitor's device memory (5 cells x
+ * 8 bytes per cell and a few KB; blocking); any call discards cached step
+ * graphs.  on = 0 stops the recording (the memory stays until fv_destroy). */
+int fv_set_monitor(fv_handle h, int on);
+
+/* Norms recorded by the latest monitored stage 1, as fv_residual_norms
+ * defines them (out_host[0..4] L2, [5..9] Linf; host pointer, 10 doubles).
+ * Synchronises `stream` (the stream the step ran on).  FV_ERR_INVALID_ARG if
+ * the monitor is off or no monitored stage has been launched since it was
+ * turned on; FV_ERR_NONFINITE (out_host still written) when that residual
+ * had NaN/Inf entries. */
+int fv_monitor_norms(fv_handle h, double* out_host, void* stream);
 
 /* Autotuner of the batched launch (not in the paper): times `reps` launches
  * of RK stage 1 with step dt for every compiled tile shape and a set of

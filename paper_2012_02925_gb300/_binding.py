@@ -22,7 +22,8 @@ PRECISIONS = {"fp64": PREC_FP64, "df64": PREC_DF64, "fp32flux": PREC_FP32FLUX}
 EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error", "fv_state_size",
            "fv_field_size", "fv_cell_count", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-           "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries")
+           "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
+           "fv_monitor_norms")
 
 
 class FvError(RuntimeError):
@@ -98,9 +99,12 @@ def load_library(path: Optional[str] = None):
     L.fv_autotune.argtypes = [vp, dbl, i32, vp]
     L.fv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.fv_set_boundaries.argtypes = [vp, ctypes.POINTER(fv_bc_patch), i32]
+    L.fv_set_monitor.argtypes = [vp, i32]
+    L.fv_monitor_norms.argtypes = [vp, vp, vp]
     for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
-              "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries"):
+              "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
+              "fv_monitor_norms"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -284,6 +288,20 @@ class Solver:
     def residual_norms(self, buffer: int = 0, stream=None):
         out = np.zeros(10)
         rc = self._L.fv_residual_norms(self._h, int(buffer), out.ctypes.data, _stream(stream))
+        if rc == FV_ERR_NONFINITE:
+            raise FvError(rc, self._L.fv_last_error(self._h).decode())
+        self._check(rc)
+        return out[:5].copy(), out[5:].copy()
+
+    def set_monitor(self, on: bool = True):
+        """Record the residual norms of every RK stage 1 from now on (the
+        residual of the state each step starts from; see fv_set_monitor)."""
+        self._check(self._L.fv_set_monitor(self._h, 1 if on else 0))
+
+    def monitor_norms(self, stream=None):
+        """(L2, Linf) per variable recorded by the latest monitored stage 1."""
+        out = np.zeros(10)
+        rc = self._L.fv_monitor_norms(self._h, out.ctypes.data, _stream(stream))
         if rc == FV_ERR_NONFINITE:
             raise FvError(rc, self._L.fv_last_error(self._h).decode())
         self._check(rc)

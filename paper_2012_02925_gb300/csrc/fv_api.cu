@@ -65,6 +65,13 @@ struct fv_ctx {
   struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
   EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
   long long nedges = 0;
+  // residual monitor: RK stage 1 stores its residual (rmon) and reduces it
+  // into mon_norm (see fv_set_monitor)
+  int monitor = 0;
+  bool mon_ran = false;
+  void* rmon = nullptr;
+  double* mon_partials = nullptr;
+  double* mon_norm = nullptr;
   int device = 0, nsm = 0;
   std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
   std::string err;
@@ -511,56 +518,6 @@ __global__ void edge_fill_kernel(const fv_ctx::EdgeItem* __restrict__ items, lon
 // ---------------------------------------------------------------------------
 // residual norms (deterministic two-level reduction)
 // ---------------------------------------------------------------------------
-constexpr int NORM_THREADS = 256;
-
-__global__ void norm_partial_kernel(const double* __restrict__ r, long long n_per_var, double* partials) {
-  __shared__ double ssum[NORM_THREADS / 32], smax[NORM_THREADS / 32];
-  __shared__ int sbad[NORM_THREADS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = 0; v < 5; ++v) {
-    double s = 0.0, m = 0.0;
-    int bad = 0;
-    const double* rv = r + v * n_per_var;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n_per_var; x += (long long)gridDim.x * blockDim.x) {
-      const double y = rv[x];
-      if (!isfinite(y)) bad = 1;
-      s += y * y;
-      m = fmax(m, fabs(y));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_down_sync(0xffffffffu, s, o);
-      m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-      bad |= __shfl_down_sync(0xffffffffu, bad, o);
-    }
-    if (lane == 0) { ssum[warp] = s; smax[warp] = m; sbad[warp] = bad; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double ts = 0.0, tm = 0.0;
-      int tb = 0;
-      for (int w = 0; w < NORM_THREADS / 32; ++w) { ts += ssum[w]; tm = fmax(tm, smax[w]); tb |= sbad[w]; }
-      partials[(v * 3 + 0) * gridDim.x + blockIdx.x] = ts;
-      partials[(v * 3 + 1) * gridDim.x + blockIdx.x] = tm;
-      partials[(v * 3 + 2) * gridDim.x + blockIdx.x] = tb;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void norm_final_kernel(const double* partials, int nparts, long long n_per_var, double* out) {
-  const int v = threadIdx.x;
-  if (v < 5) {
-    double s = 0.0, m = 0.0, b = 0.0;
-    for (int p = 0; p < nparts; ++p) {
-      s += partials[(v * 3 + 0) * nparts + p];
-      m = fmax(m, partials[(v * 3 + 1) * nparts + p]);
-      b += partials[(v * 3 + 2) * nparts + p];
-    }
-    out[v] = sqrt(s / (double)n_per_var);
-    out[5 + v] = m;
-    out[10 + v] = b;
-  }
-}
-
 int grid_for(long long n, int threads, int nsm) {
   long long g = (n + threads - 1) / threads;
   return (int)std::max<long long>(1, std::min<long long>(g, (long long)nsm * 16));
@@ -715,7 +672,15 @@ int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
   a.q0 = h->buf[0];
   a.qout = h->buf[bo];
   a.alpha_dt = h->cfg.alpha[m - 1] * dt;
-  return launch_stage(h, a, s);
+  const bool mon = m == 1 && h->monitor;
+  if (mon) a.rmon = h->rmon;
+  rc = launch_stage(h, a, s);
+  if (rc || !mon) return rc;
+  if (fv_monitor_reduce(h->rmon, h->cfg.precision == FV_PREC_FP64, h->ncell, h->mon_partials, 2 * h->nsm,
+                        h->mon_norm, s))
+    return cuda_fail(h, cudaGetLastError(), "residual monitor reduction");
+  h->mon_ran = true;
+  return FV_OK;
 }
 
 // copy between the packed ghosted layout and the internal layout (identical
@@ -1292,6 +1257,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
   cudaFree(h->geo_t);
   cudaFree(h->geo); cudaFree(h->d_vtiles); cudaFree(h->d_edges);
+  cudaFree(h->rmon); cudaFree(h->mon_partials); cudaFree(h->mon_norm);
   for (int d = 0; d < 3; ++d) { cudaFree(h->fvis[d]); cudaFree(h->fgeo[d]); }
   delete h;
   return FV_OK;
@@ -1552,11 +1518,42 @@ int fv_residual_norms(fv_handle hh, int buffer, double* out_host, void* stream) 
   a.rout_varmajor = 1;
   rc = launch_stage(h, a, s);
   if (rc) return rc;
-  norm_partial_kernel<<<nparts, NORM_THREADS, 0, s>>>(h->scratch_r, h->ncell, h->partials);
-  norm_final_kernel<<<1, 32, 0, s>>>(h->partials, nparts, h->ncell, h->d_norm);
-  CK(h, cudaGetLastError());
+  if (fv_monitor_reduce(h->scratch_r, 1, h->ncell, h->partials, nparts, h->d_norm, s))
+    return cuda_fail(h, cudaGetLastError(), "residual norm reduction");
   double tmp[15];
   CK(h, cudaMemcpyAsync(tmp, h->d_norm, sizeof(double) * 15, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  std::memcpy(out_host, tmp, sizeof(double) * 10);
+  for (int v = 0; v < 5; ++v)
+    if (tmp[10 + v] != 0.0) return fail(h, FV_ERR_NONFINITE, "residual has non-finite entries");
+  return FV_OK;
+}
+
+int fv_set_monitor(fv_handle hh, int on) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  CK(h, cudaDeviceSynchronize());
+  if (on && !h->rmon) {
+    const size_t eb = h->cfg.precision == FV_PREC_FP64 ? sizeof(double) : sizeof(float2);
+    CK(h, cudaMalloc(&h->rmon, eb * 5 * h->ncell));
+    CK(h, cudaMalloc(&h->mon_partials, sizeof(double) * 15 * 2 * h->nsm));
+    CK(h, cudaMalloc(&h->mon_norm, sizeof(double) * 16));
+  }
+  h->monitor = on ? 1 : 0;
+  h->mon_ran = false;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  h->graphs.clear();
+  return FV_OK;
+}
+
+int fv_monitor_norms(fv_handle hh, double* out_host, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!out_host) return fail(h, FV_ERR_INVALID_ARG, "out_host is NULL");
+  if (!h->monitor || !h->mon_ran) return fail(h, FV_ERR_INVALID_ARG, "no monitored RK stage 1 has run");
+  cudaStream_t s = (cudaStream_t)stream;
+  double tmp[15];
+  CK(h, cudaMemcpyAsync(tmp, h->mon_norm, sizeof(double) * 15, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   std::memcpy(out_host, tmp, sizeof(double) * 10);
   for (int v = 0; v < 5; ++v)

@@ -90,6 +90,8 @@ struct FvStageArgs {
                                 // per cell of every block padded by one layer, binary32
   double* rout;                 // residual output or null
   int rout_varmajor;            // 0: [block][5][cells]; 1: [5][all cells]
+  void* rmon;                   // RK mode: the residual also stored here, [5][all cells], as binary64
+                                // (binary64 form) or (hi, lo) binary32 pairs (other forms); or null
   long long ncell_total;
   double alpha_dt;              // alpha_m * dt
   FvFaceParams fp;
@@ -186,3 +188,13 @@ struct FvViscArgs {
 // F_v.S of every face of every direction (binary64: precision 0,
 // double-float: 1)
 int fv_visc_faces(const FvViscArgs& a, int precision, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Residual norms (fv_monitor.cu)
+// ---------------------------------------------------------------------------
+
+// r: [5][ncell] residual as binary64 (binary64 != 0) or (hi, lo) binary32
+// pairs; partials: 15 * nparts doubles of scratch; out: 15 doubles on the
+// device = per variable sqrt(mean R^2), max |R|, non-finite flag count.
+int fv_monitor_reduce(const void* r, int binary64, long long ncell, double* partials, int nparts, double* out,
+                      cudaStream_t s);

@@ -475,6 +475,19 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
 #pragma unroll
               for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], fac, R[n]);
             }
+            if (args.rmon) {
+              // the residual monitor's copy of R, in the accumulator's own
+              // storage (no binary64 conversion on the FP64 unit)
+              const long long mi = B.cell_off + cell;
+              if constexpr (std::is_same<AT, double>::value) {
+#pragma unroll
+                for (int n = 0; n < 5; ++n) static_cast<double*>(args.rmon)[n * args.ncell_total + mi] = R[n];
+              } else {
+#pragma unroll
+                for (int n = 0; n < 5; ++n)
+                  static_cast<float2*>(args.rmon)[n * args.ncell_total + mi] = make_float2(R[n].hi, R[n].lo);
+              }
+            }
           } else {
             double* ro = args.rout;
             if (args.rout_varmajor) {
