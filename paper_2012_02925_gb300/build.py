@@ -12,7 +12,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfvgb.so")
 SOURCES = ["fv_api.cu", "fv_stage_fp64.cu", "fv_stage_df64.cu", "fv_stage_df64_fast.cu", "fv_stage_fp32.cu",
            "fv_stage_fp32_fast.cu", "fv_stage_fp32_visc.cu", "fv_stage_fp32_fast_visc.cu", "fv_noalloc.cu",
-           "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu"]
+           "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu", "fv_stage_fp64_visc.cu", "fv_stage_df64_visc.cu",
+           "fv_stage_df64_fast_visc.cu"]
 HEADERS = ["fv_arith.cuh", "fv_face.cuh", "fv_stage.cuh", "fv_viscface.cuh", "fv_internal.h", "fv_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

@@ -61,7 +61,7 @@ struct fv_ctx {
   void* fgeo[3] = {nullptr, nullptr, nullptr};    // other forms: face records (G_a, G_b, G_c, S) [nvfaces[d]][12]
   FvViscTile* d_vtiles = nullptr;   // work units of the viscous face kernel
   int nvtiles = 0;
-  void* fvis[3] = {nullptr, nullptr, nullptr};    // viscous face fluxes [4][nvfaces[d]], storage type
+  void* fvis[3] = {nullptr, nullptr, nullptr};    // viscous face fluxes [nvfaces[d]][4], storage type
   struct EdgeItem { long long dst, dplane, s1, s1plane, s2, s2plane; };
   EdgeItem* d_edges = nullptr;      // depth-1 edge ghost fills
   long long nedges = 0;
@@ -537,7 +537,6 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
   for (int d = 0; d < h->cfg.dim; ++d) {
     v.fgeo[d] = h->fgeo[d];
     v.fv[d] = h->fvis[d];
-    v.vstride[d] = h->nvfaces[d];
   }
   v.vp.gamma = h->cfg.gamma;
   v.vp.mu = h->cfg.mu;
@@ -555,15 +554,16 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
 int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
   int rc;
   const FvLaunch& l = h->launch;
-  if (h->cfg.visc && !l.visc) {
-    // binary64 and double-float: the viscous fluxes by the separate kernels
+  if (l.visc && h->cfg.precision != FV_PREC_FP32FLUX) {
+    // binary64 and double-float: the viscous fluxes by the separate kernel
     rc = do_visc(h, a.qin, s);
     if (rc) return rc;
   }
   switch (h->cfg.precision) {
-    case FV_PREC_FP64: rc = fv_launch_stage_fp64(a, l, s); break;
+    case FV_PREC_FP64: rc = l.visc ? fv_launch_stage_fp64_visc(a, l, s) : fv_launch_stage_fp64(a, l, s); break;
     case FV_PREC_DF64:
-      rc = l.fast ? fv_launch_stage_df64_fast(a, l, s) : fv_launch_stage_df64(a, l, s);
+      if (l.visc) rc = l.fast ? fv_launch_stage_df64_fast_visc(a, l, s) : fv_launch_stage_df64_visc(a, l, s);
+      else rc = l.fast ? fv_launch_stage_df64_fast(a, l, s) : fv_launch_stage_df64(a, l, s);
       break;
     default:
       if (l.visc) rc = l.fast ? fv_launch_stage_fp32_fast_visc(a, l, s) : fv_launch_stage_fp32_visc(a, l, s);
@@ -595,7 +595,7 @@ FvStageArgs base_args(fv_ctx* h) {
   a.fp.limiter = h->cfg.limiter;
   a.fp.fix_all = h->cfg.fix_all;
   a.fp.flux = h->cfg.flux;
-  if (h->cfg.visc && h->launch.visc) {
+  if (h->launch.visc && h->cfg.precision == FV_PREC_FP32FLUX) {
     // binary32: viscous terms fused into the stage kernel
     a.geo = h->geo_t;
     a.vp.gamma = h->cfg.gamma;
@@ -607,7 +607,7 @@ FvStageArgs base_args(fv_ctx* h) {
     a.vp.sutherland = h->cfg.sutherland;
     a.vp.dim = h->cfg.dim;
   } else if (h->cfg.visc) {
-    for (int d = 0; d < h->cfg.dim; ++d) { a.fv[d] = h->fvis[d]; a.vstride[d] = h->nvfaces[d]; }
+    for (int d = 0; d < h->cfg.dim; ++d) a.fv[d] = h->fvis[d];
   }
   return a;
 }
@@ -676,7 +676,7 @@ int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
   if (mon) a.rmon = h->rmon;
   rc = launch_stage(h, a, s);
   if (rc || !mon) return rc;
-  if (fv_monitor_reduce(h->rmon, h->cfg.precision == FV_PREC_FP64, h->ncell, h->mon_partials, 2 * h->nsm,
+  if (fv_monitor_reduce(h->rmon, h->cfg.precision == FV_PREC_FP64, h->ncell, h->mon_partials, FV_NORM_PARTS * h->nsm,
                         h->mon_norm, s))
     return cuda_fail(h, cudaGetLastError(), "residual monitor reduction");
   h->mon_ran = true;
@@ -735,17 +735,22 @@ void choose_launch(fv_ctx* h) {
   l.ty = FV_SHAPE_TABLE[shape - 1][1];
   l.threads = FV_SHAPE_TABLE[shape - 1][2];
   l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.eps, c.kappa, c.harten, c.fix_all);
-  // the binary32 form fuses the viscous faces into the stage kernel (its T on
-  // the fly costs a MUFU reciprocal); for binary64 and double-float the
-  // separate kernels measured faster
-  l.visc = c.visc && c.precision == FV_PREC_FP32FLUX;
+  // viscous kernels: the binary32 form fuses the viscous faces into the
+  // stage kernel (its T on the fly costs a MUFU reciprocal); for binary64
+  // and double-float a separate kernel measured faster, and their _visc
+  // stage kernels subtract its per-face fluxes
+  l.visc = c.visc != 0;
   h->launch = l;
 }
 
 int query_occupancy(fv_ctx* h, size_t* smem) {
   switch (h->cfg.precision) {
-    case FV_PREC_FP64: return fv_stage_occupancy_fp64(h->launch, smem);
+    case FV_PREC_FP64:
+      return h->launch.visc ? fv_stage_occupancy_fp64_visc(h->launch, smem) : fv_stage_occupancy_fp64(h->launch, smem);
     case FV_PREC_DF64:
+      if (h->launch.visc)
+        return h->launch.fast ? fv_stage_occupancy_df64_fast_visc(h->launch, smem)
+                              : fv_stage_occupancy_df64_visc(h->launch, smem);
       return h->launch.fast ? fv_stage_occupancy_df64_fast(h->launch, smem) : fv_stage_occupancy_df64(h->launch, smem);
     default:
       if (h->launch.visc)
@@ -1505,7 +1510,7 @@ int fv_residual_norms(fv_handle hh, int buffer, double* out_host, void* stream) 
   if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
   if (!out_host) return fail(h, FV_ERR_INVALID_ARG, "out_host is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int nparts = h->nsm * 2;
+  const int nparts = FV_NORM_PARTS * h->nsm;
   if (!h->scratch_r) CK(h, cudaMalloc(&h->scratch_r, sizeof(double) * 5 * h->ncell));
   if (!h->partials) CK(h, cudaMalloc(&h->partials, sizeof(double) * 15 * nparts));
   if (!h->d_norm) CK(h, cudaMalloc(&h->d_norm, sizeof(double) * 16));
@@ -1536,7 +1541,7 @@ int fv_set_monitor(fv_handle hh, int on) {
   if (on && !h->rmon) {
     const size_t eb = h->cfg.precision == FV_PREC_FP64 ? sizeof(double) : sizeof(float2);
     CK(h, cudaMalloc(&h->rmon, eb * 5 * h->ncell));
-    CK(h, cudaMalloc(&h->mon_partials, sizeof(double) * 15 * 2 * h->nsm));
+    CK(h, cudaMalloc(&h->mon_partials, sizeof(double) * 15 * FV_NORM_PARTS * h->nsm));
     CK(h, cudaMalloc(&h->mon_norm, sizeof(double) * 16));
   }
   h->monitor = on ? 1 : 0;

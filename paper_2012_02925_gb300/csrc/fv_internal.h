@@ -82,9 +82,8 @@ struct FvStageArgs {
   const double* invvol;         // 1/Omega per interior cell
   const double* srcvol;         // S*Omega, [block][5][cells], or null
   const float2* srcvol2;        // the same as double-float (hi, lo) pairs, or null
-  const void* fv[3];            // viscous face fluxes per direction, [4][faces] (momentum, energy), in the
-                                // form's storage type (binary64, binary32 pairs, binary32), or null
-  long long vstride[3];         // faces per direction of fv
+  const void* fv[3];            // viscous face fluxes per direction, one (momentum x, y, z, energy) record
+                                // per face in the form's storage type (binary64, binary32 pairs), or null
   FvViscParams vp;              // the binary32 form's fused viscous terms (VISC kernels)
   const void* geo;              // and their 12-entry (Omega, Sbar_xi, Sbar_eta, Sbar_zeta, pads) geometry record
                                 // per cell of every block padded by one layer, binary32
@@ -128,12 +127,19 @@ int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem_bytes);
 // the binary32 form with the laminar viscous terms fused into the face loop
-// (fv_stage_fp32[_fast]_visc.cu); the other forms evaluate them in separate
-// kernels (fv_visc.cu) and read the per-face fluxes in the cell sums
+// (fv_stage_fp32[_fast]_visc.cu); the other forms evaluate them in a
+// separate kernel (fv_visc.cu) and their _visc kernels read the per-face
+// fluxes in the cell sums
 int fv_launch_stage_fp32_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
 int fv_launch_stage_fp32_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
 int fv_stage_occupancy_fp32_visc(const FvLaunch& l, size_t* smem_bytes);
 int fv_stage_occupancy_fp32_fast_visc(const FvLaunch& l, size_t* smem_bytes);
+int fv_launch_stage_fp64_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_df64_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_launch_stage_df64_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
+int fv_stage_occupancy_fp64_visc(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_df64_visc(const FvLaunch& l, size_t* smem_bytes);
+int fv_stage_occupancy_df64_fast_visc(const FvLaunch& l, size_t* smem_bytes);
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
 constexpr int FV_NUM_SHAPES = 8;
@@ -180,8 +186,7 @@ struct FvViscArgs {
   int ntiles;
   const double* q;                 // state buffer (ghosts, edge ghosts filled)
   const void* fgeo[3];             // per direction: the face geometry records
-  void* fv[3];                     // per direction: viscous fluxes [4][vstride]
-  long long vstride[3];
+  void* fv[3];                     // per direction: viscous fluxes, one 4-value record per face
   FvViscParams vp;
 };
 
@@ -194,7 +199,9 @@ int fv_visc_faces(const FvViscArgs& a, int precision, cudaStream_t s);
 // ---------------------------------------------------------------------------
 
 // r: [5][ncell] residual as binary64 (binary64 != 0) or (hi, lo) binary32
-// pairs; partials: 15 * nparts doubles of scratch; out: 15 doubles on the
-// device = per variable sqrt(mean R^2), max |R|, non-finite flag count.
+// pairs; partials: 15 * nparts doubles of scratch (nparts = FV_NORM_PARTS
+// CTAs per SM); out: 15 doubles on the device = per variable
+// sqrt(mean R^2), max |R|, non-finite flag count.
+constexpr int FV_NORM_PARTS = 8;
 int fv_monitor_reduce(const void* r, int binary64, long long ncell, double* partials, int nparts, double* out,
                       cudaStream_t s);

@@ -26,47 +26,57 @@ __device__ __forceinline__ df64 mon_shfl(df64 y, int o) {
 }
 
 // per-CTA partial sums of R^2, maxima of |R| and non-finite flags of each
-// variable: partials[(v * 3 + {0, 1, 2}) * gridDim.x + CTA]
+// variable: partials[(v * 3 + {0, 1, 2}) * gridDim.x + CTA].  One pass over
+// the cells with the five variables' loads independent of each other (a
+// pass per variable kept one dependent load chain per thread in flight)
 template <class ST, class A>
 __global__ void __launch_bounds__(MON_THREADS) monitor_partial_kernel(const ST* __restrict__ r, long long n,
                                                                       double* __restrict__ partials) {
   using S = Sc<A>;
-  __shared__ A ssum[MON_THREADS / 32], smax[MON_THREADS / 32];
+  __shared__ A ssum[5][MON_THREADS / 32], smax[5][MON_THREADS / 32];
   __shared__ int sbad[MON_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  A s[5], m[5];
+  int bad = 0;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { s[v] = S::c(0.0); m[v] = S::c(0.0); }
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+       x += (long long)gridDim.x * blockDim.x) {
+    A y[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) y[v] = mon_ld(r + v * n, x);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      if (!mon_finite(y[v])) bad = 1;
+      s[v] = s[v] + y[v] * y[v];
+      const A ay = S::abs(y[v]);
+      if (S::lt(m[v], ay)) m[v] = ay;
+    }
+  }
+#pragma unroll
   for (int v = 0; v < 5; ++v) {
-    A s = S::c(0.0), m = S::c(0.0);
-    int bad = 0;
-    const ST* rv = r + v * n;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
-         x += (long long)gridDim.x * blockDim.x) {
-      const A y = mon_ld(rv, x);
-      if (!mon_finite(y)) bad = 1;
-      s = s + y * y;
-      const A ay = S::abs(y);
-      if (S::lt(m, ay)) m = ay;
-    }
     for (int o = 16; o > 0; o >>= 1) {
-      s = s + mon_shfl(s, o);
-      const A mo = mon_shfl(m, o);
-      if (S::lt(m, mo)) m = mo;
-      bad |= __shfl_down_sync(0xffffffffu, bad, o);
+      s[v] = s[v] + mon_shfl(s[v], o);
+      const A mo = mon_shfl(m[v], o);
+      if (S::lt(m[v], mo)) m[v] = mo;
     }
-    if (lane == 0) { ssum[warp] = s; smax[warp] = m; sbad[warp] = bad; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      A ts = S::c(0.0), tm = S::c(0.0);
-      int tb = 0;
-      for (int w = 0; w < MON_THREADS / 32; ++w) {
-        ts = ts + ssum[w];
-        if (S::lt(tm, smax[w])) tm = smax[w];
-        tb |= sbad[w];
-      }
-      partials[(v * 3 + 0) * gridDim.x + blockIdx.x] = S::to_d(ts);
-      partials[(v * 3 + 1) * gridDim.x + blockIdx.x] = S::to_d(tm);
-      partials[(v * 3 + 2) * gridDim.x + blockIdx.x] = tb;
+    if (lane == 0) { ssum[v][warp] = s[v]; smax[v][warp] = m[v]; }
+  }
+  for (int o = 16; o > 0; o >>= 1) bad |= __shfl_down_sync(0xffffffffu, bad, o);
+  if (lane == 0) sbad[warp] = bad;
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    const int v = threadIdx.x;
+    A ts = S::c(0.0), tm = S::c(0.0);
+    int tb = 0;
+    for (int w = 0; w < MON_THREADS / 32; ++w) {
+      ts = ts + ssum[v][w];
+      if (S::lt(tm, smax[v][w])) tm = smax[v][w];
+      tb |= sbad[w];
     }
-    __syncthreads();
+    partials[(v * 3 + 0) * gridDim.x + blockIdx.x] = S::to_d(ts);
+    partials[(v * 3 + 1) * gridDim.x + blockIdx.x] = S::to_d(tm);
+    partials[(v * 3 + 2) * gridDim.x + blockIdx.x] = tb;
   }
 }
 

@@ -97,8 +97,14 @@ constexpr int stage_min_ctas() {
   return sizeof(T) == 4 ? (NT <= 128 ? 8 : 4) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
 }
 
+// VISC: the laminar viscous terms.  The binary32 form evaluates them in the
+// face loop (FUSED_VISC); the wider forms subtract the per-face fluxes of the
+// separate viscous kernel in the cell sums (VISC_PAIRS).  Without VISC
+// neither code path exists in the kernel.
 template <class T, int TX, int TY, int NT, bool DIM3, bool PF, bool FAST, bool VISC>
 __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel(const FvStageArgs args) {
+  constexpr bool FUSED_VISC = VISC && std::is_same<T, float>::value;
+  constexpr bool VISC_PAIRS = VISC && !std::is_same<T, float>::value;
   using S = Sc<T>;
   using CC = typename std::conditional<FAST, FaceCFast<T>, FaceC<T>>::type;
   using AT = typename Acc<T>::type;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
       } else {
         face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
       }
-      if constexpr (VISC) {
+      if constexpr (FUSED_VISC) {
         // F_i - F_v: the cell sums below then carry the viscous pairs too
         T gl[10], gr[10], fvv[4];
         VGeo<T>::ld10(geo, vis.gR - vis.gstep, gl);
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
           }
         }
         VisArgs vis;
-        if constexpr (VISC) {
+        if constexpr (FUSED_VISC) {
           // cell R of the face in block coordinates, and its tangential
           // neighbours (and L's) in the plane ring
           int ri, rj, rk;
@@ -405,6 +411,31 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
           const long long vy = B.vface_off[1] + ((long long)k * (nj + 1) + j) * ni + i;
           const long long vz = B.vface_off[2] + ((long long)k * nj + j) * ni + i;
           const long long vzs = (long long)ni * nj;
+          // the viscous pairs (x, y, z in order), from the per-face records
+          // (momentum, energy) the separate kernel stores like the metrics
+          AT rvis[4];
+          if constexpr (VISC_PAIRS) {
+            {
+              const MT* f0 = reinterpret_cast<const MT*>(args.fv[0]);
+              const MT* f1 = reinterpret_cast<const MT*>(args.fv[1]);
+              T a[4], b[4];
+              MetricStore<T>::ld4(f0, vx + 1, a[0], a[1], a[2], a[3]);
+              MetricStore<T>::ld4(f0, vx, b[0], b[1], b[2], b[3]);
+#pragma unroll
+              for (int n = 0; n < 4; ++n) rvis[n] = a[n] - b[n];
+              MetricStore<T>::ld4(f1, vy + ni, a[0], a[1], a[2], a[3]);
+              MetricStore<T>::ld4(f1, vy, b[0], b[1], b[2], b[3]);
+#pragma unroll
+              for (int n = 0; n < 4; ++n) rvis[n] = rvis[n] + (a[n] - b[n]);
+              if (DIM3) {
+                const MT* f2 = reinterpret_cast<const MT*>(args.fv[2]);
+                MetricStore<T>::ld4(f2, vz + vzs, a[0], a[1], a[2], a[3]);
+                MetricStore<T>::ld4(f2, vz, b[0], b[1], b[2], b[3]);
+#pragma unroll
+                for (int n = 0; n < 4; ++n) rvis[n] = rvis[n] + (a[n] - b[n]);
+              }
+            }
+          }
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
             const T x1 = Fx[n * NXI + y * (TX + 1) + x + 1], x0 = Fx[n * NXI + y * (TX + 1) + x];
@@ -434,17 +465,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel
               if (DIM3)
                 r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
                                      Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
-              if (args.fv[0] && n > 0) {
-                // the viscous pairs, stored like the metrics of this form
-                const MT* f0 = reinterpret_cast<const MT*>(args.fv[0]) + (n - 1) * args.vstride[0];
-                const MT* f1 = reinterpret_cast<const MT*>(args.fv[1]) + (n - 1) * args.vstride[1];
-                AT rv = (MetricStore<T>::ld(f0, vx + 1) - MetricStore<T>::ld(f0, vx)) +
-                        (MetricStore<T>::ld(f1, vy + ni) - MetricStore<T>::ld(f1, vy));
-                if (DIM3) {
-                  const MT* f2 = reinterpret_cast<const MT*>(args.fv[2]) + (n - 1) * args.vstride[2];
-                  rv = rv + (MetricStore<T>::ld(f2, vz + vzs) - MetricStore<T>::ld(f2, vz));
-                }
-                r = r - rv;
+              if constexpr (VISC_PAIRS) {
+                if (n > 0) r = r - rvis[n - 1];
               }
               if constexpr (std::is_same<AT, df64>::value) {
                 if (args.srcvol2) {

@@ -16,7 +16,8 @@
 // evaluates the xi, eta and zeta faces at its position (the faces on the
 // low sides of its cell, plus the high-side faces of the block's last cells)
 // from the ring.  The conserved state of the next plane is copied
-// asynchronously into a staging plane while the faces are computed.  The fluxes go to per-face arrays that the fused stage
+// asynchronously into a staging plane while the faces are computed.  The
+// fluxes go to per-face records (4 values, 32 bytes) that the fused stage
 // kernel differences per cell.
 #include <cuda_pipeline.h>
 
@@ -31,6 +32,11 @@ template <> struct VT<double> {
   using type = double;
   static __device__ __forceinline__ double get(double v) { return v; }
   static __device__ __forceinline__ double put(double v) { return v; }
+  static __device__ __forceinline__ void st4(double* p, long long f, const double v[4]) {
+    double2* q = reinterpret_cast<double2*>(p + 4 * f);
+    q[0] = make_double2(v[0], v[1]);
+    q[1] = make_double2(v[2], v[3]);
+  }
   static __device__ __forceinline__ void ld12(const double* p, long long f, double o[12]) {
     const double2* q = reinterpret_cast<const double2*>(p + 12 * f);
 #pragma unroll
@@ -45,6 +51,11 @@ template <> struct VT<df64> {
   using type = float2;
   static __device__ __forceinline__ df64 get(float2 v) { return mk(v.x, v.y); }
   static __device__ __forceinline__ float2 put(df64 v) { return make_float2(v.hi, v.lo); }
+  static __device__ __forceinline__ void st4(float2* p, long long f, const df64 v[4]) {
+    float4* q = reinterpret_cast<float4*>(p + 4 * f);
+    q[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    q[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+  }
   static __device__ __forceinline__ void ld12(const float2* p, long long f, df64 o[12]) {
     const float4* q = reinterpret_cast<const float4*>(p + 12 * f);
 #pragma unroll
@@ -234,10 +245,7 @@ __global__ void __launch_bounds__(TX * TY, 2) visc_faces_kernel(const FvViscArgs
       }
       T fv[4];
       face_flux<T, THREE>(K, suth, da, db, dc, uf, Tf, g, fv);
-      MT* out = reinterpret_cast<MT*>(a.fv[dir]);
-      const long long vs = a.vstride[dir];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) out[x * vs + f] = V::put(fv[x]);
+      V::st4(reinterpret_cast<MT*>(a.fv[dir]), f, fv);
     }
     if (more) {
       __syncthreads();
