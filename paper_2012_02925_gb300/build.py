@@ -10,10 +10,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfvgb.so")
-SOURCES = ["fv_api.cu", "fv_stage_fp64.cu", "fv_stage_df64.cu", "fv_stage_df64_fast.cu", "fv_stage_fp32.cu",
-           "fv_stage_fp32_fast.cu", "fv_stage_fp32_visc.cu", "fv_stage_fp32_fast_visc.cu", "fv_noalloc.cu",
-           "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu", "fv_stage_fp64_visc.cu", "fv_stage_df64_visc.cu",
-           "fv_stage_df64_fast_visc.cu"]
+# the stage kernel variants (fv_stage_<form>[_fast][_visc][_bc].cu, one per
+# translation unit so that they compile in parallel), then the rest
+STAGE_VARIANTS = ["fp64", "fp64_bc", "fp64_visc", "fp64_visc_bc"] + [
+    form + fast + visc + bc for form in ("df64", "fp32") for fast in ("", "_fast") for visc in ("", "_visc")
+    for bc in ("", "_bc")]
+SOURCES = ["fv_stage_%s.cu" % v for v in STAGE_VARIANTS] + [
+    "fv_api.cu", "fv_noalloc.cu", "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu"]
 HEADERS = ["fv_arith.cuh", "fv_face.cuh", "fv_stage.cuh", "fv_viscface.cuh", "fv_internal.h", "fv_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
@@ -50,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             os.replace(o + ".tmp", o)
         return o
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(4, os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     if force or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()

@@ -551,6 +551,26 @@ int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
   return FV_OK;
 }
 
+// the compiled stage kernel variant of the handle's form, scheme, viscous
+// terms and boundary overwrites
+struct StageVariant {
+  int (*launch)(const FvStageArgs&, const FvLaunch&, cudaStream_t);
+  int (*occupancy)(const FvLaunch&, size_t*);
+};
+StageVariant stage_variant(const fv_ctx* h) {
+#define FV_VARIANT_ENTRY(NAME) {fv_launch_stage_##NAME, fv_stage_occupancy_##NAME},
+  // in FV_STAGE_VARIANTS order: [form][fast][visc][bc], binary64 without fast
+  static const StageVariant table[] = {FV_STAGE_VARIANTS(FV_VARIANT_ENTRY)};
+#undef FV_VARIANT_ENTRY
+  const FvLaunch& l = h->launch;
+  const int tail = (l.visc ? 2 : 0) + (l.bc ? 1 : 0);
+  switch (h->cfg.precision) {
+    case FV_PREC_FP64: return table[tail];
+    case FV_PREC_DF64: return table[4 + (l.fast ? 4 : 0) + tail];
+    default: return table[12 + (l.fast ? 4 : 0) + tail];
+  }
+}
+
 int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
   int rc;
   const FvLaunch& l = h->launch;
@@ -559,17 +579,7 @@ int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
     rc = do_visc(h, a.qin, s);
     if (rc) return rc;
   }
-  switch (h->cfg.precision) {
-    case FV_PREC_FP64: rc = l.visc ? fv_launch_stage_fp64_visc(a, l, s) : fv_launch_stage_fp64(a, l, s); break;
-    case FV_PREC_DF64:
-      if (l.visc) rc = l.fast ? fv_launch_stage_df64_fast_visc(a, l, s) : fv_launch_stage_df64_visc(a, l, s);
-      else rc = l.fast ? fv_launch_stage_df64_fast(a, l, s) : fv_launch_stage_df64(a, l, s);
-      break;
-    default:
-      if (l.visc) rc = l.fast ? fv_launch_stage_fp32_fast_visc(a, l, s) : fv_launch_stage_fp32_visc(a, l, s);
-      else rc = l.fast ? fv_launch_stage_fp32_fast(a, l, s) : fv_launch_stage_fp32(a, l, s);
-      break;
-  }
+  rc = stage_variant(h).launch(a, l, s);
   if (rc == -2) return fail(h, FV_ERR_UNSUPPORTED, "tile shape not compiled");
   if (rc != 0) return cuda_fail(h, cudaGetLastError(), "stage kernel launch");
   return FV_OK;
@@ -740,25 +750,12 @@ void choose_launch(fv_ctx* h) {
   // and double-float a separate kernel measured faster, and their _visc
   // stage kernels subtract its per-face fluxes
   l.visc = c.visc != 0;
+  l.bc = 0;
+  for (const FvBlockDev& b : h->hb) l.bc |= b.bcmap != nullptr;
   h->launch = l;
 }
 
-int query_occupancy(fv_ctx* h, size_t* smem) {
-  switch (h->cfg.precision) {
-    case FV_PREC_FP64:
-      return h->launch.visc ? fv_stage_occupancy_fp64_visc(h->launch, smem) : fv_stage_occupancy_fp64(h->launch, smem);
-    case FV_PREC_DF64:
-      if (h->launch.visc)
-        return h->launch.fast ? fv_stage_occupancy_df64_fast_visc(h->launch, smem)
-                              : fv_stage_occupancy_df64_visc(h->launch, smem);
-      return h->launch.fast ? fv_stage_occupancy_df64_fast(h->launch, smem) : fv_stage_occupancy_df64(h->launch, smem);
-    default:
-      if (h->launch.visc)
-        return h->launch.fast ? fv_stage_occupancy_fp32_fast_visc(h->launch, smem)
-                              : fv_stage_occupancy_fp32_visc(h->launch, smem);
-      return h->launch.fast ? fv_stage_occupancy_fp32_fast(h->launch, smem) : fv_stage_occupancy_fp32(h->launch, smem);
-  }
-}
+int query_occupancy(fv_ctx* h, size_t* smem) { return stage_variant(h).occupancy(h->launch, smem); }
 
 int build_tiles(fv_ctx* h) {
   const FvLaunch& l = h->launch;
@@ -1439,7 +1436,10 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
   h->bcs.assign(patches, patches + n);
   h->nbc = n;
   h->bc_items = items;
-  return FV_OK;
+  // the stage kernel variant with (or without) the boundary overwrites, and
+  // its occupancy and tile table
+  choose_launch(h);
+  return build_tiles(h);
 }
 
 int fv_exchange_ghosts(fv_handle hh, int buffer, void* stream) {

@@ -96,14 +96,16 @@ struct FvStageArgs {
   FvFaceParams fp;
 };
 
-// Kernel launchers, one translation unit per arithmetic form.
+// Kernel launchers, one translation unit per compiled variant.
 struct FvLaunch {
   int shape;                    // compiled tile shape id (1-based)
   int tx, ty, threads;          // tile shape
   int grid;                     // CTAs (persistent)
   int three_d;
   int fast;                     // the kernel with the default scheme compiled in
-  int visc;                     // the kernel with the laminar viscous terms fused in (binary32 form)
+  int visc;                     // the kernel with the laminar viscous terms (fused for binary32, the
+                                // separate kernel's pairs for the other forms)
+  int bc;                       // the kernel with the boundary-face flux overwrites
 };
 
 // The default scheme (Roe flux, van Leer limiter, eps = 1, kappa = -1,
@@ -113,33 +115,20 @@ inline bool fv_default_scheme(int flux, int limiter, double eps, double kappa, d
   return flux == 0 && limiter == 1 && eps == 1.0 && kappa == -1.0 && harten > 0.0 && fix_all == 0;
 }
 
-// binary64 has the generic kernels only; the other forms have both, in two
-// translation units each (fv_stage_<form>.cu, fv_stage_<form>_fast.cu)
-int fv_launch_stage_fp64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_df64(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_df64_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_fp32(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_fp32_fast(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-// occupancy queries: CTAs per SM for a tile shape (0 = shape not compiled)
-int fv_stage_occupancy_fp64(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_df64(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_df64_fast(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_fp32(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_fp32_fast(const FvLaunch& l, size_t* smem_bytes);
-// the binary32 form with the laminar viscous terms fused into the face loop
-// (fv_stage_fp32[_fast]_visc.cu); the other forms evaluate them in a
-// separate kernel (fv_visc.cu) and their _visc kernels read the per-face
-// fluxes in the cell sums
-int fv_launch_stage_fp32_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_fp32_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_stage_occupancy_fp32_visc(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_fp32_fast_visc(const FvLaunch& l, size_t* smem_bytes);
-int fv_launch_stage_fp64_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_df64_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_launch_stage_df64_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);
-int fv_stage_occupancy_fp64_visc(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_df64_visc(const FvLaunch& l, size_t* smem_bytes);
-int fv_stage_occupancy_df64_fast_visc(const FvLaunch& l, size_t* smem_bytes);
+// Stage kernel variants, fv_stage_<name>.cu each: the form (fp64, df64,
+// fp32 = binary32 flux), _fast = default scheme compiled in (not binary64),
+// _visc = laminar viscous terms, _bc = boundary-face flux overwrites.
+// launch: enqueue on a stream; occupancy: CTAs per SM for the launch's tile
+// shape (0 = shape not compiled) and its dynamic shared memory.
+#define FV_STAGE_VARIANTS(X)                                                                  \
+  X(fp64) X(fp64_bc) X(fp64_visc) X(fp64_visc_bc) X(df64) X(df64_bc) X(df64_visc) X(df64_visc_bc) \
+  X(df64_fast) X(df64_fast_bc) X(df64_fast_visc) X(df64_fast_visc_bc) X(fp32) X(fp32_bc)      \
+  X(fp32_visc) X(fp32_visc_bc) X(fp32_fast) X(fp32_fast_bc) X(fp32_fast_visc) X(fp32_fast_visc_bc)
+#define FV_DECLARE_STAGE_VARIANT(NAME)                                                       \
+  int fv_launch_stage_##NAME(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);     \
+  int fv_stage_occupancy_##NAME(const FvLaunch& l, size_t* smem_bytes);
+FV_STAGE_VARIANTS(FV_DECLARE_STAGE_VARIANT)
+#undef FV_DECLARE_STAGE_VARIANT
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
 constexpr int FV_NUM_SHAPES = 8;

@@ -1,7 +1,10 @@
-// Fused stage kernel instantiated for the double-float form with the laminar viscous pairs of the separate viscous kernel, default scheme compiled in.
+// Fused stage kernel instantiated for the double-float form: default scheme compiled in, laminar
+// viscous pairs of the separate viscous kernel, no boundary-face overwrites.
 #include "fv_stage.cuh"
 
 int fv_launch_stage_df64_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<df64, true, true>(a, l, s);
+  return fv_dispatch_launch<df64, true, true, false>(a, l, s);
 }
-int fv_stage_occupancy_df64_fast_visc(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<df64, true, true>(l, smem); }
+int fv_stage_occupancy_df64_fast_visc(const FvLaunch& l, size_t* smem) {
+  return fv_dispatch_occupancy<df64, true, true, false>(l, smem);
+}

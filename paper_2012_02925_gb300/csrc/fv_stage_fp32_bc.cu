@@ -1,0 +1,10 @@
+// Fused stage kernel instantiated for the binary32-flux form: generic scheme switches,
+// boundary-face flux overwrites.
+#include "fv_stage.cuh"
+
+int fv_launch_stage_fp32_bc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
+  return fv_dispatch_launch<float, false, false, true>(a, l, s);
+}
+int fv_stage_occupancy_fp32_bc(const FvLaunch& l, size_t* smem) {
+  return fv_dispatch_occupancy<float, false, false, true>(l, smem);
+}

@@ -1,7 +1,10 @@
-// Fused stage kernel instantiated for the binary32-flux form with the laminar viscous terms, default scheme compiled in.
+// Fused stage kernel instantiated for the binary32-flux form: default scheme compiled in, laminar
+// viscous terms fused into the face loop, no boundary-face overwrites.
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp32_fast_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<float, true, true>(a, l, s);
+  return fv_dispatch_launch<float, true, true, false>(a, l, s);
 }
-int fv_stage_occupancy_fp32_fast_visc(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<float, true, true>(l, smem); }
+int fv_stage_occupancy_fp32_fast_visc(const FvLaunch& l, size_t* smem) {
+  return fv_dispatch_occupancy<float, true, true, false>(l, smem);
+}

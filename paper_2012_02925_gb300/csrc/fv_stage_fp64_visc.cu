@@ -1,7 +1,10 @@
-// Fused stage kernel instantiated for the binary64 form with the laminar viscous pairs of the separate viscous kernel, generic scheme switches.
+// Fused stage kernel instantiated for the binary64 form: generic scheme switches, laminar viscous
+// pairs of the separate viscous kernel, no boundary-face overwrites.
 #include "fv_stage.cuh"
 
 int fv_launch_stage_fp64_visc(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  return fv_dispatch_launch<double, false, true>(a, l, s);
+  return fv_dispatch_launch<double, false, true, false>(a, l, s);
 }
-int fv_stage_occupancy_fp64_visc(const FvLaunch& l, size_t* smem) { return fv_dispatch_occupancy<double, false, true>(l, smem); }
+int fv_stage_occupancy_fp64_visc(const FvLaunch& l, size_t* smem) {
+  return fv_dispatch_occupancy<double, false, true, false>(l, smem);
+}
