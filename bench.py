@@ -582,7 +582,7 @@ def main():
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
     ap.add_argument("--variant-workloads",
-                    default="mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid,mms128+ns,ogrid+ns")
+                    default="vortex,mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid,mms128+ns,ogrid+ns")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
