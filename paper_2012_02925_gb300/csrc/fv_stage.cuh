@@ -92,9 +92,9 @@ struct StageSmem {
 
 // resident CTAs per SM the register allocation must allow (shared memory
 // permits this many for the compiled shapes)
-template <class T, int NT>
+template <class T, int NT, bool VISC>
 constexpr int stage_min_ctas() {
-  return sizeof(T) == 4 ? (NT <= 128 ? 8 : 4) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
+  return sizeof(T) == 4 ? (VISC ? (NT <= 128 ? 6 : 3) : (NT <= 128 ? 8 : 4)) : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1));
 }
 
 // VISC: the laminar viscous terms.  The binary32 form evaluates them in the
@@ -105,7 +105,7 @@ constexpr int stage_min_ctas() {
 // face) their code is not compiled in, which on the 128^3 block made both
 // the double-float and the binary32 kernels 10 % faster.
 template <class T, int TX, int TY, int NT, bool DIM3, bool PF, bool FAST, bool VISC, bool BC>
-__global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT>())) fv_stage_kernel(const FvStageArgs args) {
+__global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_kernel(const FvStageArgs args) {
   constexpr bool FUSED_VISC = VISC && std::is_same<T, float>::value;
   constexpr bool VISC_PAIRS = VISC && !std::is_same<T, float>::value;
   using S = Sc<T>;
