@@ -99,7 +99,9 @@ constexpr int stage_min_ctas() {
 
 // VISC: the laminar viscous terms.  The binary32 form evaluates them in the
 // face loop (FUSED_VISC); the wider forms subtract the per-face fluxes of the
-// separate viscous kernel in the cell sums (VISC_PAIRS).  Without VISC
+// separate viscous kernel from each face's inviscid flux in the face loop
+// (VISC_PAIRS: one record load per face, issued before the inviscid flux
+// whose arithmetic covers its latency).  Without VISC
 // neither code path exists in the kernel.  BC: the boundary-code lookup and
 // the overwritten wall and farfield fluxes; without it (no block has such a
 // face) their code is not compiled in, which on the 128^3 block made both
@@ -223,6 +225,13 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         const MT* m = dir == 0 ? mxi : (dir == 1 ? meta : mzeta);
         MetricStore<T>::ld4(m, f, nx, ny, nz, A);
       }
+      // the separate viscous kernel's F_v.S of this face (same face order
+      // as the metrics, all blocks); loaded here, used after the flux
+      T fva, fvb, fvc, fvd;
+      if constexpr (VISC_PAIRS) {
+        const MT* vr = reinterpret_cast<const MT*>(args.fv[dir == 0 ? 0 : (dir == 1 ? 1 : 2)]);
+        MetricStore<T>::ld4(vr, B.vface_off[dir] + (f - B.face_off[dir]), fva, fvb, fvc, fvd);
+      }
       T out[5];
       if (code == FV_BCK_SLIP_WALL || code == FV_BCK_NOSLIP_WALL) {
         // nearest interior cells: s2, s3 on a min face, s1, s0 on a max face
@@ -245,6 +254,13 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
                           DIM3, gl, gr, dir, dir == 0 ? 1 : 0, dir == 2 ? 1 : 2, nx * A, ny * A, nz * A, fvv);
 #pragma unroll
         for (int n = 0; n < 4; ++n) out[1 + n] = out[1 + n] - fvv[n];
+      }
+      if constexpr (VISC_PAIRS) {
+        // F_i - F_v, as the fused binary32 path stores it
+        out[1] = out[1] - fva;
+        out[2] = out[2] - fvb;
+        out[3] = out[3] - fvc;
+        out[4] = out[4] - fvd;
       }
 #pragma unroll
       for (int n = 0; n < 5; ++n) dst[n * dstr] = out[n];
@@ -409,36 +425,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
           const long long ncell_b = (long long)ni * nj * nk;
           AT R[5];
           const long long src_off = 5 * B.cell_off + cell;
-          // viscous face fluxes of this cell's six faces (laminar terms on)
-          const long long vx = B.vface_off[0] + ((long long)k * nj + j) * (ni + 1) + i;
-          const long long vy = B.vface_off[1] + ((long long)k * (nj + 1) + j) * ni + i;
-          const long long vz = B.vface_off[2] + ((long long)k * nj + j) * ni + i;
-          const long long vzs = (long long)ni * nj;
-          // the viscous pairs (x, y, z in order), from the per-face records
-          // (momentum, energy) the separate kernel stores like the metrics
-          AT rvis[4];
-          if constexpr (VISC_PAIRS) {
-            {
-              const MT* f0 = reinterpret_cast<const MT*>(args.fv[0]);
-              const MT* f1 = reinterpret_cast<const MT*>(args.fv[1]);
-              T a[4], b[4];
-              MetricStore<T>::ld4(f0, vx + 1, a[0], a[1], a[2], a[3]);
-              MetricStore<T>::ld4(f0, vx, b[0], b[1], b[2], b[3]);
-#pragma unroll
-              for (int n = 0; n < 4; ++n) rvis[n] = a[n] - b[n];
-              MetricStore<T>::ld4(f1, vy + ni, a[0], a[1], a[2], a[3]);
-              MetricStore<T>::ld4(f1, vy, b[0], b[1], b[2], b[3]);
-#pragma unroll
-              for (int n = 0; n < 4; ++n) rvis[n] = rvis[n] + (a[n] - b[n]);
-              if (DIM3) {
-                const MT* f2 = reinterpret_cast<const MT*>(args.fv[2]);
-                MetricStore<T>::ld4(f2, vz + vzs, a[0], a[1], a[2], a[3]);
-                MetricStore<T>::ld4(f2, vz, b[0], b[1], b[2], b[3]);
-#pragma unroll
-                for (int n = 0; n < 4; ++n) rvis[n] = rvis[n] + (a[n] - b[n]);
-              }
-            }
-          }
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
             const T x1 = Fx[n * NXI + y * (TX + 1) + x + 1], x0 = Fx[n * NXI + y * (TX + 1) + x];
@@ -468,9 +454,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
               if (DIM3)
                 r = r + Acc<T>::diff(Fz[((k + 1) & 1) * 5 * NZETA + n * NZETA + cc],
                                      Fz[(k & 1) * 5 * NZETA + n * NZETA + cc]);
-              if constexpr (VISC_PAIRS) {
-                if (n > 0) r = r - rvis[n - 1];
-              }
               if constexpr (std::is_same<AT, df64>::value) {
                 if (args.srcvol2) {
                   const float2 sv = __ldg(args.srcvol2 + src_off + n * ncell_b);

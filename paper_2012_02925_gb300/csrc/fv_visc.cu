@@ -18,7 +18,7 @@
 // from the ring.  The conserved state of the next plane is copied
 // asynchronously into a staging plane while the faces are computed.  The
 // fluxes go to per-face records (4 values, 32 bytes) that the fused stage
-// kernel differences per cell.
+// kernel subtracts from each face's inviscid flux.
 #include <cuda_pipeline.h>
 
 #include "fv_arith.cuh"
