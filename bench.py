@@ -246,19 +246,26 @@ def make_solver(pb, precision, tile=0, kchunk=0, tune=True, reps=3):
     return s
 
 
-def time_steps(s, pb, steps, warmup, use_graph=True):
+def time_steps(s, pb, steps, warmup, use_graph=True, per_step=None):
+    """Device time of `steps` RK steps (CUDA events on the launching stream);
+    with a list `per_step`, an event after every step also gives each step's
+    time (the repeats whose spread is reported)."""
     import torch
     for _ in range(warmup):
         s.rk_step(pb.dt, use_graph=use_graph)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1 if per_step is not None else 2)]
+    ev[0].record(st)
+    for n in range(steps):
         s.rk_step(pb.dt, use_graph=use_graph)
-    e1.record(st)
+        if per_step is not None:
+            ev[n + 1].record(st)
+    ev[-1].record(st)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / 1e3
+    if per_step is not None:
+        per_step.extend(ev[n].elapsed_time(ev[n + 1]) for n in range(steps))
+    return ev[0].elapsed_time(ev[-1]) / 1e3
 
 
 def time_stage_kernels(s, pb, reps):
@@ -349,7 +356,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        elapsed = time_steps(s, pb, args.steps, 0)
+        step_ms = []
+        elapsed = time_steps(s, pb, args.steps, 0, per_step=step_ms)
     if dist:
         elapsed = max_over_ranks(elapsed, dist, "cuda")
     cell_updates = pb.ncells * M * args.steps * world
@@ -369,6 +377,9 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps * 1e3,
+        # the K timed steps as repeats (an event after each): their spread
+        "spread": {"repeats": len(step_ms), "ms_per_step_min": min(step_ms),
+                   "ms_per_step_median": statistics.median(step_ms), "ms_per_step_max": max(step_ms)},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
