@@ -547,8 +547,20 @@ def cpu_baseline(name: str, min_seconds: float = 10.0, max_steps: int = 400):
         q = o.run(q, sp.dt, M)
         steps += 1
     el = time.perf_counter() - t0
+    # the same on one core (the paper compares its GPU codes with 1 and 16
+    # CPU cores): whole RK steps for at least 3 s
+    o1 = oracle.Oracle(sp, threads=1)
+    q1 = sp.q.copy()
+    steps1 = 0
+    t1 = time.perf_counter()
+    while steps1 < max_steps and (time.perf_counter() - t1) < 3.0:
+        q1 = o1.run(q1, sp.dt, M)
+        steps1 += 1
+    el1 = time.perf_counter() - t1
     return {"value": sp.ncells * M * steps / el / 1e9, "unit": "Gcell-updates/s", "cores": cores,
-            "kind": "oracle", "sample": desc + ", %d step(s) of %d stages after one warm-up step, %.1f s" % (steps, M, el)}
+            "kind": "oracle", "sample": desc + ", %d step(s) of %d stages after one warm-up step, %.1f s" % (steps, M, el),
+            "single_core": {"value": sp.ncells * M * steps1 / el1 / 1e9, "cores": 1,
+                            "sample": "the same sample, %d step(s), %.1f s" % (steps1, el1)}}
 
 
 def run_reference(args):
