@@ -347,3 +347,17 @@ def test_adjoint_refuses_other_fluxes():
         s.adjoint_vjp(1, pb.dt, torch.from_numpy(pb.q).cuda(), z, z.clone(), z.clone())
     assert e.value.code == fv.FV_ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_zero_time_step_leaves_the_state(prec):
+    """Degenerate step: with dt = 0 every stage's update alpha dt / Omega R
+    vanishes, so Q^(M) = Q^(0) bit for bit in every form (graph and plain)."""
+    pb = cases.mms_3d((19, 11, 7), curvilinear=True)
+    s = solver(pb, prec)
+    q0 = s.get_state(0).cpu().numpy().copy()
+    s.rk_step(0.0, use_graph=False)
+    s.rk_step(0.0, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    assert np.array_equal(got, q0)
