@@ -142,22 +142,26 @@ __global__ void __launch_bounds__(TX * TY, 2) visc_faces_kernel(const FvViscArgs
     if (e >= W * H || kk < -1 || kk > nk || ci > ni || cj > nj) return -1;
     return qoff + (long long)(kk + 2) * kst + (long long)(cj + 2) * jst + (ci + 2);
   };
-  // Double-float: T goes into the ring as T - tref with T formed in
-  // binary64 and tref a binary32 value, the T of the tile's first interior
-  // cell.  The T gradient divides differences of T by the cell size, so
-  // double-float's ~48-bit significand of T itself cost the 128^3 laminar
-  // energy residual 2e-12 of its terms' scale; the deviation keeps those
-  // bits (binary64 T: no reference).
+  // Double-float: T goes into the ring as T - tref, tref a binary32 value
+  // (the T of the tile's first interior cell).  The T gradient divides
+  // differences of T by the cell size, so double-float's ~48-bit
+  // significand of T itself cost the 128^3 laminar energy residual 2e-12 of
+  // its terms' scale.  The deviation is formed without that loss: its
+  // numerator rho^2 R (T - tref) = (gamma - 1)(E rho - |m|^2 / 2) - tref R
+  // rho^2 in binary64 (products only: no binary64 division), then divided by
+  // rho^2 R in double-float, whose relative error now applies to the small
+  // deviation (binary64 T: no reference).
   constexpr bool TDEV = std::is_same<T, df64>::value;
-  auto temp_d = [&](double r, double m1, double m2, double m3, double en) {
-    return (a.vp.gamma - 1.0) * fma(en, r, -0.5 * (m1 * m1 + m2 * m2 + m3 * m3)) / (r * r * a.vp.r_gas);
-  };
+  const double gm1d = a.vp.gamma - 1.0;
   double tref_d = 0.0;
   if constexpr (TDEV) {
     const int ri = min(tile.i0, ni - 1), rj = min(tile.j0, nj - 1), rk = THREE ? min(k0, nk - 1) : 0;
     const long long c = qoff + (long long)(rk + 2) * kst + (long long)(rj + 2) * jst + (ri + 2);
-    tref_d = (double)(float)temp_d(q[c], q[c + pl], q[c + 2 * pl], q[c + 3 * pl], q[c + 4 * pl]);
+    const double r = q[c], m1 = q[c + pl], m2 = q[c + 2 * pl], m3 = q[c + 3 * pl];
+    tref_d = (double)(float)(gm1d * fma(q[c + 4 * pl], r, -0.5 * (m1 * m1 + m2 * m2 + m3 * m3)) /
+                             (r * r * a.vp.r_gas));
   }
+  const double tref_rd = tref_d * a.vp.r_gas;
   const T tref = S::from_d(tref_d);
   // (u, v, w, T) of one cell from its conserved state into ring slot sl;
   // the never-filled corners of the ghost frame (density 0) and cells
@@ -171,7 +175,8 @@ __global__ void __launch_bounds__(TX * TY, 2) visc_faces_kernel(const FvViscArgs
       v = S::from_d(m2) * ri;
       w = S::from_d(m3) * ri;
       if constexpr (TDEV) {
-        t = S::from_d(temp_d(r, m1, m2, m3, en) - tref_d);
+        const double num = fma(gm1d, fma(en, r, -0.5 * (m1 * m1 + m2 * m2 + m3 * m3)), -(tref_rd * r) * r);
+        t = S::from_d(num) * ri * ri * iR;
       } else {
         const T p = gm1 * (S::from_d(en) - S::c(0.5) * rho * (u * u + v * v + w * w));
         t = p * ri * iR;
