@@ -209,10 +209,15 @@ class ClockSampler:
 
 
 def kernel_hash() -> str:
+    """Hash of the sources the fused stage kernel is compiled from (its
+    template, face code, arithmetic, shared structures and the translation
+    units instantiating it): the traffic measured for it is valid while this
+    is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2012_02925_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f in ("fv_stage.cuh", "fv_face.cuh", "fv_arith.cuh", "fv_viscface.cuh", "fv_internal.h") or \
+                (f.startswith("fv_stage_") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
