@@ -100,8 +100,8 @@ constexpr int stage_min_ctas() {
 // VISC: the laminar viscous terms.  The binary32 form evaluates them in the
 // face loop (FUSED_VISC); the wider forms subtract the per-face fluxes of the
 // separate viscous kernel from each face's inviscid flux in the face loop
-// (VISC_PAIRS: one record load per face, issued before the inviscid flux
-// whose arithmetic covers its latency).  Without VISC
+// (VISC_PAIRS: one record load per face after the inviscid flux; loaded
+// before it, the record's registers slowed the flux by 4 %).  Without VISC
 // neither code path exists in the kernel.  BC: the boundary-code lookup and
 // the overwritten wall and farfield fluxes; without it (no block has such a
 // face) their code is not compiled in, which on the 128^3 block made both
@@ -225,13 +225,6 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         const MT* m = dir == 0 ? mxi : (dir == 1 ? meta : mzeta);
         MetricStore<T>::ld4(m, f, nx, ny, nz, A);
       }
-      // the separate viscous kernel's F_v.S of this face (same face order
-      // as the metrics, all blocks); loaded here, used after the flux
-      T fva, fvb, fvc, fvd;
-      if constexpr (VISC_PAIRS) {
-        const MT* vr = reinterpret_cast<const MT*>(args.fv[dir == 0 ? 0 : (dir == 1 ? 1 : 2)]);
-        MetricStore<T>::ld4(vr, B.vface_off[dir] + (f - B.face_off[dir]), fva, fvb, fvc, fvd);
-      }
       T out[5];
       if (code == FV_BCK_SLIP_WALL || code == FV_BCK_NOSLIP_WALL) {
         // nearest interior cells: s2, s3 on a min face, s1, s0 on a max face
@@ -256,7 +249,12 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         for (int n = 0; n < 4; ++n) out[1 + n] = out[1 + n] - fvv[n];
       }
       if constexpr (VISC_PAIRS) {
-        // F_i - F_v, as the fused binary32 path stores it
+        // F_i - F_v, as the fused binary32 path stores it; the separate
+        // viscous kernel's F_v.S of this face (same face order as the
+        // metrics, all blocks)
+        T fva, fvb, fvc, fvd;
+        const MT* vr = reinterpret_cast<const MT*>(args.fv[dir == 0 ? 0 : (dir == 1 ? 1 : 2)]);
+        MetricStore<T>::ld4(vr, B.vface_off[dir] + (f - B.face_off[dir]), fva, fvb, fvc, fvd);
         out[1] = out[1] - fva;
         out[2] = out[2] - fvb;
         out[3] = out[3] - fvc;
