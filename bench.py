@@ -337,6 +337,15 @@ def max_over_ranks(x: float, dist, device: str) -> float:
     return float(t.item())
 
 
+def workload_config(pb, args, world):
+    """The JSON line's config: the workload as both arms name it."""
+    curv = pb.blocks[0].nodes is not None
+    return {"workload": pb.name, "cells": pb.ncells, "blocks": len(pb.blocks), "rk_stages": len(pb.params["alpha"]),
+            "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+            "l2_flush": "inputs larger than L2 (state+metrics %.0f MB)" % (
+                (3 * 5 * 8 * pb.ncells + (80 if curv else 0) * pb.ncells) / 1e6)}
+
+
 def run_gpu(args):
     import torch
     import paper_2012_02925_gb300 as fv  # noqa: F401
@@ -391,10 +400,7 @@ def run_gpu(args):
         "dtype": {"fp64": "f64", "df64": "f64 state / f32x2 double-float arithmetic",
                   "fp32flux": "f64 state / f32 flux / f32x2+f64 accumulate+update"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": pb.name, "cells": pb.ncells, "blocks": len(pb.blocks), "rk_stages": M,
-                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
-                   "l2_flush": "inputs larger than L2 (state+metrics %.0f MB)" % (
-                       (3 * 5 * 8 * pb.ncells + (80 if curv else 0) * pb.ncells) / 1e6)},
+        "config": workload_config(pb, args, world),
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -589,9 +595,10 @@ def run_reference(args):
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": sp.name, "cells": sp.ncells, "rk_stages": M},
+           "config": workload_config(workload(args.workload), args, int(os.environ.get("WORLD_SIZE", "1"))),
            "cpu_baseline": {"value": v, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
-                            "sample": desc},
+                            "sample": desc + " (the oracle computes in binary64), %d timed step(s) of %d stages"
+                            % (args.steps, M)},
            "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
 
