@@ -236,6 +236,20 @@ int64_t fv_cell_count(fv_handle h);
  * (fixed / Dirichlet ghosts). */
 int fv_set_state(fv_handle h, const double* q, void* stream);
 
+/* Upload overlapped with computation: fv_stage_state copies a packed ghosted
+ * state (host or device; pinned host memory for an asynchronous copy) into a
+ * handle-owned staging buffer on `stream` - typically a copy stream, so that
+ * the upload of the next step's input runs while the current step computes -
+ * and fv_set_state_staged then sets it as fv_set_state does, on `stream`
+ * (device-to-device).  The caller orders the two streams (the staged copy
+ * must be complete before fv_set_state_staged reads it, and that read before
+ * the next fv_stage_state overwrites it) and keeps the host buffer alive
+ * until the copy is done.  The first fv_stage_state allocates the staging
+ * buffer (the packed state's size; blocking).  fv_set_state_staged before
+ * any fv_stage_state: FV_ERR_INVALID_ARG. */
+int fv_stage_state(fv_handle h, const double* q, void* stream);
+int fv_set_state_staged(fv_handle h, void* stream);
+
 /* Overwrite one state buffer (0 = Q^(0), 1, 2 = stage buffers) with a packed
  * ghosted state (host or device); the other buffers are untouched.  Used to
  * replay a stage from a checkpoint (the adjoint's forward recomputation). */

@@ -23,7 +23,7 @@ EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error
            "fv_field_size", "fv_cell_count", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
            "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
-           "fv_monitor_norms")
+           "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged")
 
 
 class FvError(RuntimeError):
@@ -100,11 +100,13 @@ def load_library(path: Optional[str] = None):
     L.fv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.fv_set_boundaries.argtypes = [vp, ctypes.POINTER(fv_bc_patch), i32]
     L.fv_set_monitor.argtypes = [vp, i32]
+    L.fv_stage_state.argtypes = [vp, vp, vp]
+    L.fv_set_state_staged.argtypes = [vp, vp]
     L.fv_monitor_norms.argtypes = [vp, vp, vp]
     for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
               "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
-              "fv_monitor_norms"):
+              "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -234,6 +236,14 @@ class Solver:
     # -- C ABI calls ---------------------------------------------------------------
     def set_state(self, q, stream=None):
         self._check(self._L.fv_set_state(self._h, _ptr(q), _stream(stream)))
+
+    def stage_state(self, q, stream=None):
+        """Copy a packed state into the handle's staging buffer on `stream`
+        (see fv_stage_state); set_state_staged() then makes it the state."""
+        self._check(self._L.fv_stage_state(self._h, _ptr(q), _stream(stream)))
+
+    def set_state_staged(self, stream=None):
+        self._check(self._L.fv_set_state_staged(self._h, _stream(stream)))
 
     def set_buffer(self, buffer: int, q, stream=None):
         self._check(self._L.fv_set_buffer(self._h, int(buffer), _ptr(q), _stream(stream)))

@@ -42,6 +42,8 @@ struct fv_ctx {
   double* srcvol = nullptr;
   float2* srcvol2 = nullptr;        // S*Omega as double-float pairs (non-binary64 forms)
   double* scratch_r = nullptr;      // residual (variable-major) for norms
+  double* stage_buf = nullptr;      // a packed state staged by fv_stage_state
+  bool staged = false;
   double* partials = nullptr;       // per-CTA norm partials
   double* d_norm = nullptr;         // 11 doubles
   double* adj_contrib = nullptr;    // adjoint: per-face input cotangents (20 per face)
@@ -1254,7 +1256,7 @@ int fv_destroy(fv_handle hh) {
   for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
   cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns); cudaFree(h->d_tile_counter);
   cudaFree(h->invvol); cudaFree(h->vol); cudaFree(h->srcvol); cudaFree(h->srcvol2);
-  cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm);
+  cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm); cudaFree(h->stage_buf);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
   cudaFree(h->geo_t);
@@ -1279,6 +1281,24 @@ int fv_set_state(fv_handle hh, const double* q, void* stream) {
   for (int x = 1; x < 3; ++x)
     CK(h, cudaMemcpyAsync(h->buf[x], h->buf[0], sizeof(double) * h->state_elems, cudaMemcpyDeviceToDevice, s));
   return FV_OK;
+}
+
+int fv_stage_state(fv_handle hh, const double* q, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!q) return fail(h, FV_ERR_INVALID_ARG, "q is NULL");
+  if (!h->stage_buf) CK(h, cudaMalloc(&h->stage_buf, sizeof(double) * h->ext_state_elems));
+  CK(h, cudaMemcpyAsync(h->stage_buf, q, sizeof(double) * h->ext_state_elems, cudaMemcpyDefault,
+                        (cudaStream_t)stream));
+  h->staged = true;
+  return FV_OK;
+}
+
+int fv_set_state_staged(fv_handle hh, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (!h->staged) return fail(h, FV_ERR_INVALID_ARG, "no state has been staged");
+  return fv_set_state(hh, h->stage_buf, stream);
 }
 
 int fv_set_buffer(fv_handle hh, int buffer, const double* q, void* stream) {

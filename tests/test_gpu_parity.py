@@ -361,3 +361,27 @@ def test_zero_time_step_leaves_the_state(prec):
     got = s.get_state(0).cpu().numpy()
     s.close()
     assert np.array_equal(got, q0)
+
+
+def test_staged_upload_equals_direct_set_state():
+    """fv_stage_state + fv_set_state_staged (the upload overlapped on another
+    stream) leave exactly the state fv_set_state leaves; without a staged
+    state the second call is refused."""
+    import paper_2012_02925_gb300 as fv
+    pb = cases.mms_3d((21, 13, 9), curvilinear=True)
+    s = solver(pb, "df64")
+    with pytest.raises(fv.FvError) as e:
+        s.set_state_staged()
+    assert e.value.code == fv.FV_ERR_INVALID_ARG
+    host = torch.from_numpy(pb.q).pin_memory()
+    copy = torch.cuda.Stream()
+    s.stage_state(host, stream=copy.cuda_stream)
+    copy.synchronize()
+    s.set_state_staged()
+    s.rk_step(pb.dt, use_graph=False)
+    a = s.get_state(0).cpu().numpy()
+    s.set_state(host)
+    s.rk_step(pb.dt, use_graph=False)
+    b = s.get_state(0).cpu().numpy()
+    s.close()
+    assert np.array_equal(a, b)
