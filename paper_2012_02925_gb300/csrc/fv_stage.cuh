@@ -76,12 +76,14 @@ __device__ __forceinline__ double rk_apply(double q0, df64 fac, df64 R) {
   return q0 - fv_df2d(d);
 }
 
-template <class T, int TX, int TY>
+// NV: variables per ring cell (the primitives, and with the fused viscous
+// terms a sixth: T - tref)
+template <class T, int TX, int TY, int NV = 5>
 struct StageSmem {
   static constexpr int W = TX + 4, H = TY + 4, PL = W * H;
   static constexpr int NXI = (TX + 1) * TY, NETA = TX * (TY + 1), NZETA = TX * TY;
   static constexpr __host__ __device__ size_t typed(bool three_d) {
-    return sizeof(T) * (size_t)((three_d ? 4 : 1) * 5 * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0));
+    return sizeof(T) * (size_t)((three_d ? 4 : 1) * NV * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0));
   }
   // with prefetch: + a binary64 staging plane that cp.async fills while the
   // faces of the previous plane are computed
@@ -114,15 +116,16 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
   using CC = typename std::conditional<FAST, FaceCFast<T>, FaceC<T>>::type;
   using AT = typename Acc<T>::type;
   using MT = typename MetricStore<T>::type;
-  using SM = StageSmem<T, TX, TY>;
+  constexpr int NV = FUSED_VISC ? 6 : 5;
+  using SM = StageSmem<T, TX, TY, NV>;
   constexpr int W = SM::W, PL = SM::PL;
   constexpr int NXI = SM::NXI, NETA = SM::NETA, NZETA = SM::NZETA;
   constexpr int NSLOT = DIM3 ? 4 : 1;
   constexpr int NFACE = NXI + NETA + (DIM3 ? NZETA : 0);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Vs = reinterpret_cast<T*>(smem_raw);        // [NSLOT][5][H][W]
-  T* Fx = Vs + NSLOT * 5 * PL;                    // [5][TY][TX+1]
+  T* Vs = reinterpret_cast<T*>(smem_raw);        // [NSLOT][NV][H][W]
+  T* Fx = Vs + NSLOT * NV * PL;                   // [5][TY][TX+1]
   T* Fy = Fx + 5 * NXI;                           // [5][TY+1][TX]
   T* Fz = Fy + 5 * NETA;                          // [2][5][TY][TX]
   double* stg = reinterpret_cast<double*>(smem_raw + ((SM::typed(DIM3) + 15) / 16) * 16);  // [5][H][W] (PF)
@@ -159,20 +162,51 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
       const int j = j0 - 2 + rr, i = i0 - 2 + c;
       loff[r] = (it < PL && i < ni + 2 && j < nj + 2) ? (int)((j + 2) * js + (i + 2)) : -1;
     }
+    // The fused viscous terms difference T across one cell, so the ring's
+    // sixth variable holds T - tref (tref: the binary32 T of the tile's first
+    // interior cell) with its numerator rho^2 R (T - tref) =
+    // (gamma - 1)(E rho - |m|^2 / 2) - tref R rho^2 formed in double-float
+    // from the binary64 state: the binary32 T itself would carry 2^-24 of T
+    // into every gradient (128^3 laminar energy residual: 2.6e-5 of its
+    // terms' scale)
+    float tref = 0.0f;
+    df64 trefR = mk(0.0f, 0.0f);
+    if constexpr (FUSED_VISC) {
+      const int ri = min(i0, ni - 1), rj = min(j0, nj - 1), rk = DIM3 ? min(max(k0, 0), nk - 1) : 0;
+      const double* c = qin + (long long)(rk + 2) * ks + (long long)(rj + 2) * js + (ri + 2);
+      const double r = c[0], m1 = c[pl], m2 = c[2 * pl], m3 = c[3 * pl];
+      tref = (float)((args.vp.gamma - 1.0) * fma(c[4 * pl], r, -0.5 * (m1 * m1 + m2 * m2 + m3 * m3)) /
+                     (r * r * args.vp.r_gas));
+      trefR = fv_d2df((double)tref * args.vp.r_gas);
+    }
+    const df64 gm1_df = Sc<df64>::c(args.vp.gamma - 1.0);
+    const float iR_f = (float)(1.0 / args.vp.r_gas);
+    auto t_dev = [&](const double* qd, float rho) -> float {
+      const df64 r = fv_d2df(qd[0]), m1 = fv_d2df(qd[1]), m2 = fv_d2df(qd[2]), m3 = fv_d2df(qd[3]);
+      const df64 e = fv_d2df(qd[4]);
+      const df64 num = gm1_df * (e * r - Sc<df64>::halve(Sc<df64>::dot3(m1, m1, m2, m2, m3, m3))) - (trefR * r) * r;
+      const float ri = __fdividef(1.0f, rho);
+      return FADD(num.hi, num.lo) * ri * ri * iR_f;
+    };
     // stage plane kk (ghosted index kk + 2 in memory) into ring slot `slot`
     auto load_plane = [&](int kk, int slot) {
-      T* dst = Vs + slot * 5 * PL;
+      T* dst = Vs + slot * NV * PL;
       const double* base = qin + (long long)(kk + 2) * ks;
 #pragma unroll
       for (int r = 0; r < LROUNDS; ++r) {
         if (loff[r] < 0) continue;
         const double* src = base + loff[r];
+        double qd[5];
         T q[5], V[5];
 #pragma unroll
-        for (int n = 0; n < 5; ++n) q[n] = S::from_d(__ldg(src + n * pl));
+        for (int n = 0; n < 5; ++n) {
+          qd[n] = __ldg(src + n * pl);
+          q[n] = S::from_d(qd[n]);
+        }
         prim_from_cons(C, q, V);
 #pragma unroll
         for (int n = 0; n < 5; ++n) dst[n * PL + tid + r * NT] = V[n];
+        if constexpr (FUSED_VISC) dst[5 * PL + tid + r * NT] = t_dev(qd, V[0]);
       }
     };
 
@@ -191,17 +225,22 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
     };
     auto convert_staged = [&](int slot) {
       __pipeline_wait_prior(0);
-      T* dst = Vs + slot * 5 * PL;
+      T* dst = Vs + slot * NV * PL;
 #pragma unroll
       for (int r = 0; r < LROUNDS; ++r) {
         if (loff[r] < 0) continue;
         const int it = tid + r * NT;
+        double qd[5];
         T q[5], V[5];
 #pragma unroll
-        for (int n = 0; n < 5; ++n) q[n] = S::from_d(stg[n * PL + it]);
+        for (int n = 0; n < 5; ++n) {
+          qd[n] = stg[n * PL + it];
+          q[n] = S::from_d(qd[n]);
+        }
         prim_from_cons(C, q, V);
 #pragma unroll
         for (int n = 0; n < 5; ++n) dst[n * PL + it] = V[n];
+        if constexpr (FUSED_VISC) dst[5 * PL + it] = t_dev(qd, V[0]);
       }
     };
 
@@ -244,7 +283,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         VGeo<T>::ld10(geo, vis.gR - vis.gstep, gl);
         VGeo<T>::ld10(geo, vis.gR, gr);
         viscous_face_flux(VK, s1, s2, vis.Lbm, vis.Lbp, vis.Rbm, vis.Rbp, vis.Lcm, vis.Lcp, vis.Rcm, vis.Rcp, PL,
-                          DIM3, gl, gr, dir, dir == 0 ? 1 : 0, dir == 2 ? 1 : 2, nx * A, ny * A, nz * A, fvv);
+                          DIM3, gl, gr, dir, dir == 0 ? 1 : 0, dir == 2 ? 1 : 2, nx * A, ny * A, nz * A, tref, fvv);
 #pragma unroll
         for (int n = 0; n < 4; ++n) out[1 + n] = out[1 + n] - fvv[n];
       }
@@ -327,7 +366,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
           __syncthreads();
         }
       }
-      const T* P = Vs + slot * 5 * PL;
+      const T* P = Vs + slot * NV * PL;
       // ---- every face of this plane (and the zeta faces above it), once;
       // one call site of the face code for all three directions ----
       for (int it = tid; it < NFACE; it += NT) {
@@ -341,10 +380,10 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         long long f;
         if (DIM3 && d == 2) {
           // zeta face between planes k and k+1: stencil k-1 .. k+2 from the ring
-          s0 = Vs + ((k - 1) & 3) * 5 * PL + off;
-          s1 = Vs + (k & 3) * 5 * PL + off;
-          s2 = Vs + ((k + 1) & 3) * 5 * PL + off;
-          s3 = Vs + ((k + 2) & 3) * 5 * PL + off;
+          s0 = Vs + ((k - 1) & 3) * NV * PL + off;
+          s1 = Vs + (k & 3) * NV * PL + off;
+          s2 = Vs + ((k + 1) & 3) * NV * PL + off;
+          s3 = Vs + ((k + 2) & 3) * NV * PL + off;
           dp = Fz + ((k + 1) & 1) * 5 * NZETA + dst;
           dstr = NZETA;
           f = met + (k + 1) * kfz;
@@ -404,8 +443,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
             vis.Lcm = s1 - W; vis.Lcp = s1 + W; vis.Rcm = s2 - W; vis.Rcp = s2 + W;
           } else {
             const long long oL = s1 - P, oR = s2 - P;
-            const T* Pm = Vs + ((k - 1) & 3) * 5 * PL;
-            const T* Pp = Vs + ((k + 1) & 3) * 5 * PL;
+            const T* Pm = Vs + ((k - 1) & 3) * NV * PL;
+            const T* Pp = Vs + ((k + 1) & 3) * NV * PL;
             vis.Lcm = Pm + oL; vis.Lcp = Pp + oL; vis.Rcm = Pm + oR; vis.Rcp = Pp + oR;
           }
         }
@@ -526,7 +565,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
 // creation), so a launch is a plain enqueue that stream capture accepts.
 template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC, bool BC>
 static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  const size_t smem = StageSmem<T, TX, TY>::bytes(l.three_d != 0, PF);
+  const size_t smem = StageSmem<T, TX, TY, (VISC && std::is_same<T, float>::value) ? 6 : 5>::bytes(l.three_d != 0, PF);
   if (l.three_d) {
     fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC, BC><<<l.grid, NT, smem, s>>>(a);
   } else {
@@ -537,7 +576,7 @@ static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t 
 
 template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC, bool BC>
 static int occupancy_t(bool three_d, size_t* smem_out) {
-  const size_t smem = StageSmem<T, TX, TY>::bytes(three_d, PF);
+  const size_t smem = StageSmem<T, TX, TY, (VISC && std::is_same<T, float>::value) ? 6 : 5>::bytes(three_d, PF);
   int n = 0;
   if (three_d) {
     auto k = fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC, BC>;

@@ -7,9 +7,10 @@
 //   grad phi = [(phi_R - phi_L) A_a + D_b A_b + D_c A_c] / Omega_f,
 //   D_b = ((phi_L,b+ - phi_L,b-) + (phi_R,b+ - phi_R,b-)) / 4,
 // with A_d the mean of the two cells' averaged face vectors of family d and
-// Omega_f their mean volume (no c term in 2D).  The stencil's primitives come
-// from the kernel's shared-memory plane ring; the cell geometry records
-// (Omega, Sbar_xi, Sbar_eta, Sbar_zeta) from global memory.
+// Omega_f their mean volume (no c term in 2D).  The stencil's velocities and
+// T (as its deviation from a reference of the tile) come from the kernel's
+// shared-memory plane ring; the cell geometry records (Omega, Sbar_xi,
+// Sbar_eta, Sbar_zeta) from global memory.
 #pragma once
 #include "fv_arith.cuh"
 #include "fv_internal.h"
@@ -72,18 +73,18 @@ __device__ __forceinline__ ViscC<T> make_visc_consts(const FvViscParams& p) {
 }
 
 // fv = F_v.S (momentum x, y, z, energy) of the face between L and R along
-// axis a; cell pointers address component 0 of the primitives (rho, u, v, w,
-// p), components cs apart; gl, gr: geometry records of L and R; b_ax, c_ax:
-// the tangential axes.
+// axis a; cell pointers address component 0 of the ring cells (rho, u, v, w,
+// p, T - tref), components cs apart; gl, gr: geometry records of L and R;
+// b_ax, c_ax: the tangential axes; tref: the tile's reference T.
 template <class T>
 __device__ __forceinline__ void viscous_face_flux(const ViscC<T>& K, const T* L, const T* R, const T* Lbm,
                                                   const T* Lbp, const T* Rbm, const T* Rbp, const T* Lcm,
                                                   const T* Lcp, const T* Rcm, const T* Rcp, int cs, bool three,
                                                   const T gl[10], const T gr[10], int a_ax, int b_ax, int c_ax,
-                                                  T Sx, T Sy, T Sz, T fv[4]) {
+                                                  T Sx, T Sy, T Sz, T tref, T fv[4]) {
   using S = Sc<T>;
-  auto temp = [&](const T* c) { return c[4 * cs] * S::rcp(c[0]) * K.iR; };
-  auto phi = [&](const T* c, int m) { return m < 3 ? c[(1 + m) * cs] : temp(c); };
+  // (u, v, w) are ring variables 1..3, T - tref is variable 5
+  auto phi = [&](const T* c, int m) { return c[(m < 3 ? 1 + m : 5) * cs]; };
   const T iOm = S::rcp(S::halve(gl[0] + gr[0]));
   T Aa[3], Ab[3], Ac[3];
 #pragma unroll
@@ -113,7 +114,7 @@ __device__ __forceinline__ void viscous_face_flux(const ViscC<T>& K, const T* L,
   T uf[3];
 #pragma unroll
   for (int x = 0; x < 3; ++x) uf[x] = S::halve(L[(1 + x) * cs] + R[(1 + x) * cs]);
-  const T Tf = S::halve(tL + tR);
+  const T Tf = S::halve(tL + tR) + tref;
   T mu = K.mu;
   if (K.sutherland) {
     const T tr = Tf * K.itref;

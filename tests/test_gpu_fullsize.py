@@ -170,15 +170,6 @@ def bench_workloads():
     return get
 
 
-# The binary32 flux form's laminar terms difference binary32 primitives
-# (2^-24 relative rounding) across one cell: the gradients' error grows as
-# 1/h.  On the 128^3 manufactured solution (mu = 0.05, the viscous part a
-# sizeable fraction of R) that measured 2.6e-5 of the terms' scale; the
-# inviscid binary32 residual and the O-grid's air viscosity stay within
-# 1e-5.  Bound for the laminar 128^3 block: 5e-5.
-TOL_LAMINAR_FP32_128 = 5e-5
-
-
 @pytest.mark.parametrize("name,prec", [(w, p) for w in ("mms128+ns", "inlet", "ogrid+ns")
                                        for p in ("fp64", "df64", "fp32flux")])
 def test_boundary_and_laminar_workloads_every_cell(bench_workloads, name, prec):
@@ -187,5 +178,4 @@ def test_boundary_and_laminar_workloads_every_cell(bench_workloads, name, prec):
     s.exchange_ghosts(0)
     r = s.residual(0).cpu().numpy()
     s.close()
-    tol = TOL_LAMINAR_FP32_128 if (name == "mms128+ns" and prec == "fp32flux") else TOL_RES[prec]
-    assert rel_err_fields(r, ref, o, q) <= tol
+    assert rel_err_fields(r, ref, o, q) <= TOL_RES[prec]
