@@ -381,7 +381,7 @@ def run_gpu(args):
     stage_times, ex_time = time_stage_kernels(s, pb, min(20, max(3, args.steps // 2)))
     roof = roofline(pb, args.precision, stage_times, ex_time, curv, pk, peak_kind, traffic)
     # end to end through the public API with host buffers
-    e2e = run_e2e(s, pb, min(40, max(3, args.steps // 4)))
+    e2e = run_e2e(s, pb, min(40, max(3, args.steps // 4)), dist, world)
     launches_per_step = M * (2 if pb.conns else 1)
     result = {
         "metric": "Gcell-updates/s per RK stage",
@@ -423,7 +423,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(s, pb, steps):
+def run_e2e(s, pb, steps, dist=None, world=1):
     """Same metric through the public API with HOST buffers: per step the
     state goes host->device (pinned), one RK step runs, and the residual norms
     of the state the step starts from (10 doubles, recorded by the step's
@@ -463,14 +463,20 @@ def run_e2e(s, pb, steps):
     for name, step in (("serial", serial_step), ("overlapped", overlapped_step)):
         step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(steps):
             step()
         torch.cuda.synchronize()
-        out[name] = pb.ncells * s.n_stages * steps / (time.perf_counter() - t0) / 1e9
+        el = time.perf_counter() - t0
+        if dist:
+            el = max_over_ranks(el, dist, "cuda")
+        # whole job: every rank's cells over the slowest rank's time
+        out[name] = pb.ncells * s.n_stages * steps * world / el / 1e9
     s.set_monitor(False)
     return {"value": out["overlapped"], "unit": "Gcell-updates/s",
-            "h2d_bytes_per_step": int(pb.q.nbytes), "d2h_bytes_per_step": 80,
+            "h2d_bytes_per_step": int(pb.q.nbytes) * world, "d2h_bytes_per_step": 80 * world,
             "upload": "overlapped with the previous step on a copy stream", "serial_value": out["serial"]}
 
 
