@@ -304,7 +304,7 @@ def time_stage_kernels(s, pb, reps):
 def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, traffic):
     M = len(stage_times)
     kt = [max(t - ex_time, 1e-12) for t in stage_times]
-    byts = [algorithmic_bytes(pb, m + 1, curvilinear) - (80.0 * 0 if not pb.conns else 0.0) for m in range(M)]
+    byts = [algorithmic_bytes(pb, m + 1, curvilinear) for m in range(M)]
     gbs = sum(byts) / sum(kt) / 1e9
     hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     r = {"kernel": "fv_stage_kernel<%s>" % precision, "bytes_per_launch": sum(byts) / M,
@@ -323,8 +323,8 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
                   "frac": achieved / peak, "ops_per_launch": ops,
                   "peak_source": "derived: " + ("nominal FP64 1.25 TFLOP/s" if precision == "fp64" else
                                                 "152 SMs x 128 lanes x 2.07 GHz / binary32 cost per op")})
-    t = traffic.get(precision)
-    r["traffic"] = t
+    # measured DRAM bytes of one launch, for the workload they were captured on
+    r["traffic"] = traffic.get(precision) if traffic.get("workload") == pb.name else None
     return r
 
 
