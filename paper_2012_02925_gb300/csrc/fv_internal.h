@@ -92,7 +92,9 @@ struct FvStageArgs {
   void* rmon;                   // RK mode: the residual also stored here, [5][all cells], as binary64
                                 // (binary64 form) or (hi, lo) binary32 pairs (other forms); or null
   long long ncell_total;
-  double alpha_dt;              // alpha_m * dt
+  double alpha_dt;              // alpha_m * dt (dt_dev null)
+  const double* dt_dev;         // or: dt read from device memory (a replayed graph), alpha_dt = alpha * *dt_dev
+  double alpha;                 // alpha_m
   FvFaceParams fp;
 };
 

@@ -503,20 +503,22 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
             }
           }
           if (args.mode == FV_MODE_RK) {
+            // the same binary64 product the host forms when dt is passed by value
+            const double alpha_dt = args.dt_dev ? args.alpha * *args.dt_dev : args.alpha_dt;
             const double iv = cart ? B.cart_invvol : __ldg(args.invvol + B.cell_off + cell);
             const double* q0 = args.q0 + B.qoff + q_idx;
             double* qo = args.qout + B.qoff + q_idx;
             if constexpr (std::is_same<AT, double>::value) {
 #pragma unroll
-              for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], args.alpha_dt, iv, R[n]);
+              for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], alpha_dt, iv, R[n]);
             } else if constexpr (std::is_same<T, float>::value) {
               // binary32 increment (its rounding is far below the error of
               // the binary32 face fluxes it sums), one binary64 add
-              const float fac = FMUL(fv_d2f_rn(args.alpha_dt), fv_d2f_rn(iv));
+              const float fac = FMUL(fv_d2f_rn(alpha_dt), fv_d2f_rn(iv));
 #pragma unroll
               for (int n = 0; n < 5; ++n) qo[n * pl] = q0[n * pl] - fv_f2d(FMUL(fac, FADD(R[n].hi, R[n].lo)));
             } else {
-              const df64 fac = fv_d2df(args.alpha_dt) * fv_d2df(iv);
+              const df64 fac = fv_d2df(alpha_dt) * fv_d2df(iv);
 #pragma unroll
               for (int n = 0; n < 5; ++n) qo[n * pl] = rk_apply(q0[n * pl], fac, R[n]);
             }
