@@ -3,12 +3,18 @@
 Metric: Gcell-updates/s per RK stage (cells x stages / s) on the 3D
 manufactured-solution block, 128^3 perturbed-curvilinear cells, FP64 state,
 MUSCL + van Leer + Roe, 4-stage RK (the synthetic stand-in for the paper's
-cases; Section 8 cases' grids are not available).  One step = one full RK
-step: per stage the ghost exchange and the fused residual + update kernel.
+cases; Section 8 cases' grids are not available), in plain binary64
+arithmetic.  One step = one full RK step: per stage the ghost fill and the
+fused residual + update kernel.
 
-Printed: one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
-(the only other place this file runs oracle code) on a bounded sample of the
-same workload.
+Printed (rank 0): one JSON line per variant workload / form and one for the
+adjoint workload, then LAST the short headline line.  Its ``forms`` list
+reports the double-float and binary32-flux forms and the batched multi-block
+workload against the binary64 line, with each form's error against the
+binary64 path (one residual; and the binary32-flux form's drift after 100
+stages).  ``--impl reference`` times the CPU oracle (the only other place
+this file runs oracle code) on a bounded sample of the same workload;
+``--peaks`` prints the measured arithmetic rates only.
 """
 from __future__ import annotations
 
@@ -61,10 +67,24 @@ def alu_ops_per_cell(dim: int = 3, visc: bool = False) -> int:
     return n
 
 
-def alu_peak(precision: str) -> float:
-    """FP64-operation roofline of the arithmetic forms: the nominal FP64 rate
-    for binary64; for double-float, the FP32 lane rate divided by the mean
-    binary32 cost of one emulated operation over the face's operation mix."""
+def alu_peak(precision: str, rates: dict):
+    """Measured FP64-operation roofline of the arithmetic forms and how it
+    was obtained.  binary64: twice the measured binary64 FMA rate (FLOP/s,
+    an FMA counted as two operations).  double-float: the measured rate of
+    the face's operation mix, sum_k n_k / sum_k (n_k / rate_k) over the
+    oracle's per-face counts n_k of add, multiply, divide, square root and
+    absolute value and the measured double-float rate of each."""
+    if precision == "fp64":
+        return 2.0 * rates["fp64_fma"], "measured: 2 x binary64 FMA rate (fv_probe_alu_rates)"
+    key = {"add": "df64_add", "mul": "df64_mul", "div": "df64_div", "sqrt": "df64_sqrt", "abs": "df64_abs"}
+    t = sum(FACE_OPS[k] / rates[key[k]] for k in FACE_OPS)
+    return sum(FACE_OPS.values()) / t, "measured: double-float rates over the face's operation mix"
+
+
+def nominal_alu_peak(precision: str) -> float:
+    """Unit-count estimate, for context beside the measured peak: the
+    nominal FP64 rate, or the FP32 lane rate over the mean binary32 cost of
+    one emulated operation in the face's mix."""
     if precision == "fp64":
         return FP64_NOMINAL_FLOPS
     mix = sum(FACE_OPS[k] * DF64_COST[k] for k in FACE_OPS) / sum(FACE_OPS.values())
@@ -301,7 +321,13 @@ def time_stage_kernels(s, pb, reps):
     return out, ex
 
 
-def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, traffic):
+def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, traffic, rates):
+    """Roofline of the fused stage kernel: algorithmic work per launch over
+    the launch's average CUDA-event time (the ghost fill subtracted).  The
+    FP64-accurate forms are bound by arithmetic: algorithmic FP64 operations
+    (the oracle's counts) against the measured peak of their arithmetic; the
+    binary32-flux form by HBM: algorithmic bytes against the measured copy
+    bandwidth.  The HBM fraction is reported for every form."""
     M = len(stage_times)
     kt = [max(t - ex_time, 1e-12) for t in stage_times]
     byts = [algorithmic_bytes(pb, m + 1, curvilinear) for m in range(M)]
@@ -312,17 +338,14 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
     r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": peak_kind}
     if precision == "fp32flux":
         r.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                  "peak_source": peak_kind})
+                  "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"})
     else:
-        # FP64-accurate forms are bound by arithmetic: algorithmic FP64
-        # operations per launch / launch time against the derived peak
         ops = alu_ops_per_cell(pb.dim, bool(pb.params.get("visc", 0))) * pb.ncells
         achieved = ops / (sum(kt) / M) / 1e9
-        peak = alu_peak(precision) / 1e9
-        r.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s (FP64 ops)",
-                  "frac": achieved / peak, "ops_per_launch": ops,
-                  "peak_source": "derived: " + ("nominal FP64 1.25 TFLOP/s" if precision == "fp64" else
-                                                "152 SMs x 128 lanes x 2.07 GHz / binary32 cost per op")})
+        peak, how = alu_peak(precision, rates)
+        r.update({"bound": "alu", "achieved": achieved, "peak": peak / 1e9, "unit": "G FP64-op/s",
+                  "frac": achieved / (peak / 1e9), "ops_per_launch": ops, "peak_source": how,
+                  "nominal_peak": nominal_alu_peak(precision) / 1e9})
     # measured DRAM bytes of one launch, for the workload they were captured on
     r["traffic"] = traffic.get(precision) if traffic.get("workload") == pb.name else None
     return r
@@ -346,9 +369,68 @@ def workload_config(pb, args, world):
                 (3 * 5 * 8 * pb.ncells + (80 if curv else 0) * pb.ncells) / 1e6)}
 
 
+def sig(x, n=4):
+    """Round for the compact headline line (floats to n significant digits)."""
+    if isinstance(x, float):
+        return float("%.*g" % (n, x)) if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: sig(v, n) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, n) for v in x]
+    return x
+
+
+def compact_roofline(r):
+    keys = ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source")
+    out = {k: r[k] for k in keys if k in r}
+    out["hbm_frac"] = r["hbm"]["frac"]
+    out["kernel"] = r["kernel"]
+    out["avg_launch_ms"] = r["avg_launch_s"] * 1e3
+    return out
+
+
+def field_errors(a, b):
+    """Per variable max|a - b| / max|b| over a [5][n] field pair (plain
+    relative L-infinity, the paper's parallel-vs-serial measure)."""
+    a = a.reshape(5, -1)
+    b = b.reshape(5, -1)
+    out = []
+    for v in range(5):
+        m = float(np.abs(b[v]).max())
+        out.append(float(np.abs(a[v] - b[v]).max()) / m if m > 0 else 0.0)
+    return out
+
+
+def form_errors(pb, stages=100):
+    """Each form's error against the binary64 path on the benchmark block:
+    one residual of the initial state (plain relative L-infinity per
+    variable) and the interior state after `stages` RK stages (the drift).
+    The binary64 path itself matches the CPU oracle within 1e-12 (one
+    residual) and 1e-10 (100 stages) in the GPU parity tests."""
+    import torch
+    ref_r = ref_q = None
+    out = {}
+    b = pb.blocks[0]
+    g = (b.nk + 4, b.nj + 4, b.ni + 4)
+    for prec in ("fp64", "df64", "fp32flux"):
+        s = make_solver(pb, prec, tune=False)
+        r = s.residual(0).cpu().numpy()
+        for _ in range(stages // s.n_stages):
+            s.rk_step(pb.dt, use_graph=True)
+        q = s.get_state(0).view(5, *g)[:, 2:-2, 2:-2, 2:-2].reshape(5, -1).cpu().numpy()
+        s.close()
+        torch.cuda.synchronize()
+        if prec == "fp64":
+            ref_r, ref_q = r, q
+            continue
+        out[prec] = {"residual_rel_linf": field_errors(r, ref_r), "drift_stages": stages,
+                     "state_rel_linf": field_errors(q, ref_q)}
+    return out
+
+
 def run_gpu(args):
     import torch
-    import paper_2012_02925_gb300 as fv  # noqa: F401
+    import paper_2012_02925_gb300 as fv
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -357,6 +439,7 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    rates = fv.probe_alu_rates()
     pb = workload(args.workload)
     curv = pb.blocks[0].nodes is not None
     s = make_solver(pb, args.precision, args.tile, args.kchunk)
@@ -379,10 +462,39 @@ def run_gpu(args):
     pk, peak_kind = peaks()
     traffic = load_traffic()
     stage_times, ex_time = time_stage_kernels(s, pb, min(20, max(3, args.steps // 2)))
-    roof = roofline(pb, args.precision, stage_times, ex_time, curv, pk, peak_kind, traffic)
+    roof = roofline(pb, args.precision, stage_times, ex_time, curv, pk, peak_kind, traffic, rates)
     # end to end through the public API with host buffers
     e2e = run_e2e(s, pb, min(40, max(3, args.steps // 4)), dist, world)
-    launches_per_step = M * (2 if pb.conns else 1)
+    launch = s.launch()
+    s.close()
+    if rank == 0:
+        print(json.dumps({"headline_launch": launch, "roofline": sig(roof)}))
+    launches_per_step = M * (1 + (1 if pb.conns else 0) + (1 if getattr(pb, "bcs", None) else 0))
+    forms = []
+    if args.variants and rank == 0 and world == 1:
+        variants = run_variants(args, pk, peak_kind, traffic, rates)
+        for v in variants:
+            print(json.dumps({"variant": sig(v)}))
+        try:
+            adj = run_adjoint(rates=rates, pk=pk, peak_kind=peak_kind)
+        except Exception as e:  # report, do not hide
+            adj = {"error": str(e)}
+        print(json.dumps({"adjoint": sig(adj)}))
+        errs = form_errors(pb)
+        for v in variants:
+            if v.get("workload") == pb.name and v.get("precision") in ("df64", "fp32flux"):
+                f = {"form": v["precision"], "value": v["value"], "vs_fp64": v["value"] / value,
+                     "bound": v["roofline"]["bound"], "frac": v["roofline"]["frac"],
+                     "hbm_frac": v["roofline"]["hbm"]["frac"]}
+                e = errs.get(v["precision"], {})
+                f["err_residual"] = max(e.get("residual_rel_linf", [float("nan")]))
+                f["drift_100_stages"] = sig(e.get("state_rel_linf"), 2)
+                forms.append(f)
+        for v in variants:
+            if v.get("blocks", 1) > 1 and "error" not in v:
+                forms.append({"form": "batched %d blocks %s" % (v["blocks"], v["precision"]), "value": v["value"],
+                              "vs_fp64": v["value"] / value, "bound": v["roofline"]["bound"],
+                              "frac": v["roofline"]["frac"], "hbm_frac": v["roofline"]["hbm"]["frac"]})
     result = {
         "metric": "Gcell-updates/s per RK stage",
         "value": value,
@@ -392,8 +504,8 @@ def run_gpu(args):
         "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps * 1e3,
         # the K timed steps as repeats (an event after each): their spread
-        "spread": {"repeats": len(step_ms), "ms_per_step_min": min(step_ms),
-                   "ms_per_step_median": statistics.median(step_ms), "ms_per_step_max": max(step_ms)},
+        "spread": {"repeats": len(step_ms), "min_ms": min(step_ms), "median_ms": statistics.median(step_ms),
+                   "max_ms": max(step_ms)},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -401,24 +513,16 @@ def run_gpu(args):
                   "fp32flux": "f64 state / f32 flux / f32x2+f64 accumulate+update"}[args.precision],
         "data": "synthetic",
         "config": workload_config(pb, args, world),
-        "roofline": roof,
+        "roofline": compact_roofline(roof),
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
-        "stage_kernel_ms": [t * 1e3 for t in stage_times],
-        "launch": s.launch(),
+        "forms": forms,
     }
-    if args.variants and rank == 0 and world == 1:
-        result["variants"] = run_variants(args, pk, peak_kind, traffic)
-        try:
-            result["adjoint"] = run_adjoint()
-        except Exception as e:  # report, do not hide
-            result["adjoint"] = {"error": str(e)}
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args.workload)
-    s.close()
     if rank == 0:
-        print(json.dumps(result))
+        print(json.dumps(sig(result)))
     if dist:
         dist.destroy_process_group()
 
@@ -477,10 +581,10 @@ def run_e2e(s, pb, steps, dist=None, world=1):
     s.set_monitor(False)
     return {"value": out["overlapped"], "unit": "Gcell-updates/s",
             "h2d_bytes_per_step": int(pb.q.nbytes) * world, "d2h_bytes_per_step": 80 * world,
-            "upload": "overlapped with the previous step on a copy stream", "serial_value": out["serial"]}
+            "upload": "overlapped (copy stream)", "serial_value": out["serial"]}
 
 
-def run_adjoint(n=96, nstages=50):
+def run_adjoint(n=96, nstages=50, rates=None, pk=None, peak_kind=None):
     """Discrete adjoint workload: 96^3 curvilinear block, van Albada, Harten
     fix on every eigenvalue, J = integrated pressure on the k=0 face after 50
     RK stages; forward with stage checkpoints, then the VJP chain."""
@@ -521,13 +625,22 @@ def run_adjoint(n=96, nstages=50):
     torch.cuda.synchronize()
     vjp_s = e0.elapsed_time(e1) / 1e3 / 5
     s.close()
-    return {"workload": pb.name + "_adjoint", "stages": nstages, "cells": pb.ncells,
-            "forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1,
-            "vjp_stage_ms": vjp_s * 1e3, "vjp_value": pb.ncells / vjp_s / 1e9, "unit": "Gcell-updates/s",
-            "precision": "fp64"}
+    out = {"workload": pb.name + "_adjoint", "stages": nstages, "cells": pb.ncells,
+           "forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1,
+           "vjp_stage_ms": vjp_s * 1e3, "vjp_value": pb.ncells / vjp_s / 1e9, "unit": "Gcell-updates/s",
+           "precision": "fp64"}
+    if rates is not None:
+        # one VJP stage reads the checkpoint (40 B) and lambda_out (40 B),
+        # the metrics (80 B), and writes lambda_in (40 B) and updates
+        # lambda_Q0 (80 B): 280 B per cell
+        byts = 280.0 * pb.ncells
+        hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+        out["roofline"] = {"bound": "alu", "hbm_frac": byts / vjp_s / 1e9 / hbm,
+                           "fp64_peak_g": 2.0 * rates["fp64_fma"] / 1e9, "peak_source": peak_kind}
+    return out
 
 
-def run_variants(args, pk, peak_kind, traffic):
+def run_variants(args, pk, peak_kind, traffic, rates):
     out = []
     specs = [(w, p) for w in args.variant_workloads.split(",") for p in args.variant_precisions.split(",")]
     cache = {}
@@ -548,7 +661,7 @@ def run_variants(args, pk, peak_kind, traffic):
             out.append({"workload": pb.name, "precision": prec, "blocks": len(pb.blocks), "cells": pb.ncells,
                         "value": pb.ncells * s.n_stages * steps / el / 1e9, "unit": "Gcell-updates/s",
                         "launch": s.launch(), "ghost_fill_s": ex,
-                        "roofline": roofline(pb, prec, st, ex, curv, pk, peak_kind, traffic)})
+                        "roofline": roofline(pb, prec, st, ex, curv, pk, peak_kind, traffic, rates)})
             s.close()
         except Exception as e:  # report, do not hide
             out.append({"workload": wname, "precision": prec, "error": str(e)})
@@ -636,16 +749,29 @@ def run_reference(args):
     print(json.dumps(res))
 
 
+def run_peaks():
+    """Measured arithmetic rates of the current GPU (fv_probe_alu_rates) and
+    the peaks the forms are graded against, one JSON line."""
+    import torch
+    import paper_2012_02925_gb300 as fv
+    torch.cuda.set_device(0)
+    rates = fv.probe_alu_rates()
+    out = {"gpu": torch.cuda.get_device_name(0), "rates_per_s": rates,
+           "peaks": {p: dict(zip(("value_per_s", "how"), alu_peak(p, rates))) for p in ("fp64", "df64")},
+           "nominal": {p: nominal_alu_peak(p) for p in ("fp64", "df64")}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # 200 steps of the 128^3 block: a timed region of ~0.7 s, long enough for
-    # several clock samples
+    # 200 steps of the 128^3 block: a timed region of a few seconds, long
+    # enough for many clock samples
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fvgb", choices=["fvgb", "reference"])
     ap.add_argument("--workload", default="mms128")
-    ap.add_argument("--precision", default="df64", choices=["fp64", "df64", "fp32flux"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32flux"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
@@ -653,10 +779,13 @@ def main():
                     default="vortex,mms128,multiblock,large,mms128+vl,mms128+sw,inlet,ogrid,mms128+ns,ogrid+ns")
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--peaks", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.peaks:
+        run_peaks()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

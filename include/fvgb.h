@@ -303,9 +303,19 @@ int fv_residual(fv_handle h, int buffer, double* r_dev, void* stream);
  * fv_set_monitor) also its two reduction kernels. */
 int fv_rk_stage(fv_handle h, int stage, double dt, void* stream);
 
-/* A whole time step: stages 1..n_stages.  With use_graph != 0 the stage
- * sequence is captured once per (stream, dt) as a CUDA graph and replayed. */
+/* A whole time step: stages 1..n_stages (Section 2's M-step scheme).  With
+ * use_graph != 0 the stage sequence is captured once per stream as a CUDA
+ * graph and replayed; the graph reads dt from a device slot of its own, which
+ * a one-thread kernel on `stream` rewrites whenever dt differs from the
+ * previous step's, so a changing dt (CFL-based stepping) re-captures nothing.
+ * At most 8 streams keep a graph; a ninth evicts the least recently used one
+ * (after a device synchronisation).  The first step on a stream allocates 8
+ * bytes and instantiates its graph (blocking). */
 int fv_rk_step(fv_handle h, double dt, int use_graph, void* stream);
+
+/* Number of RK-step graphs fv_rk_step currently holds (one per stream it has
+ * stepped on, at most 8); -1 for a NULL handle. */
+int fv_graph_count(fv_handle h);
 
 /* Residual norms of buffer `buffer` (after a ghost exchange of it): per
  * variable L2 = sqrt(mean over all interior cells of R^2) in out_host[0..4]
@@ -358,6 +368,72 @@ int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, con
                    double* lam_in_dev, double* lam_q0_dev, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Cross-device halo: connections whose two sides live on different devices
+ * (ranks) after the blocks are split and aggregated onto processors
+ * (Section 4: Cartesian splitting, over-decomposition and aggregation;
+ * Section 5: decomposing and re-linking connected boundaries).  Section 7.2
+ * V1 packs such boundary data into contiguous send buffers and unpacks
+ * received ones on the GPU, V5/V6 exchange them with non-blocking calls, all
+ * posted before the wait, and V10 (GPUDirect) sends device buffers directly.
+ * The library does the device half: fv_halo_pack gathers this handle's donor
+ * cells into a send buffer and fv_halo_unpack scatters a receive buffer into
+ * this handle's ghost cells; the transfer itself is the caller's (e.g.
+ * NCCL/torch.distributed point-to-point calls on the device buffers).
+ *
+ * Each slab is one fv_connection as fv_create_blocks defines it, with only
+ * the local side's block index meaningful:
+ *   send[i]: src_block (this handle's block), src_face, src_lo, transform,
+ *            and dst_face, dst_lo, dst_hi (the receiver's patch, which fixes
+ *            the item order and count); dst_block is ignored;
+ *   recv[i]: dst_block (this handle's block), dst_face, dst_lo, dst_hi;
+ *            src_block, src_face, src_lo and transform are ignored.
+ * A slab holds n = 2 L0 L1 ghost cells (depth 1 and 2, L0 = dst_hi[0] -
+ * dst_lo[0], L1 = dst_hi[1] - dst_lo[1]) in the order (a, b, depth), a
+ * fastest, as 5 variable planes of n doubles; slabs lie back to back in table
+ * order.  A sender and its receiver must list a connection with the same
+ * dst patch, in the same position of their tables' segments for each other.
+ * fv_set_halo validates the tables (FV_ERR_INVALID_ARG: ranges, transforms,
+ * recv patches overlapping each other or this handle's own connections),
+ * replaces any previous tables and synchronises the device; the device
+ * tables it allocates are freed by fv_destroy.  Blocks whose ghosts come from
+ * a recv slab must not also have them fixed by fv_set_state's caller. */
+int fv_set_halo(fv_handle h, const fv_connection* send, int nsend, const fv_connection* recv, int nrecv);
+
+/* Doubles in the send (recv == 0) or receive (recv != 0) buffer: 5 x the
+ * slab cells of the table; -1 for a NULL handle. */
+int64_t fv_halo_size(fv_handle h, int recv);
+
+/* Gather the send slabs' donor cells (depth 1, 2 inside the src face) of
+ * state buffer `buffer` (0, 1, 2 as fv_rk_stage numbers them) into send_dev
+ * (device, fv_halo_size(h, 0) doubles).  One kernel launch on `stream`;
+ * nothing when the table is empty. */
+int fv_halo_pack(fv_handle h, int buffer, double* send_dev, void* stream);
+
+/* Scatter recv_dev (device, fv_halo_size(h, 1) doubles, as a sender's
+ * fv_halo_pack wrote it) into the recv slabs' ghost cells of state buffer
+ * `buffer`.  One kernel launch on `stream`. */
+int fv_halo_unpack(fv_handle h, int buffer, const double* recv_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Arithmetic throughput probe (measurement support; no paper counterpart).
+ * The paper's P100/V100 ran binary64 at half the binary32 rate; the stage
+ * kernel's arithmetic roofline on another part needs that part's measured
+ * rates.  Runs short probe kernels on the current device (8 CTAs of 256
+ * threads per SM, 8 independent dependency chains per thread) and writes to
+ * out_host (host pointer, n_out >= FV_PROBE_NRATES doubles) operations per
+ * second of: [0] binary64 FMA, [1] add, [2] multiply, [3] the compiler's IEEE
+ * reciprocal 1.0/x, [4] IEEE square root, [5] binary32 FMA, and the
+ * double-float operations of the stage kernel's other form: [6] add,
+ * [7] multiply, [8] quotient, [9] square root, [10] absolute value.
+ * Allocates and frees 2 KB, synchronises `stream`, takes ~50 ms.
+ * FV_ERR_INVALID_ARG for a NULL pointer or short array, FV_ERR_CUDA if a
+ * launch fails.
+ * ------------------------------------------------------------------------- */
+#define FV_PROBE_NRATES 11
+
+int fv_probe_alu_rates(double* out_host, int n_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free residual norms.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory while they
  * run - code inside a CUDA-graph capture or a framework's caching allocator
@@ -376,8 +452,12 @@ int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, con
  * the library until the process exits, it is shared by every call, and calls
  * whose kernels overlap on the GPU race on it (serialise them on one stream).
  * The first call on a device looks up that array's device address, so make
- * it before any stream capture that includes this call.  Nothing is
- * allocated or freed.
+ * it before any stream capture that includes this call; the address is kept
+ * until the process exits, so after a cudaDeviceReset() of a device this
+ * entry point must not be called on that device again.  Nothing is
+ * allocated or freed.  The launch status returned is that of this call's
+ * own launches (an error left by an earlier, unrelated call is neither
+ * reported nor cleared).
  * Returns FV_ERR_INVALID_ARG for NULL pointers or n outside
  * [1, FV_NOALLOC_MAX_N], FV_ERR_CUDA when the address lookup or a launch
  * fails, FV_ERR_UNSUPPORTED for device ordinals above 63.

@@ -8,8 +8,8 @@ memory and streams; every numerical step runs in the library's CUDA kernels.
 """
 from ._binding import (EXPORTS, FV_ERR_CUDA, FV_ERR_INVALID_ARG, FV_ERR_NONFINITE, FV_ERR_OOM,
                        FV_ERR_TIMEOUT, FV_ERR_UNSUPPORTED, FV_OK, LIB_PATH, PREC_DF64, PREC_FP32FLUX,
-                       PREC_FP64, PRECISIONS, FvError, Solver, load_library)
+                       PREC_FP64, PRECISIONS, FvError, Solver, load_library, probe_alu_rates)
 
-__all__ = ["Solver", "FvError", "load_library", "LIB_PATH", "EXPORTS", "PRECISIONS", "PREC_FP64", "PREC_DF64",
+__all__ = ["Solver", "FvError", "load_library", "probe_alu_rates", "LIB_PATH", "EXPORTS", "PRECISIONS", "PREC_FP64", "PREC_DF64",
            "PREC_FP32FLUX", "FV_OK", "FV_ERR_INVALID_ARG", "FV_ERR_CUDA", "FV_ERR_OOM", "FV_ERR_NONFINITE",
            "FV_ERR_TIMEOUT", "FV_ERR_UNSUPPORTED"]

@@ -23,7 +23,8 @@ EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error
            "fv_field_size", "fv_cell_count", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
            "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
            "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
-           "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged")
+           "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged", "fv_graph_count",
+           "fv_probe_alu_rates", "fv_set_halo", "fv_halo_size", "fv_halo_pack", "fv_halo_unpack")
 
 
 class FvError(RuntimeError):
@@ -103,6 +104,18 @@ def load_library(path: Optional[str] = None):
     L.fv_stage_state.argtypes = [vp, vp, vp]
     L.fv_set_state_staged.argtypes = [vp, vp]
     L.fv_monitor_norms.argtypes = [vp, vp, vp]
+    L.fv_graph_count.argtypes = [vp]
+    L.fv_graph_count.restype = i32
+    L.fv_probe_alu_rates.argtypes = [vp, i32, vp]
+    L.fv_probe_alu_rates.restype = i32
+    L.fv_set_halo.argtypes = [vp, ctypes.POINTER(fv_connection), i32, ctypes.POINTER(fv_connection), i32]
+    L.fv_set_halo.restype = i32
+    L.fv_halo_size.argtypes = [vp, i32]
+    L.fv_halo_size.restype = i64
+    L.fv_halo_pack.argtypes = [vp, i32, vp, vp]
+    L.fv_halo_pack.restype = i32
+    L.fv_halo_unpack.argtypes = [vp, i32, vp, vp]
+    L.fv_halo_unpack.restype = i32
     for f in ("fv_create_blocks", "fv_destroy", "fv_set_state", "fv_set_buffer", "fv_get_state", "fv_set_source",
               "fv_exchange_ghosts", "fv_residual", "fv_rk_stage", "fv_rk_step", "fv_residual_norms",
               "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
@@ -132,6 +145,36 @@ def _stream(stream) -> int:
     return 0
 
 
+PROBE_RATES = ("fp64_fma", "fp64_add", "fp64_mul", "fp64_rcp", "fp64_sqrt", "fp32_fma",
+               "df64_add", "df64_mul", "df64_div", "df64_sqrt", "df64_abs")
+
+
+def probe_alu_rates(stream=None) -> dict:
+    """Measured operations/s of the arithmetic the stage kernel's forms use
+    (fv_probe_alu_rates) on the current device."""
+    L = load_library()
+    out = np.zeros(len(PROBE_RATES))
+    rc = L.fv_probe_alu_rates(out.ctypes.data, len(PROBE_RATES), _stream(stream))
+    if rc != FV_OK:
+        raise FvError(rc, "fv_probe_alu_rates failed")
+    return dict(zip(PROBE_RATES, out.tolist()))
+
+
+def _conn_table(conns: Sequence):
+    """ctypes array of fv_connection from objects with the fields of
+    cases.Connection (at least one entry, so that the pointer is valid)."""
+    cs = (fv_connection * max(1, len(conns)))()
+    for n, c in enumerate(conns):
+        e = cs[n]
+        e.dst_block, e.dst_face = int(c.dst_block), int(c.dst_face)
+        e.dst_lo[0], e.dst_lo[1] = map(int, c.dst_lo)
+        e.dst_hi[0], e.dst_hi[1] = map(int, c.dst_hi)
+        e.src_block, e.src_face = int(c.src_block), int(c.src_face)
+        e.src_lo[0], e.src_lo[1] = map(int, c.src_lo)
+        e.transform[0], e.transform[1] = map(int, c.transform)
+    return cs
+
+
 class Solver:
     """One fvgb handle: blocks, connections and method parameters on the
     current CUDA device.  Method names follow the C ABI."""
@@ -155,15 +198,7 @@ class Solver:
             for x in range(3):
                 d.x0[x] = float(b.x0[x])
                 d.h[x] = float(b.h[x])
-        cs = (fv_connection * max(1, len(conns)))()
-        for n, c in enumerate(conns):
-            e = cs[n]
-            e.dst_block, e.dst_face = int(c.dst_block), int(c.dst_face)
-            e.dst_lo[0], e.dst_lo[1] = map(int, c.dst_lo)
-            e.dst_hi[0], e.dst_hi[1] = map(int, c.dst_hi)
-            e.src_block, e.src_face = int(c.src_block), int(c.src_face)
-            e.src_lo[0], e.src_lo[1] = map(int, c.src_lo)
-            e.transform[0], e.transform[1] = map(int, c.transform)
+        cs = _conn_table(conns)
         cfg = fv_config()
         L.fv_config_default(ctypes.byref(cfg))
         cfg.gamma = params.get("gamma", 1.4)
@@ -294,6 +329,27 @@ class Solver:
 
     def rk_step(self, dt: float, use_graph: bool = True, stream=None):
         self._check(self._L.fv_rk_step(self._h, float(dt), int(bool(use_graph)), _stream(stream)))
+
+    # -- cross-device halo (fv_set_halo) ---------------------------------------
+    def set_halo(self, send: Sequence, recv: Sequence) -> None:
+        """Send and receive slab tables (connections with the local side's
+        block index in this handle's numbering; see fv_set_halo)."""
+        self._check(self._L.fv_set_halo(self._h, _conn_table(send), len(send), _conn_table(recv), len(recv)))
+
+    def halo_size(self, recv: bool) -> int:
+        return int(self._L.fv_halo_size(self._h, 1 if recv else 0))
+
+    def halo_pack(self, buffer: int, send, stream=None):
+        self._check(self._L.fv_halo_pack(self._h, int(buffer), _ptr(send) if send is not None else None,
+                                         _stream(stream)))
+
+    def halo_unpack(self, buffer: int, recv, stream=None):
+        self._check(self._L.fv_halo_unpack(self._h, int(buffer), _ptr(recv) if recv is not None else None,
+                                           _stream(stream)))
+
+    def graph_count(self) -> int:
+        """RK-step graphs held (one per stream stepped on with use_graph)."""
+        return int(self._L.fv_graph_count(self._h))
 
     def residual_norms(self, buffer: int = 0, stream=None):
         out = np.zeros(10)

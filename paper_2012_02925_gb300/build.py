@@ -16,7 +16,7 @@ STAGE_VARIANTS = ["fp64", "fp64_bc", "fp64_visc", "fp64_visc_bc"] + [
     form + fast + visc + bc for form in ("df64", "fp32") for fast in ("", "_fast") for visc in ("", "_visc")
     for bc in ("", "_bc")]
 SOURCES = ["fv_stage_%s.cu" % v for v in STAGE_VARIANTS] + [
-    "fv_api.cu", "fv_noalloc.cu", "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu"]
+    "fv_api.cu", "fv_noalloc.cu", "fv_probe.cu", "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu"]
 HEADERS = ["fv_arith.cuh", "fv_face.cuh", "fv_stage.cuh", "fv_viscface.cuh", "fv_internal.h", "fv_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

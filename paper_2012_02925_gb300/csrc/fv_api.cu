@@ -17,6 +17,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// streams whose RK-step graph fv_rk_step keeps at one time
+constexpr int FV_MAX_GRAPHS = 8;
+
 }  // namespace
 
 struct fv_ctx {
@@ -50,6 +53,12 @@ struct fv_ctx {
   double* adj_lamg = nullptr;       // adjoint: ghosted cotangent of Q^(m-1)
   double* adj_qx = nullptr;         // adjoint: X(Q^(m-1)), the exchanged stage input
   std::vector<FvConnDev> hconns;
+  // cross-device halo slabs (fv_set_halo): send = this device's donor side,
+  // recv = this device's ghost side; item offsets count slab items
+  FvConnDev* d_hsend = nullptr;
+  FvConnDev* d_hrecv = nullptr;
+  int nhsend = 0, nhrecv = 0;
+  long long hsend_items = 0, hrecv_items = 0;
   std::vector<fv_bc_patch> bcs;     // physical boundary patches as set
   FvBcDev* d_bcs = nullptr;
   int nbc = 0;
@@ -75,7 +84,18 @@ struct fv_ctx {
   double* mon_partials = nullptr;
   double* mon_norm = nullptr;
   int device = 0, nsm = 0;
-  std::map<std::pair<double, cudaStream_t>, cudaGraphExec_t> graphs;
+  // fv_rk_step's graphs, one per stream, each with its own device slot for
+  // dt (set by a one-thread kernel on that stream when dt changes, so that a
+  // new dt neither re-captures nor instantiates anything); at most
+  // FV_MAX_GRAPHS streams, the least recently used evicted
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    double* dt_dev = nullptr;
+    double dt = 0.0;
+    unsigned long long used = 0;
+  };
+  std::map<cudaStream_t, StepGraph> graphs;
+  unsigned long long graph_clock = 0;
   std::string err;
 };
 
@@ -185,6 +205,9 @@ __global__ void volume_kernel(const double* nodes, int ni, int nj, int nk, doubl
   }
 }
 
+// one value into device memory, in stream order (a replayed graph's dt)
+__global__ void set_scalar_kernel(double* p, double v) { *p = v; }
+
 __global__ void fill_kernel(double* p, long long n, double v) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) p[x] = v;
 }
@@ -208,10 +231,20 @@ __global__ void split_kernel(const double* in, float2* out, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// ghost exchange: work item = (connection, tangential a, b, depth d)
+// ghost exchange: work item = (connection, tangential a, b, depth d), a
+// fastest.  XCH_COPY: dst ghost <- src donor, both blocks on this device
+// (Section 2, Section 4).  Across devices (Section 7.2 V1, pack/unpack) the
+// same item order splits into halves: XCH_PACK writes the donor cells of
+// this device's src blocks into a contiguous slab buffer, XCH_UNPACK writes
+// a received slab buffer into this device's dst ghosts.  Connection c's slab
+// occupies buf[5*item_off, 5*(item_off + n_c)), variable-major (n_c = 2 L0 L1
+// items: the 5 values of item x at x, x + n_c, ...).
 // ---------------------------------------------------------------------------
+enum { XCH_COPY = 0, XCH_PACK = 1, XCH_UNPACK = 2 };
+
+template <int MODE>
 __global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvConnDev* __restrict__ conns, int nconn,
-                                long long nitems, double* q) {
+                                long long nitems, double* q, double* buf) {
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
        it += (long long)gridDim.x * blockDim.x) {
     int lo = 0, hi = nconn - 1;
@@ -221,31 +254,48 @@ __global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvC
     }
     const FvConnDev c = conns[lo];
     long long local = it - c.item_off;
+    const long long li = local;
     const int a = (int)(local % c.L0);
     local /= c.L0;
     const int b = (int)(local % c.L1);
     const int d = (int)(local / c.L1) + 1;
-    const FvBlockDev& D = blocks[c.dst_block];
-    const FvBlockDev& S = blocks[c.src_block];
-    const int da = c.dst_face >> 1, sa = c.src_face >> 1;
-    const int dext[3] = {D.ni, D.nj, D.nk}, sext[3] = {S.ni, S.nj, S.nk};
-    int dc[3], sc[3];
-    const int dt0 = da == 0 ? 1 : 0, dt1 = da == 2 ? 1 : 2;
-    const int st0 = sa == 0 ? 1 : 0, st1 = sa == 2 ? 1 : 2;
-    dc[dt0] = c.dlo0 + a;
-    dc[dt1] = c.dlo1 + b;
-    dc[da] = (c.dst_face & 1) ? dext[da] - 1 + d : -d;
-    int st[2] = {c.slo0, c.slo1};
-    const int u0 = (c.t0 < 0 ? -c.t0 : c.t0) - 1, u1 = (c.t1 < 0 ? -c.t1 : c.t1) - 1;
-    st[u0] += c.t0 > 0 ? a : -a;
-    st[u1] += c.t1 > 0 ? b : -b;
-    sc[st0] = st[0];
-    sc[st1] = st[1];
-    sc[sa] = (c.src_face & 1) ? sext[sa] - d : d - 1;
-    const long long di = D.qoff + (long long)(dc[2] + 2) * D.kstride + (long long)(dc[1] + 2) * D.jstride + (dc[0] + 2);
-    const long long si = S.qoff + (long long)(sc[2] + 2) * S.kstride + (long long)(sc[1] + 2) * S.jstride + (sc[0] + 2);
+    long long di = 0, si = 0, dplane = 0, splane = 0;
+    if (MODE != XCH_PACK) {
+      const FvBlockDev& D = blocks[c.dst_block];
+      const int da = c.dst_face >> 1;
+      const int dext[3] = {D.ni, D.nj, D.nk};
+      int dc[3];
+      const int dt0 = da == 0 ? 1 : 0, dt1 = da == 2 ? 1 : 2;
+      dc[dt0] = c.dlo0 + a;
+      dc[dt1] = c.dlo1 + b;
+      dc[da] = (c.dst_face & 1) ? dext[da] - 1 + d : -d;
+      di = D.qoff + (long long)(dc[2] + 2) * D.kstride + (long long)(dc[1] + 2) * D.jstride + (dc[0] + 2);
+      dplane = D.plane;
+    }
+    if (MODE != XCH_UNPACK) {
+      const FvBlockDev& S = blocks[c.src_block];
+      const int sa = c.src_face >> 1;
+      const int sext[3] = {S.ni, S.nj, S.nk};
+      int sc[3];
+      const int st0 = sa == 0 ? 1 : 0, st1 = sa == 2 ? 1 : 2;
+      int st[2] = {c.slo0, c.slo1};
+      const int u0 = (c.t0 < 0 ? -c.t0 : c.t0) - 1, u1 = (c.t1 < 0 ? -c.t1 : c.t1) - 1;
+      st[u0] += c.t0 > 0 ? a : -a;
+      st[u1] += c.t1 > 0 ? b : -b;
+      sc[st0] = st[0];
+      sc[st1] = st[1];
+      sc[sa] = (c.src_face & 1) ? sext[sa] - d : d - 1;
+      si = S.qoff + (long long)(sc[2] + 2) * S.kstride + (long long)(sc[1] + 2) * S.jstride + (sc[0] + 2);
+      splane = S.plane;
+    }
+    const long long nc = 2LL * c.L0 * c.L1;
+    double* slab = buf + 5 * c.item_off + li;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) q[di + v * D.plane] = q[si + v * S.plane];
+    for (int v = 0; v < 5; ++v) {
+      if (MODE == XCH_COPY) q[di + v * dplane] = q[si + v * splane];
+      if (MODE == XCH_PACK) slab[v * nc] = q[si + v * splane];
+      if (MODE == XCH_UNPACK) q[di + v * dplane] = slab[v * nc];
+    }
   }
 }
 
@@ -527,6 +577,16 @@ int grid_for(long long n, int threads, int nsm) {
 
 fv_ctx* H(fv_handle h) { return reinterpret_cast<fv_ctx*>(h); }
 
+// destroy the cached RK-step graphs (one still running is freed when it
+// completes; cudaFree waits for the device, so no dt slot is freed in use)
+void drop_graphs(fv_ctx* h) {
+  for (auto& g : h->graphs) {
+    cudaGraphExecDestroy(g.second.exec);
+    cudaFree(g.second.dt_dev);
+  }
+  h->graphs.clear();
+}
+
 // laminar viscous terms of state q: face variables, then the face fluxes of
 // every direction (they feed the fused kernel through FvStageArgs::fv)
 int do_visc(fv_ctx* h, const double* q, cudaStream_t s) {
@@ -638,8 +698,8 @@ int stage_out(const fv_ctx* h, int m) {
 int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
   const int threads = 256;
   if (h->conn_items) {
-    exchange_kernel<<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(h->d_blocks, h->d_conns, h->nconn,
-                                                                              h->conn_items, q);
+    exchange_kernel<XCH_COPY><<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(
+        h->d_blocks, h->d_conns, h->nconn, h->conn_items, q, nullptr);
     CK(h, cudaGetLastError());
   }
   if (h->bc_items) {
@@ -674,7 +734,9 @@ int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
   return FV_OK;
 }
 
-int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
+// dt_dev: null, or device memory holding dt (a captured graph reads it at
+// replay; alpha_m * dt is then formed by the kernel, the same binary64 product)
+int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s, const double* dt_dev = nullptr) {
   const int bi = stage_in(h, m), bo = stage_out(h, m);
   int rc = do_exchange(h, h->buf[bi], s);
   if (rc) return rc;
@@ -684,6 +746,8 @@ int do_stage(fv_ctx* h, int m, double dt, cudaStream_t s) {
   a.q0 = h->buf[0];
   a.qout = h->buf[bo];
   a.alpha_dt = h->cfg.alpha[m - 1] * dt;
+  a.alpha = h->cfg.alpha[m - 1];
+  a.dt_dev = dt_dev;
   const bool mon = m == 1 && h->monitor;
   if (mon) a.rmon = h->rmon;
   rc = launch_stage(h, a, s);
@@ -1251,7 +1315,7 @@ int fv_destroy(fv_handle hh) {
   if (!hh) return FV_ERR_INVALID_ARG;
   fv_ctx* h = H(hh);
   cudaDeviceSynchronize();
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+  drop_graphs(h);
   for (int x = 0; x < 3; ++x) cudaFree(h->buf[x]);
   for (int d = 0; d < 3; ++d) cudaFree(h->metric[d]);
   cudaFree(h->d_blocks); cudaFree(h->d_tiles); cudaFree(h->d_conns); cudaFree(h->d_tile_counter);
@@ -1259,6 +1323,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm); cudaFree(h->stage_buf);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
+  cudaFree(h->d_hsend); cudaFree(h->d_hrecv);
   cudaFree(h->geo_t);
   cudaFree(h->geo); cudaFree(h->d_vtiles); cudaFree(h->d_edges);
   cudaFree(h->rmon); cudaFree(h->mon_partials); cudaFree(h->mon_norm);
@@ -1327,8 +1392,7 @@ int fv_set_source(fv_handle hh, const double* src, void* stream) {
   if (!hh) return FV_ERR_INVALID_ARG;
   fv_ctx* h = H(hh);
   cudaStream_t s = (cudaStream_t)stream;
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
-  h->graphs.clear();
+  drop_graphs(h);
   if (!src) {
     if (h->srcvol || h->srcvol2) {
       CK(h, cudaStreamSynchronize(s));
@@ -1434,8 +1498,7 @@ int fv_set_boundaries(fv_handle hh, const fv_bc_patch* patches, int n) {
   }
   CK(h, cudaDeviceSynchronize());
   // drop the old set first (a failed allocation below leaves no boundaries)
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
-  h->graphs.clear();
+  drop_graphs(h);
   h->nbc = 0;
   h->bc_items = 0;
   h->bcs.clear();
@@ -1500,27 +1563,50 @@ int fv_rk_step(fv_handle hh, double dt, int use_graph, void* stream) {
     }
     return FV_OK;
   }
-  auto key = std::make_pair(dt, s);
-  auto it = h->graphs.find(key);
+  auto it = h->graphs.find(s);
   if (it == h->graphs.end()) {
+    if ((int)h->graphs.size() >= FV_MAX_GRAPHS) {
+      // evict the least recently used stream's graph; the device is idle
+      // first, so neither it nor its dt slot is in use
+      auto lru = h->graphs.begin();
+      for (auto g = h->graphs.begin(); g != h->graphs.end(); ++g)
+        if (g->second.used < lru->second.used) lru = g;
+      CK(h, cudaDeviceSynchronize());
+      cudaGraphExecDestroy(lru->second.exec);
+      cudaFree(lru->second.dt_dev);
+      h->graphs.erase(lru);
+    }
+    fv_ctx::StepGraph sg;
+    CK(h, cudaMalloc(&sg.dt_dev, sizeof(double)));
     cudaStream_t cs;
-    CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cudaFree(sg.dt_dev); return cuda_fail(h, e, "cudaStreamCreateWithFlags"); }
     cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(h, e, "cudaStreamBeginCapture"); }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaFree(sg.dt_dev); return cuda_fail(h, e, "cudaStreamBeginCapture"); }
     int rc = FV_OK;
-    for (int m = 1; m <= h->cfg.n_stages && rc == FV_OK; ++m) rc = do_stage(h, m, dt, cs);
+    for (int m = 1; m <= h->cfg.n_stages && rc == FV_OK; ++m) rc = do_stage(h, m, dt, cs, sg.dt_dev);
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
-    if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    cudaGraphExec_t ex;
-    e = cudaGraphInstantiate(&ex, g, 0);
+    if (rc || e != cudaSuccess) {
+      cudaFree(sg.dt_dev);
+      return rc ? rc : cuda_fail(h, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&sg.exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-    it = h->graphs.emplace(key, ex).first;
+    if (e != cudaSuccess) { cudaFree(sg.dt_dev); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    // dt differs from any value the slot holds: written below
+    sg.dt = std::nan("");
+    it = h->graphs.emplace(s, sg).first;
   }
-  CK(h, cudaGraphLaunch(it->second, s));
+  fv_ctx::StepGraph& sg = it->second;
+  if (!(sg.dt == dt)) {
+    set_scalar_kernel<<<1, 1, 0, s>>>(sg.dt_dev, dt);
+    CK(h, cudaGetLastError());
+    sg.dt = dt;
+  }
+  sg.used = ++h->graph_clock;
+  CK(h, cudaGraphLaunch(sg.exec, s));
   return FV_OK;
 }
 
@@ -1566,8 +1652,7 @@ int fv_set_monitor(fv_handle hh, int on) {
   }
   h->monitor = on ? 1 : 0;
   h->mon_ran = false;
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
-  h->graphs.clear();
+  drop_graphs(h);
   return FV_OK;
 }
 
@@ -1623,10 +1708,138 @@ int fv_autotune(fv_handle hh, double dt, int reps, void* stream) {
   h->cfg.kchunk = best_kc;
   choose_launch(h);
   int rc = build_tiles(h);
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
-  h->graphs.clear();
+  drop_graphs(h);
   CK(h, cudaGetLastError());
   return rc;
+}
+
+int fv_set_halo(fv_handle hh, const fv_connection* send, int nsend, const fv_connection* recv, int nrecv) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (nsend < 0 || nrecv < 0 || (nsend && !send) || (nrecv && !recv))
+    return fail(h, FV_ERR_INVALID_ARG, "halo: negative count or NULL table");
+  const int nb = (int)h->hb.size();
+  auto ext = [&](int blk, int axis) { const FvBlockDev& B = h->hb[blk]; return axis == 0 ? B.ni : (axis == 1 ? B.nj : B.nk); };
+  // ghost cells already written by this device's own connections
+  std::vector<std::vector<std::vector<char>>> used(nb, std::vector<std::vector<char>>(6));
+  auto mark = [&](const fv_connection& x, const std::string& tag) -> int {
+    const int da = x.dst_face / 2;
+    const int t0 = da == 0 ? 1 : 0, t1 = da == 2 ? 1 : 2;
+    auto& u = used[x.dst_block][x.dst_face];
+    if (u.empty()) u.assign((size_t)ext(x.dst_block, t0) * ext(x.dst_block, t1), 0);
+    for (int b = x.dst_lo[1]; b < x.dst_hi[1]; ++b)
+      for (int a = x.dst_lo[0]; a < x.dst_hi[0]; ++a) {
+        char& f = u[(size_t)b * ext(x.dst_block, t0) + a];
+        if (f) return fail(h, FV_ERR_INVALID_ARG, tag + "dst ghost cells already filled by another connection");
+        f = 1;
+      }
+    return FV_OK;
+  };
+  for (const fv_connection& x : h->conns) mark(x, "");
+  const int maxface = h->cfg.dim == 2 ? 3 : 5;
+  for (int side = 0; side < 2; ++side) {
+    const fv_connection* tab = side ? recv : send;
+    const int n = side ? nrecv : nsend;
+    for (int c = 0; c < n; ++c) {
+      const fv_connection& x = tab[c];
+      const std::string tag = std::string(side ? "halo recv " : "halo send ") + std::to_string(c) + ": ";
+      const int L0 = x.dst_hi[0] - x.dst_lo[0], L1 = x.dst_hi[1] - x.dst_lo[1];
+      if (L0 <= 0 || L1 <= 0) return fail(h, FV_ERR_INVALID_ARG, tag + "empty patch");
+      if (side) {
+        if (x.dst_block < 0 || x.dst_block >= nb || x.dst_face < 0 || x.dst_face > maxface)
+          return fail(h, FV_ERR_INVALID_ARG, tag + "dst block or face out of range");
+        const int da = x.dst_face / 2;
+        const int t0 = da == 0 ? 1 : 0, t1 = da == 2 ? 1 : 2;
+        if (x.dst_lo[0] < 0 || x.dst_lo[1] < 0 || x.dst_hi[0] > ext(x.dst_block, t0) || x.dst_hi[1] > ext(x.dst_block, t1))
+          return fail(h, FV_ERR_INVALID_ARG, tag + "dst patch outside the face");
+        int rc = mark(x, tag);
+        if (rc) return rc;
+      } else {
+        if (x.src_block < 0 || x.src_block >= nb || x.src_face < 0 || x.src_face > maxface)
+          return fail(h, FV_ERR_INVALID_ARG, tag + "src block or face out of range");
+        const int t0 = x.transform[0], t1 = x.transform[1];
+        if (!(std::abs(t0) == 1 || std::abs(t0) == 2) || !(std::abs(t1) == 1 || std::abs(t1) == 2) ||
+            std::abs(t0) == std::abs(t1))
+          return fail(h, FV_ERR_INVALID_ARG, tag + "transform must be a signed permutation of (1,2)");
+        const int sa = x.src_face / 2;
+        if (ext(x.src_block, sa) < FV_GHOST) return fail(h, FV_ERR_INVALID_ARG, tag + "src block thinner than the ghost depth");
+        const int st[2] = {sa == 0 ? 1 : 0, sa == 2 ? 1 : 2};
+        for (int t = 0; t < 2; ++t) {
+          const int T = t == 0 ? t0 : t1;
+          const int u = std::abs(T) - 1;
+          const int L = t == 0 ? L0 : L1;
+          const int first = x.src_lo[u], last = x.src_lo[u] + (T > 0 ? L - 1 : -(L - 1));
+          if (std::min(first, last) < 0 || std::max(first, last) >= ext(x.src_block, st[u]))
+            return fail(h, FV_ERR_INVALID_ARG, tag + "src patch outside the src face");
+        }
+      }
+    }
+  }
+  CK(h, cudaDeviceSynchronize());
+  cudaFree(h->d_hsend); cudaFree(h->d_hrecv);
+  h->d_hsend = h->d_hrecv = nullptr;
+  h->nhsend = h->nhrecv = 0;
+  h->hsend_items = h->hrecv_items = 0;
+  for (int side = 0; side < 2; ++side) {
+    const fv_connection* tab = side ? recv : send;
+    const int n = side ? nrecv : nsend;
+    if (!n) continue;
+    std::vector<FvConnDev> cd(n);
+    long long items = 0;
+    for (int c = 0; c < n; ++c) {
+      const fv_connection& x = tab[c];
+      FvConnDev& y = cd[c];
+      y.dst_block = side ? x.dst_block : -1; y.dst_face = x.dst_face;
+      y.dlo0 = x.dst_lo[0]; y.dlo1 = x.dst_lo[1];
+      y.L0 = x.dst_hi[0] - x.dst_lo[0]; y.L1 = x.dst_hi[1] - x.dst_lo[1];
+      y.src_block = side ? -1 : x.src_block; y.src_face = x.src_face;
+      y.slo0 = x.src_lo[0]; y.slo1 = x.src_lo[1];
+      y.t0 = x.transform[0]; y.t1 = x.transform[1];
+      y.item_off = items;
+      items += 2LL * y.L0 * y.L1;
+    }
+    FvConnDev** dst = side ? &h->d_hrecv : &h->d_hsend;
+    CK(h, cudaMalloc(dst, sizeof(FvConnDev) * n));
+    CK(h, cudaMemcpy(*dst, cd.data(), sizeof(FvConnDev) * n, cudaMemcpyHostToDevice));
+    (side ? h->nhrecv : h->nhsend) = n;
+    (side ? h->hrecv_items : h->hsend_items) = items;
+  }
+  return FV_OK;
+}
+
+int64_t fv_halo_size(fv_handle hh, int recv) {
+  if (!hh) return -1;
+  const fv_ctx* h = H(hh);
+  return 5 * (recv ? h->hrecv_items : h->hsend_items);
+}
+
+int fv_halo_pack(fv_handle hh, int buffer, double* send_dev, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  if (!h->hsend_items) return FV_OK;
+  if (!send_dev) return fail(h, FV_ERR_INVALID_ARG, "send_dev is NULL");
+  exchange_kernel<XCH_PACK><<<grid_for(h->hsend_items, 256, h->nsm), 256, 0, (cudaStream_t)stream>>>(
+      h->d_blocks, h->d_hsend, h->nhsend, h->hsend_items, h->buf[buffer], send_dev);
+  CK(h, cudaGetLastError());
+  return FV_OK;
+}
+
+int fv_halo_unpack(fv_handle hh, int buffer, const double* recv_dev, void* stream) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
+  if (!h->hrecv_items) return FV_OK;
+  if (!recv_dev) return fail(h, FV_ERR_INVALID_ARG, "recv_dev is NULL");
+  exchange_kernel<XCH_UNPACK><<<grid_for(h->hrecv_items, 256, h->nsm), 256, 0, (cudaStream_t)stream>>>(
+      h->d_blocks, h->d_hrecv, h->nhrecv, h->hrecv_items, h->buf[buffer], const_cast<double*>(recv_dev));
+  CK(h, cudaGetLastError());
+  return FV_OK;
+}
+
+int fv_graph_count(fv_handle hh) {
+  if (!hh) return -1;
+  return (int)H(hh)->graphs.size();
 }
 
 int fv_get_launch(fv_handle hh, int* out4) {

@@ -34,7 +34,10 @@ std::mutex g_scratch_mu;
 
 // Device address of g_norm_scratch on the current device.  In host code the
 // symbol name is only a host-side stand-in, so the address must be queried
-// once per device, with that device current.
+// once per device, with that device current.  The address is kept for the
+// life of the process: a cudaDeviceReset() of a device unloads the module
+// and invalidates it, so a process that resets a device must not call this
+// entry point on that device afterwards.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FV_ERR_CUDA;
@@ -112,9 +115,16 @@ extern "C" int fv_field_norms_noalloc(const double* field_dev, int64_t n, double
   double* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc != FV_OK) return rc;
-  const int parts = (int)((n + FV_NOALLOC_CHUNK - 1) / FV_NOALLOC_CHUNK);
+  int parts = (int)((n + FV_NOALLOC_CHUNK - 1) / FV_NOALLOC_CHUNK);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  chunk_norms<<<parts, kThreads, 0, s>>>(field_dev, n, scratch);
-  finish_norms<<<1, 32, 0, s>>>(scratch, parts, n, out_dev);
-  return cudaGetLastError() == cudaSuccess ? FV_OK : FV_ERR_CUDA;
+  // cudaLaunchKernel reports the status of this launch itself, so an error
+  // another caller left in the thread's last-error slot is neither reported
+  // here nor cleared
+  long long nn = n;
+  void* a1[] = {&field_dev, &nn, &scratch};
+  if (cudaLaunchKernel((const void*)chunk_norms, dim3(parts), dim3(kThreads), a1, 0, s) != cudaSuccess)
+    return FV_ERR_CUDA;
+  void* a2[] = {&scratch, &parts, &nn, &out_dev};
+  if (cudaLaunchKernel((const void*)finish_norms, dim3(1), dim3(32), a2, 0, s) != cudaSuccess) return FV_ERR_CUDA;
+  return FV_OK;
 }
