@@ -2,7 +2,11 @@
 benchmark uses (autotuned tile shape and k-chunk).
 
 * 128^3 curvilinear manufactured-solution block: every cell of one residual
-  (all three forms) and of one full RK step (FP64-accurate forms).
+  (all three forms; the binary32-flux form also against a bound on its plain
+  error max|R - R_ref| / max|R_ref|), of one full RK step (FP64-accurate
+  forms) and of the state after 100 stages (25 graph-replayed RK steps):
+  binary64 and double-float within 1e-10, the binary32-flux form's drift
+  within a stated bound.
 * 64 seeded uneven blocks (10.9 M cells) with random connections: every cell
   of one residual after the exchange and of one RK step.
 * 512 x 512 x 256 periodic block (67 M cells): the residual on seeded
@@ -19,7 +23,7 @@ import pytest
 
 import cases
 import oracle
-from test_gpu_parity import TOL_RES, TOL_RUN, rel_err_fields, rel_err_states, solver
+from test_gpu_parity import TOL_RES, TOL_RES_NS, TOL_RUN, field_errors, log_errors, rel_err_fields, rel_err_states, solver
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,15 +51,48 @@ def tuned(pb, prec, reps=2):
     return s
 
 
+# The binary32-flux form at the benchmark size: R cancels to the truncation
+# error (max|R| is 1e-5 to 5e-5 of the terms it sums at 128^3), so the
+# form's ~1e-7 rounding of the terms is a visible fraction of R itself.
+# Bounds on the plain relative error of one residual and on the drift of the
+# state over 100 stages, both per variable against the oracle (measured on a
+# GB300: at most 4.8e-2 and 4.6e-7).
+FP32_PLAIN_RES = 0.1
+FP32_DRIFT_100 = 2e-6
+
+
+@pytest.fixture(scope="module")
+def mms128_oracle(mms128):
+    o = oracle.Oracle(mms128)
+    return o, o.residual(mms128.q.copy()), o.run(mms128.q.copy(), mms128.dt, 100)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "df64", "fp32flux"])
-def test_mms128_every_cell_residual(mms128, prec):
+def test_mms128_every_cell_residual(mms128, mms128_oracle, prec):
     pb = mms128
-    o = oracle.Oracle(pb)
-    ref = o.residual(pb.q.copy())
+    o, ref, _ = mms128_oracle
     s = tuned(pb, prec)
     r = s.residual(0).cpu().numpy()
     s.close()
+    term, plain = field_errors(r, ref, o)
     assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
+    if prec == "fp32flux":
+        assert max(plain) <= FP32_PLAIN_RES, plain
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32flux"])
+def test_mms128_100_stages(mms128, mms128_oracle, prec):
+    """The benchmark's launch (autotuned shape and k-chunk, graph replay with
+    its dynamic tile counter reset between launches) over 100 stages."""
+    pb = mms128
+    o, _, ref = mms128_oracle
+    s = tuned(pb, prec)
+    for _ in range(25):
+        s.rk_step(pb.dt, use_graph=True)
+    got = s.get_state(0).cpu().numpy()
+    s.close()
+    err = rel_err_states(got, ref, o)
+    assert err <= (TOL_RUN[prec] if prec != "fp32flux" else FP32_DRIFT_100), err
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
@@ -178,4 +215,4 @@ def test_boundary_and_laminar_workloads_every_cell(bench_workloads, name, prec):
     s.exchange_ghosts(0)
     r = s.residual(0).cpu().numpy()
     s.close()
-    assert rel_err_fields(r, ref, o, q) <= TOL_RES[prec]
+    assert rel_err_fields(r, ref, o, q) <= (TOL_RES_NS if pb.params.get("visc", 0) else TOL_RES)[prec]

@@ -14,7 +14,7 @@ import pytest
 
 import cases
 import oracle
-from test_gpu_parity import TOL_RES, flux_scale, solver
+from test_gpu_parity import TOL_RES_NS as TOL_RES, flux_scale, solver
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

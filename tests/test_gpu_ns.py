@@ -12,7 +12,7 @@ import pytest
 
 import cases
 import oracle
-from test_gpu_parity import TOL_RES, rel_err_fields, rel_err_states, solver
+from test_gpu_parity import TOL_RES_NS as TOL_RES, rel_err_fields, rel_err_states, solver
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu

@@ -1,13 +1,24 @@
 """CUDA library vs CPU oracle, element by element, through the C ABI.
 
-Tolerances (relative L-infinity per variable, normalised by the field's
-maximum magnitude; paper Section 8 compares parallel and serial solutions the
-same way at 1e-12):
+Tolerances (relative L-infinity per variable; paper Section 8 compares
+parallel and serial solutions the same way at 1e-12).  States are normalised
+by the field's largest magnitude.  Residuals are normalised by the larger of
+max|R| and the magnitude of the terms R sums (the largest physical normal
+flux times the largest face area): on a smooth field R cancels down to the
+truncation error, and rounding in any evaluation order is relative to the
+terms, not to R.
   FP64 and DF64 forms: 1e-12 on one residual, 1e-10 after 100 RK stages;
-  FP32-flux form: 1e-5 on one residual (its drift over stages is reported by
-  the benchmark).
+  FP32-flux form: 3e-6 on one inviscid residual (1e-5 with the laminar
+  terms, whose gradients amplify the primitives' rounding), and at the
+  benchmark size also a bound on the plain error max|R - R_ref| / max|R_ref|
+  and on its drift over 100 stages (test_gpu_fullsize.py).
+Setting FVGB_PARITY_LOG=<file> makes the tests append every measured error
+(both normalisations, per variable) to that file as JSON lines.
 Sizes span several tiles with ragged tails in i, j and k.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -17,8 +28,22 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL_RES = {"fp64": 1e-12, "df64": 1e-12, "fp32flux": 1e-5}
+# binary32 flux form: unit roundoff 6e-8 grown over the ~25 dependent
+# operations of a face (1.7e-6 of the term scale measured at worst, on the
+# 64-block batch)
+TOL_RES = {"fp64": 1e-12, "df64": 1e-12, "fp32flux": 3e-6}
+# laminar Navier-Stokes terms (binary32 form: 5.3e-6 measured on the 128^3
+# manufactured block, see the tolerance notes of the viscous kernels)
+TOL_RES_NS = {"fp64": 1e-12, "df64": 1e-12, "fp32flux": 1e-5}
 TOL_RUN = {"fp64": 1e-10, "df64": 1e-10}
+
+
+def log_errors(test, **kw):
+    """Append measured errors to $FVGB_PARITY_LOG (JSON lines), if set."""
+    path = os.environ.get("FVGB_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(test=test, **kw)) + "\n")
 
 
 def solver(pb, precision, **kw):
@@ -52,19 +77,31 @@ def flux_scale(o, q):
     return scales * smax
 
 
+def _fields(a, o):
+    return np.concatenate([a[o.roffs[n]:o.roffs[n + 1]].reshape(5, -1) for n in range(len(o.blocks))], axis=1)
+
+
+def field_errors(a, b, o, q=None):
+    """Per variable, over all blocks' packed interior fields:
+    (max|a-b| / max(max|b|, term scale), max|a-b| / max|b|)."""
+    A, B = _fields(a, o), _fields(b, o)
+    fs = flux_scale(o, q if q is not None else o.pb.q)
+    term, plain = [], []
+    for v in range(5):
+        d = float(np.abs(A[v] - B[v]).max())
+        m = float(np.abs(B[v]).max())
+        scale = max(m, fs[v])
+        term.append(d / scale if scale > 0 else 0.0)
+        plain.append(d / m if m > 0 else (0.0 if d == 0 else float("inf")))
+    return term, plain
+
+
 def rel_err_fields(a, b, o, q=None):
     """max over variables of max|a-b| / max(max|b|, term scale) over all
-    blocks' packed interior fields."""
-    A = np.concatenate([a[o.roffs[n]:o.roffs[n + 1]].reshape(5, -1) for n in range(len(o.blocks))], axis=1)
-    B = np.concatenate([b[o.roffs[n]:o.roffs[n + 1]].reshape(5, -1) for n in range(len(o.blocks))], axis=1)
-    fs = flux_scale(o, q if q is not None else o.pb.q)
-    worst = 0.0
-    for v in range(5):
-        scale = max(np.abs(B[v]).max(), fs[v])
-        if scale == 0:
-            continue
-        worst = max(worst, np.abs(A[v] - B[v]).max() / scale)
-    return worst
+    blocks' packed interior fields (both normalisations are logged)."""
+    term, plain = field_errors(a, b, o, q)
+    log_errors(os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], kind="residual", term=term, plain=plain)
+    return max(term)
 
 
 def rel_err_states(qa, qb, o):
@@ -76,7 +113,9 @@ def rel_err_states(qa, qb, o):
     ib = np.concatenate([x.reshape(5, -1) for x in o.interior(qb)], axis=1)
     mags = np.abs(ib).max(axis=1)
     scale = [mags[0], mags[1:4].max(), mags[1:4].max(), mags[1:4].max(), mags[4]]
-    return max(np.abs(ia[v] - ib[v]).max() / scale[v] for v in range(5) if scale[v] > 0)
+    errs = [float(np.abs(ia[v] - ib[v]).max() / scale[v]) if scale[v] > 0 else 0.0 for v in range(5)]
+    log_errors(os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], kind="state", err=errs)
+    return max(errs)
 
 
 def residual_pair(pb, precision, exchange=True, **kw):
@@ -385,3 +424,48 @@ def test_staged_upload_equals_direct_set_state():
     b = s.get_state(0).cpu().numpy()
     s.close()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_changing_dt_replays_one_graph(prec):
+    """CFL-style stepping: 30 distinct time steps through fv_rk_step's graph
+    (dt read from a device slot at replay) keep one cached graph and give,
+    bit for bit, the states of the uncaptured stage sequence; the binary64
+    and double-float forms also match the oracle stepped with the same dt
+    sequence."""
+    pb = cases.mms_3d((19, 11, 7), curvilinear=True)
+    dts = pb.dt * (0.5 + 0.5 * np.random.default_rng(3).random(30))
+    a, b = solver(pb, prec), solver(pb, prec)
+    for dt in dts:
+        a.rk_step(float(dt), use_graph=True)
+        b.rk_step(float(dt), use_graph=False)
+    assert a.graph_count() == 1
+    qa, qb = a.get_state(0).cpu().numpy(), b.get_state(0).cpu().numpy()
+    a.close()
+    b.close()
+    assert np.array_equal(qa, qb)
+    if prec != "fp32flux":
+        o = oracle.Oracle(pb)
+        q = pb.q.copy()
+        for dt in dts:
+            q = o.run(q, float(dt), 4)
+        assert rel_err_states(qa, q, o) <= TOL_RUN[prec]
+
+
+def test_graph_cache_is_bounded_by_streams():
+    """One graph per stream, at most eight: stepping on ten streams evicts
+    the least recently used, and every replay still steps the state."""
+    pb = cases.mms_3d((13, 9, 5), curvilinear=True)
+    a, b = solver(pb, "fp64"), solver(pb, "fp64")
+    streams = [torch.cuda.Stream() for _ in range(10)]
+    for st in streams + streams[:3]:
+        st.wait_stream(torch.cuda.current_stream())
+        a.rk_step(pb.dt, use_graph=True, stream=st.cuda_stream)
+        torch.cuda.current_stream().wait_stream(st)
+        b.rk_step(pb.dt, use_graph=False)
+    torch.cuda.synchronize()
+    assert a.graph_count() == 8
+    qa, qb = a.get_state(0).cpu().numpy(), b.get_state(0).cpu().numpy()
+    a.close()
+    b.close()
+    assert np.array_equal(qa, qb)
