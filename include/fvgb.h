@@ -424,14 +424,24 @@ int fv_halo_unpack(fv_handle h, int buffer, const double* recv_dev, void* stream
  * second of: [0] binary64 FMA, [1] add, [2] multiply, [3] the compiler's IEEE
  * reciprocal 1.0/x, [4] IEEE square root, [5] binary32 FMA, and the
  * double-float operations of the stage kernel's other form: [6] add,
- * [7] multiply, [8] quotient, [9] square root, [10] absolute value.
+ * [7] multiply, [8] quotient, [9] square root, [10] absolute value, and
+ * [11] the binary64 face code's reciprocal (see fv_check_rcp64).
  * Allocates and frees 2 KB, synchronises `stream`, takes ~50 ms.
  * FV_ERR_INVALID_ARG for a NULL pointer or short array, FV_ERR_CUDA if a
  * launch fails.
  * ------------------------------------------------------------------------- */
-#define FV_PROBE_NRATES 11
+#define FV_PROBE_NRATES 12
 
 int fv_probe_alu_rates(double* out_host, int n_out, void* stream);
+
+/* Test support for the binary64 face code's reciprocal (a Newton-type
+ * refinement of the hardware's approximate reciprocal, within one unit in
+ * the last place of 1/x): for each of the n doubles at x_dev (device) writes
+ * out_dev[2i] = that reciprocal and out_dev[2i+1] = the compiler's IEEE
+ * 1.0 / x[i] (device, 2n doubles), asynchronously on `stream`.
+ * FV_ERR_INVALID_ARG for NULL pointers or n <= 0, FV_ERR_CUDA if the launch
+ * fails. */
+int fv_check_rcp64(const double* x_dev, int64_t n, double* out_dev, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free residual norms.  The paper has no counterpart: this entry

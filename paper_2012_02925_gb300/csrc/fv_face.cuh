@@ -143,9 +143,10 @@ __device__ __forceinline__ void muscl(const CC& C, T vm1, T v0, T vp1, T vp2, T&
 
 // Harten: |l| <- (l^2 + d^2) / (2 d) when |l| < d (a branch: the fix is
 // rare, near sonic points; a select costing both sides always was slower)
+// (lam = |eigenvalue| and delta > 0 are non-negative)
 template <class T, class CC>
 __device__ __forceinline__ T entropy_fixed(const CC& C, T lam, T delta) {
-  if (Sc<T>::lt(lam, delta)) return (lam * lam + delta * delta) * Sc<T>::halve(Sc<T>::rcp(delta));
+  if (Sc<T>::lt_nonneg(lam, delta)) return (lam * lam + delta * delta) * Sc<T>::halve(Sc<T>::rcp(delta));
   return lam;
 }
 

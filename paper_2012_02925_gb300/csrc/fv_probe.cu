@@ -7,8 +7,8 @@
 // / device time (CUDA events, best of three launches after a warm-up).  The
 // chains' results feed a store that never happens at run time, so nothing is
 // optimised away.  binary64 operations are the hardware's (DFMA, DADD, DMUL)
-// and the compiler's IEEE reciprocal and square root, exactly as the binary64
-// face code calls them; the double-float operations are those of
+// and the compiler's IEEE reciprocal and square root, and the face code's
+// own reciprocal (fv_rcp64); the double-float operations are those of
 // fv_arith.cuh.
 #include <cuda_runtime.h>
 
@@ -21,7 +21,7 @@ constexpr int CHAINS = 8;
 constexpr int THREADS = 256;
 
 enum ProbeOp {
-  P_DFMA, P_DADD, P_DMUL, P_DRCP, P_DSQRT, P_FFMA, P_DF_ADD, P_DF_MUL, P_DF_DIV, P_DF_SQRT, P_DF_ABS
+  P_DFMA, P_DADD, P_DMUL, P_DRCP, P_DSQRT, P_FFMA, P_DF_ADD, P_DF_MUL, P_DF_DIV, P_DF_SQRT, P_DF_ABS, P_DRCPN
 };
 
 template <int OP>
@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(THREADS) probe_fp64(int iters, double seed, do
       if (OP == P_DMUL) x[c] = x[c] * a;
       if (OP == P_DRCP) x[c] = 1.0 / x[c];
       if (OP == P_DSQRT) x[c] = sqrt(x[c]);
+      if (OP == P_DRCPN) x[c] = fv_rcp64(x[c]);
     }
   }
   double s = 0.0;
@@ -138,10 +139,35 @@ extern "C" int fv_probe_alu_rates(double* out_host, int n_out, void* stream) {
   out_host[8] = FV_PROBE_DF(P_DF_DIV, it_dfs);
   out_host[9] = FV_PROBE_DF(P_DF_SQRT, it_dfs);
   out_host[10] = FV_PROBE_DF(P_DF_ABS, it_df);
+  out_host[11] = FV_PROBE_D(P_DRCPN, it_slow);
 #undef FV_PROBE_D
 #undef FV_PROBE_DF
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);
   return err ? FV_ERR_CUDA : FV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// binary64 reciprocal check: the face code's reciprocal next to the
+// compiler's IEEE 1.0 / x, for a test on the host
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void rcp_check_kernel(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    out[2 * i] = fv_rcp64(x[i]);
+    out[2 * i + 1] = 1.0 / x[i];
+  }
+}
+}  // namespace
+
+extern "C" int fv_check_rcp64(const double* x_dev, int64_t n, double* out_dev, void* stream) {
+  if (!x_dev || !out_dev || n <= 0) return FV_ERR_INVALID_ARG;
+  const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  long long nn = n;
+  void* args[] = {&x_dev, &nn, &out_dev};
+  if (cudaLaunchKernel((const void*)rcp_check_kernel, dim3((unsigned)blocks), dim3(256), args, 0,
+                       (cudaStream_t)stream) != cudaSuccess)
+    return FV_ERR_CUDA;
+  return FV_OK;
 }
