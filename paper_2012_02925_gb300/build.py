@@ -12,9 +12,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfvgb.so")
 # the stage kernel variants (fv_stage_<form>[_fast][_visc][_bc].cu, one per
 # translation unit so that they compile in parallel), then the rest
-STAGE_VARIANTS = ["fp64", "fp64_bc", "fp64_visc", "fp64_visc_bc"] + [
-    form + fast + visc + bc for form in ("df64", "fp32") for fast in ("", "_fast") for visc in ("", "_visc")
-    for bc in ("", "_bc")]
+STAGE_VARIANTS = [form + fast + visc + bc for form in ("fp64", "df64", "fp32") for fast in ("", "_fast")
+                  for visc in ("", "_visc") for bc in ("", "_bc")]
 SOURCES = ["fv_stage_%s.cu" % v for v in STAGE_VARIANTS] + [
     "fv_api.cu", "fv_noalloc.cu", "fv_probe.cu", "fv_adjoint.cu", "fv_visc.cu", "fv_monitor.cu"]
 HEADERS = ["fv_arith.cuh", "fv_face.cuh", "fv_stage.cuh", "fv_viscface.cuh", "fv_internal.h", "fv_adjoint.cuh"]
