@@ -587,7 +587,10 @@ def run_e2e(s, pb, steps, dist=None, world=1):
 def run_adjoint(n=96, nstages=50, rates=None, pk=None, peak_kind=None):
     """Discrete adjoint workload: 96^3 curvilinear block, van Albada, Harten
     fix on every eigenvalue, J = integrated pressure on the k=0 face after 50
-    RK stages; forward with stage checkpoints, then the VJP chain."""
+    RK stages; forward with stage checkpoints, then the VJP chain.  The face
+    sweeps run in binary64 and in double-float arithmetic
+    (fv_set_adjoint_arith); the forward binary64 stage of the same block is
+    timed beside them."""
     import torch
     import paper_2012_02925_gb300 as fv
     from paper_2012_02925_gb300.autograd import run_stages
@@ -597,46 +600,52 @@ def run_adjoint(n=96, nstages=50, rates=None, pk=None, peak_kind=None):
     s.set_state(q0)
     b = pb.blocks[0]
     g = (b.nk + 4, b.nj + 4, b.ni + 4)
+    st = torch.cuda.current_stream()
 
     def J(q):
         Q = q.view(5, *g)[:, 2, 2:-2, 2:-2].reshape(5, -1)
         return ((0.4 * (Q[4] - 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]))).sum()
-    x = q0.clone().requires_grad_(True)
-    out = run_stages(s, x, pb.dt, nstages)   # warm-up (allocates adjoint scratch)
-    J(out).backward()
-    torch.cuda.synchronize()
-    x = q0.clone().requires_grad_(True)
-    t0 = time.perf_counter()
-    out = run_stages(s, x, pb.dt, nstages)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    J(out).backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    fwd_s = timed(lambda: s.rk_stage(2, pb.dt), 10)
+    out = {"workload": pb.name + "_adjoint", "stages": nstages, "cells": pb.ncells, "unit": "Gcell-updates/s",
+           "forward_fp64_stage_ms": fwd_s * 1e3}
     lam = torch.randn(s.field_size, dtype=torch.float64, device="cuda")
     li = torch.empty_like(lam)
     l0 = torch.zeros_like(lam)
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(5):
-        s.adjoint_vjp(2, pb.dt, q0, lam, li, l0)
-    e1.record(st)
-    torch.cuda.synchronize()
-    vjp_s = e0.elapsed_time(e1) / 1e3 / 5
+    for arith in ("fp64", "df64"):
+        s.set_adjoint_arith(arith)
+        x = q0.clone().requires_grad_(True)
+        J(run_stages(s, x, pb.dt, nstages)).backward()   # warm-up (allocates adjoint scratch)
+        torch.cuda.synchronize()
+        x = q0.clone().requires_grad_(True)
+        t0 = time.perf_counter()
+        y = run_stages(s, x, pb.dt, nstages)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J(y).backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        vjp_s = timed(lambda: s.adjoint_vjp(2, pb.dt, q0, lam, li, l0), 5)
+        r = {"forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1, "vjp_stage_ms": vjp_s * 1e3,
+             "vjp_value": pb.ncells / vjp_s / 1e9, "vjp_over_forward_stage": vjp_s / fwd_s}
+        if rates is not None:
+            # one VJP stage reads the checkpoint (40 B) and lambda_out (40 B),
+            # the metrics (80 B), and writes lambda_in (40 B) and updates
+            # lambda_Q0 (80 B): 280 B per cell
+            hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+            r["hbm_frac"] = 280.0 * pb.ncells / vjp_s / 1e9 / hbm
+        out[arith] = r
     s.close()
-    out = {"workload": pb.name + "_adjoint", "stages": nstages, "cells": pb.ncells,
-           "forward_with_checkpoints_s": t1 - t0, "backward_s": t2 - t1,
-           "vjp_stage_ms": vjp_s * 1e3, "vjp_value": pb.ncells / vjp_s / 1e9, "unit": "Gcell-updates/s",
-           "precision": "fp64"}
-    if rates is not None:
-        # one VJP stage reads the checkpoint (40 B) and lambda_out (40 B),
-        # the metrics (80 B), and writes lambda_in (40 B) and updates
-        # lambda_Q0 (80 B): 280 B per cell
-        byts = 280.0 * pb.ncells
-        hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
-        out["roofline"] = {"bound": "alu", "hbm_frac": byts / vjp_s / 1e9 / hbm,
-                           "fp64_peak_g": 2.0 * rates["fp64_fma"] / 1e9, "peak_source": peak_kind}
     return out
 
 

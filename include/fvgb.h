@@ -367,6 +367,14 @@ int fv_get_launch(fv_handle h, int* out4);
 int fv_adjoint_vjp(fv_handle h, int stage, double dt, const double* qin_dev, const double* lam_out_dev,
                    double* lam_in_dev, double* lam_q0_dev, void* stream);
 
+/* Arithmetic of fv_adjoint_vjp's per-face sweeps (not in the paper):
+ * FV_PREC_FP64 (the default) or FV_PREC_DF64 - double-float on the binary32
+ * units, relative error ~1e-14 per operation, several times faster on parts
+ * whose binary64 rate is a small fraction of the binary32 rate.  States,
+ * cotangents, the gather, the exchange transpose and the accumulation stay
+ * binary64.  FV_ERR_INVALID_ARG for any other value. */
+int fv_set_adjoint_arith(fv_handle h, int precision);
+
 /* ---------------------------------------------------------------------------
  * Cross-device halo: connections whose two sides live on different devices
  * (ranks) after the blocks are split and aggregated onto processors

@@ -25,7 +25,7 @@ EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error
            "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
            "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged", "fv_graph_count",
            "fv_probe_alu_rates", "fv_set_halo", "fv_halo_size", "fv_halo_pack", "fv_halo_unpack",
-           "fv_check_rcp64")
+           "fv_check_rcp64", "fv_set_adjoint_arith")
 
 
 class FvError(RuntimeError):
@@ -109,6 +109,8 @@ def load_library(path: Optional[str] = None):
     L.fv_graph_count.restype = i32
     L.fv_probe_alu_rates.argtypes = [vp, i32, vp]
     L.fv_probe_alu_rates.restype = i32
+    L.fv_set_adjoint_arith.argtypes = [vp, i32]
+    L.fv_set_adjoint_arith.restype = i32
     L.fv_check_rcp64.argtypes = [vp, i64, vp, vp]
     L.fv_check_rcp64.restype = i32
     L.fv_set_halo.argtypes = [vp, ctypes.POINTER(fv_connection), i32, ctypes.POINTER(fv_connection), i32]
@@ -361,6 +363,10 @@ class Solver:
     def halo_unpack(self, buffer: int, recv, stream=None):
         self._check(self._L.fv_halo_unpack(self._h, int(buffer), _ptr(recv) if recv is not None else None,
                                            _stream(stream)))
+
+    def set_adjoint_arith(self, precision: str) -> None:
+        """Arithmetic of the adjoint's face sweeps: "fp64" or "df64"."""
+        self._check(self._L.fv_set_adjoint_arith(self._h, PRECISIONS[precision]))
 
     def graph_count(self) -> int:
         """RK-step graphs held (one per stream stepped on with use_graph)."""

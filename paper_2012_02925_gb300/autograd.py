@@ -7,6 +7,13 @@ chain of stages can be differentiated end to end by torch.  The tensors are
 packed ghosted states (float64, on the GPU); gradients flow through interior
 cells only - fixed ghost values are constants of the problem.
 
+Memory: a plain chain keeps one state per stage (the stage inputs, which
+the chain holds anyway; nothing is copied), O(stages).  With ``segment`` =
+k steps, ``run_stages`` keeps only the input of every k-th step and
+recomputes a segment's stages (deterministically, so the gradient is the
+same bit for bit) when its backward runs: about (stages / (k M) + k M)
+states.
+
 Everything numerical runs in the library's kernels; this module copies
 states in and out of the library's buffers and maps between the packed
 ghosted layout and the packed interior field (index gathers).
@@ -58,7 +65,9 @@ class RKStage(torch.autograd.Function):
             solver.set_buffer(src, qin.detach().contiguous())
         solver.rk_stage(m, dt)
         out = solver.get_state(dst)
-        ctx.save_for_backward(qin.detach().clone())     # stage checkpoint
+        # stage checkpoint: the input itself (stage outputs are fresh tensors
+        # nobody writes in place, so no copy is needed)
+        ctx.save_for_backward(qin)
         ctx.solver, ctx.m, ctx.dt = solver, m, dt
         return out
 
@@ -73,15 +82,31 @@ class RKStage(torch.autograd.Function):
         return scatter_interior(s, lam_q0), scatter_interior(s, lam_in), None, None, None
 
 
-def run_stages(solver, q: torch.Tensor, dt: float, nstages: int) -> torch.Tensor:
-    """Differentiable chain of ``nstages`` RK stages (whole steps of M stages,
-    the last possibly partial) starting from packed ghosted state ``q``."""
+def _chain(solver, q: torch.Tensor, dt: float, first: int, count: int) -> torch.Tensor:
+    """Stages first .. first+count-1 of the global stage sequence from q,
+    the input of stage index ``first`` (a step boundary)."""
     M = solver.n_stages
     q0 = q
     cur = q
-    for st in range(nstages):
+    for st in range(first, first + count):
         m = st % M + 1
         if m == 1:
             q0 = cur
         cur = RKStage.apply(q0, cur, solver, m, dt)
+    return cur
+
+
+def run_stages(solver, q: torch.Tensor, dt: float, nstages: int, segment: int = 0) -> torch.Tensor:
+    """Differentiable chain of ``nstages`` RK stages (whole steps of M stages,
+    the last possibly partial) starting from packed ghosted state ``q``.
+    ``segment`` > 0: recompute each run of ``segment`` steps in backward
+    instead of keeping its stage checkpoints (torch.utils.checkpoint)."""
+    if segment <= 0 or not q.requires_grad:
+        return _chain(solver, q, dt, 0, nstages)
+    from torch.utils.checkpoint import checkpoint
+    span = segment * solver.n_stages
+    cur = q
+    for first in range(0, nstages, span):
+        count = min(span, nstages - first)
+        cur = checkpoint(_chain, solver, cur, dt, first, count, use_reentrant=False)
     return cur

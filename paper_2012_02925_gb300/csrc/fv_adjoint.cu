@@ -1,5 +1,5 @@
-// Discrete adjoint (vector-Jacobian product) of one Runge-Kutta stage,
-// binary64.  Stage map: Q^(m) = Q^(0) - alpha_m dt / Omega * R(X(Q^(m-1)))
+// Discrete adjoint (vector-Jacobian product) of one Runge-Kutta stage; the
+// face VJPs in binary64 or double-float arithmetic, everything else binary64.  Stage map: Q^(m) = Q^(0) - alpha_m dt / Omega * R(X(Q^(m-1)))
 // with X the ghost exchange.  For a cotangent lam of Q^(m):
 //   mu_c   = -alpha_m dt / Omega_c * lam_c              (cotangent of R_c)
 //   Fbar_f = mu_L(f) - mu_R(f)                          (R_L holds +F_f, R_R holds -F_f)
@@ -18,11 +18,16 @@ __device__ __forceinline__ long long ghost_index(const FvBlockDev& B, int i, int
   return (long long)(k + FV_GHOST) * B.kstride + (long long)(j + FV_GHOST) * B.jstride + (i + FV_GHOST);
 }
 
-// faces of direction `dir` in block B: index f over (n_dir + 1) x (other two extents)
-__global__ void adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
-                                const double* __restrict__ lam_out, const double* __restrict__ invvol,
-                                double alpha_dt, const double* __restrict__ metric, long long mstride,
-                                const AdjParams P, double* __restrict__ contrib) {
+// faces of direction `dir` in block B: index f over (n_dir + 1) x (other two
+// extents); the face's VJP in arithmetic T, inputs and outputs binary64
+template <class T>
+__global__ void __launch_bounds__(128) adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
+                                                       const double* __restrict__ lam_out,
+                                                       const double* __restrict__ invvol, double alpha_dt,
+                                                       const double* __restrict__ metric, long long mstride,
+                                                       const AdjParams PP, double* __restrict__ contrib) {
+  using S = Sc<T>;
+  const AdjC<T> P = adj_consts<T>(PP);
   const int ei = B.ni + (dir == 0), ej = B.nj + (dir == 1), ek = B.nk + (dir == 2);
   const long long nf = (long long)ei * ej * ek;
   const long long ncell_b = (long long)B.ni * B.nj * B.nk;
@@ -34,40 +39,49 @@ __global__ void adj_face_kernel(const FvBlockDev B, int dir, const double* __res
     const int n_dir = dir == 0 ? B.ni : (dir == 1 ? B.nj : B.nk);
     const long long stride = dir == 0 ? 1 : (dir == 1 ? B.jstride : B.kstride);
     const long long c1 = ghost_index(B, i - (dir == 0), j - (dir == 1), k - (dir == 2));   // cell g-1
-    double q[4][5];
+    T q[4][5];
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int n = 0; n < 5; ++n) q[s][n] = qb[c1 + (s - 1) * stride + n * B.plane];
+      for (int n = 0; n < 5; ++n) q[s][n] = S::from_d(qb[c1 + (s - 1) * stride + n * B.plane]);
     // cotangent of the face flux from the two cells' residual cotangents
-    double Fb[5] = {0, 0, 0, 0, 0};
+    double Fd[5] = {0, 0, 0, 0, 0};
     if (g - 1 >= 0) {
       const int il = i - (dir == 0), jl = j - (dir == 1), kl = k - (dir == 2);
       const long long cl = ((long long)kl * B.nj + jl) * B.ni + il;
       const double fac = -alpha_dt * (B.cartesian ? B.cart_invvol : invvol[B.cell_off + cl]);
 #pragma unroll
-      for (int n = 0; n < 5; ++n) Fb[n] += fac * lam[n * ncell_b + cl];
+      for (int n = 0; n < 5; ++n) Fd[n] += fac * lam[n * ncell_b + cl];
     }
     if (g < n_dir) {
       const long long cr = ((long long)k * B.nj + j) * B.ni + i;
       const double fac = -alpha_dt * (B.cartesian ? B.cart_invvol : invvol[B.cell_off + cr]);
 #pragma unroll
-      for (int n = 0; n < 5; ++n) Fb[n] -= fac * lam[n * ncell_b + cr];
+      for (int n = 0; n < 5; ++n) Fd[n] -= fac * lam[n * ncell_b + cr];
     }
-    double nx, ny, nz, A;
+    T Fb[5];
+#pragma unroll
+    for (int n = 0; n < 5; ++n) Fb[n] = S::from_d(Fd[n]);
+    T nx, ny, nz, A;
     if (B.cartesian) {
-      nx = B.cart_n[dir][0]; ny = B.cart_n[dir][1]; nz = B.cart_n[dir][2]; A = B.cart_area[dir];
+      nx = S::from_d(B.cart_n[dir][0]); ny = S::from_d(B.cart_n[dir][1]); nz = S::from_d(B.cart_n[dir][2]);
+      A = S::from_d(B.cart_area[dir]);
     } else {
       const long long fi = B.face_off[dir] + f;
-      nx = metric[4 * fi]; ny = metric[4 * fi + 1]; nz = metric[4 * fi + 2]; A = metric[4 * fi + 3];
+      nx = S::from_d(metric[4 * fi]); ny = S::from_d(metric[4 * fi + 1]);
+      nz = S::from_d(metric[4 * fi + 2]); A = S::from_d(metric[4 * fi + 3]);
     }
-    double qbar[4][5] = {}, F[5];
+    T qbar[4][5], F[5];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int n = 0; n < 5; ++n) qbar[s][n] = S::c(0.0);
     face_vjp(P, q, nx, ny, nz, A, Fb, qbar, F);
     double* out = contrib + f * 20;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int n = 0; n < 5; ++n) out[s * 5 + n] = qbar[s][n];
+      for (int n = 0; n < 5; ++n) out[s * 5 + n] = S::to_d(qbar[s][n]);
   }
 }
 
@@ -170,7 +184,7 @@ int grid_of(long long n, int threads) {
 
 int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const double* lam_out, const double* invvol,
                      double alpha_dt, const double* metric, long long mstride, const FvFaceParams& fp,
-                     double* contrib, cudaStream_t s) {
+                     int double_float, double* contrib, cudaStream_t s) {
   AdjParams P;
   P.gm1 = fp.gamma - 1.0;
   P.g_gm1 = fp.gamma / (fp.gamma - 1.0);
@@ -181,7 +195,12 @@ int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const doub
   P.limiter = fp.limiter;
   P.fix_all = fp.fix_all;
   const long long nf = (long long)(B.ni + (dir == 0)) * (B.nj + (dir == 1)) * (B.nk + (dir == 2));
-  adj_face_kernel<<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride, P, contrib);
+  if (double_float)
+    adj_face_kernel<df64><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride, P,
+                                                           contrib);
+  else
+    adj_face_kernel<double><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride,
+                                                             P, contrib);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -1,4 +1,4 @@
-// Reverse-mode (vector-Jacobian) form of one face of the residual, in binary64.
+// Reverse-mode (vector-Jacobian) form of one face of the residual.
 //
 // The forward face is the one of fv_face.cuh: primitive recovery of the four
 // stencil cells (Section 2), MUSCL reconstruction with limiter, Eq. (flux) of
@@ -7,16 +7,15 @@
 // conserved inputs (4 cells x 5 variables).  Every intermediate of the forward
 // pass is recomputed and then swept backwards, statement by statement.
 //
+// Written once for an arithmetic type T (fv_arith.cuh): binary64, or
+// double-float on the FP32 pipe (~48-bit significand; GB300's FP64 unit runs
+// at 1/64 of the binary32 rate, and the sweep costs ~3 forward faces).
+//
 // The paper has no adjoint; this is the discrete adjoint of its residual.
 #pragma once
-#include <cmath>
+#include "fv_arith.cuh"
 
-#ifdef __CUDACC__
-#define FVA_HD __host__ __device__ __forceinline__
-#else
-#define FVA_HD inline
-#endif
-
+// method parameters (binary64, from the handle)
 struct AdjParams {
   double gm1, g_gm1;       // gamma - 1, gamma / (gamma - 1)
   double e4km, e4kp;       // eps/4 (1 - kappa), eps/4 (1 + kappa)
@@ -24,135 +23,190 @@ struct AdjParams {
   int limiter, fix_all;
 };
 
+// the same in the arithmetic type, with the constants the sweep uses
+template <class T>
+struct AdjC {
+  T gm1, g_gm1, e4km, e4kp, harten, va_d2, half, one, two;
+  int limiter, fix_all;
+  bool fix;
+};
+
+template <class T>
+__device__ __forceinline__ AdjC<T> adj_consts(const AdjParams& P) {
+  using S = Sc<T>;
+  AdjC<T> c;
+  c.gm1 = S::c(P.gm1);
+  c.g_gm1 = S::c(P.g_gm1);
+  c.e4km = S::c(P.e4km);
+  c.e4kp = S::c(P.e4kp);
+  c.harten = S::c(P.harten);
+  c.va_d2 = S::c(P.va_d2);
+  c.half = S::c(0.5);
+  c.one = S::c(1.0);
+  c.two = S::c(2.0);
+  c.limiter = P.limiter;
+  c.fix_all = P.fix_all;
+  c.fix = P.harten > 0.0;
+  return c;
+}
+
 // limited difference phi(a, b) = Psi(a/b) b and its partial derivatives
-FVA_HD double lim_phi(const AdjParams& P, double a, double b, double& da, double& db) {
-  if (P.limiter == 0) { da = 0.0; db = 1.0; return b; }
+template <class T>
+__device__ __forceinline__ T lim_phi(const AdjC<T>& P, T a, T b, T& da, T& db) {
+  using S = Sc<T>;
+  if (P.limiter == 0) { da = S::c(0.0); db = P.one; return b; }
   if (P.limiter == 1) {
     // van Leer: 2ab/(a+b) when ab > 0, else 0
-    if (a * b > 0.0) {
-      const double s = a + b, is2 = 1.0 / (s * s);
-      da = 2.0 * b * b * is2;
-      db = 2.0 * a * a * is2;
-      return 2.0 * a * b / s;
+    if (S::pos(a * b)) {
+      const T s = a + b, is2 = S::rcp(s * s);
+      da = S::twice(b * b * is2);
+      db = S::twice(a * a * is2);
+      return S::twice(a * b) * S::rcp(s);
     }
-    da = 0.0; db = 0.0;
-    return 0.0;
+    da = S::c(0.0); db = S::c(0.0);
+    return S::c(0.0);
   }
   // van Albada product form: N / D, N = a^2 b + a b^2, D = a^2 + b^2 + delta^2
-  const double N = a * a * b + a * b * b, D = a * a + b * b + P.va_d2, iD = 1.0 / D;
-  da = ((2.0 * a * b + b * b) - N * 2.0 * a * iD) * iD;
-  db = ((a * a + 2.0 * a * b) - N * 2.0 * b * iD) * iD;
+  const T N = a * a * b + a * b * b, D = a * a + b * b + P.va_d2, iD = S::rcp(D);
+  da = ((S::twice(a * b) + b * b) - S::twice(N * a * iD)) * iD;
+  db = ((a * a + S::twice(a * b)) - S::twice(N * b * iD)) * iD;
   return N * iD;
 }
 
+template <class T>
 struct PrimFwd {
-  double r, u, v, w, p, ri, k;
+  T r, u, v, w, p, ri, k;
 };
 
-FVA_HD PrimFwd prim_fwd(const AdjParams& P, const double q[5]) {
-  PrimFwd s;
+template <class T>
+__device__ __forceinline__ PrimFwd<T> prim_fwd(const AdjC<T>& P, const T q[5]) {
+  using S = Sc<T>;
+  PrimFwd<T> s;
   s.r = q[0];
-  s.ri = 1.0 / q[0];
+  s.ri = S::rcp(q[0]);
   s.u = q[1] * s.ri;
   s.v = q[2] * s.ri;
   s.w = q[3] * s.ri;
   s.k = s.u * s.u + s.v * s.v + s.w * s.w;
-  s.p = P.gm1 * (q[4] - 0.5 * q[0] * s.k);
+  s.p = P.gm1 * (q[4] - S::halve(q[0] * s.k));
   return s;
 }
 
-// qbar += (dV/dq)^T Vbar for V = (rho, u, v, w, p)
-FVA_HD void prim_bwd(const AdjParams& P, const double q[5], const PrimFwd& s, const double Vb[5], double qb[5]) {
-  const double pb = Vb[4];
-  qb[4] += P.gm1 * pb;
-  const double ub = Vb[1] - P.gm1 * s.r * s.u * pb;
-  const double vb = Vb[2] - P.gm1 * s.r * s.v * pb;
-  const double wb = Vb[3] - P.gm1 * s.r * s.w * pb;
-  double rb = Vb[0] - P.gm1 * 0.5 * s.k * pb;
-  qb[1] += ub * s.ri;
-  qb[2] += vb * s.ri;
-  qb[3] += wb * s.ri;
-  const double rib = ub * q[1] + vb * q[2] + wb * q[3];
-  rb += -rib * s.ri * s.ri;
-  qb[0] += rb;
+// qbar += (dV/dq)^T Vbar for V = (rho, u, v, w, p), from the primitives
+// alone (rho u = r u etc.), so the conserved inputs need not stay live
+template <class T>
+__device__ __forceinline__ void prim_bwd(const AdjC<T>& P, const PrimFwd<T>& s, const T Vb[5], T qb[5]) {
+  using S = Sc<T>;
+  const T pb = Vb[4];
+  qb[4] = qb[4] + P.gm1 * pb;
+  const T gpb = P.gm1 * s.r * pb;
+  const T ub = Vb[1] - gpb * s.u;
+  const T vb = Vb[2] - gpb * s.v;
+  const T wb = Vb[3] - gpb * s.w;
+  qb[1] = qb[1] + ub * s.ri;
+  qb[2] = qb[2] + vb * s.ri;
+  qb[3] = qb[3] + wb * s.ri;
+  // d(1/rho)/d rho = -1/rho^2 against rib = ub rho u + vb rho v + wb rho w
+  const T rib = s.r * (ub * s.u + vb * s.v + wb * s.w);
+  qb[0] = qb[0] + ((Vb[0] - S::halve(P.gm1 * s.k * pb)) - rib * s.ri * s.ri);
 }
 
-FVA_HD double fix_fwd(double l, double d, bool on, double& dl, double& dd) {
-  if (on && l < d) {
-    dl = l / d;
-    dd = 0.5 - l * l / (2.0 * d * d);
-    return (l * l + d * d) / (2.0 * d);
+template <class T>
+__device__ __forceinline__ T fix_fwd(const AdjC<T>& P, T l, T d, bool on, T& dl, T& dd) {
+  using S = Sc<T>;
+  if (on && S::lt_nonneg(l, d)) {
+    const T id = S::rcp(d);
+    dl = l * id;
+    dd = P.half - S::halve(dl * dl);
+    return S::halve((l * l + d * d) * id);
   }
-  dl = 1.0; dd = 0.0;
+  dl = P.one; dd = S::c(0.0);
   return l;
+}
+
+// sign of x as +-1 (x = 0 counts as positive)
+template <class T>
+__device__ __forceinline__ T sgn(T x) {
+  return Sc<T>::sel(Sc<T>::neg(x), Sc<T>::c(-1.0), Sc<T>::c(1.0));
 }
 
 // Face VJP: q[c][n] conserved state of stencil cell c (c = 0..3 along the face
 // normal, the face between cells 1 and 2), unit normal n, area A, cotangent Fb
 // of the 5 face fluxes (F^ |S|).  Accumulates qb[c][n].  Returns F in F (may be
 // used to check the forward).
-FVA_HD void face_vjp(const AdjParams& P, const double q[4][5], double nx, double ny, double nz, double A,
-                     const double Fb[5], double qb[4][5], double F[5]) {
+template <class T>
+__device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx, T ny, T nz, T A, const T Fb[5],
+                                         T qb[4][5], T F[5]) {
+  using S = Sc<T>;
   // ---------------- forward ----------------
-  PrimFwd s[4];
+  PrimFwd<T> s[4];
+#pragma unroll
   for (int c = 0; c < 4; ++c) s[c] = prim_fwd(P, q[c]);
-  double V[4][5];
-  for (int c = 0; c < 4; ++c) { V[c][0] = s[c].r; V[c][1] = s[c].u; V[c][2] = s[c].v; V[c][3] = s[c].w; V[c][4] = s[c].p; }
-  double VL[5], VR[5];
-  double pa[5][4], pb[5][4];  // limiter partials: [n][phi index] (a and b)
-  double dm[5], d0[5], dp[5];
+  // MUSCL states and their derivatives with respect to the three neighbour
+  // differences: VL = V1 + e4km phi(d0, dm) + e4kp phi(dm, d0),
+  // VR = V2 - e4kp phi(dp, d0) - e4km phi(d0, dp);
+  // jL0 = dVL/dd0, jLm = dVL/ddm, jR0 = dVR/dd0 (sign included), jRp = dVR/ddp
+  T VL[5], VR[5], jL0[5], jLm[5], jR0[5], jRp[5];
+#pragma unroll
   for (int n = 0; n < 5; ++n) {
-    dm[n] = V[1][n] - V[0][n];
-    d0[n] = V[2][n] - V[1][n];
-    dp[n] = V[3][n] - V[2][n];
-    const double f1 = lim_phi(P, d0[n], dm[n], pa[n][0], pb[n][0]);
-    const double f2 = lim_phi(P, dm[n], d0[n], pa[n][1], pb[n][1]);
-    const double f3 = lim_phi(P, dp[n], d0[n], pa[n][2], pb[n][2]);
-    const double f4 = lim_phi(P, d0[n], dp[n], pa[n][3], pb[n][3]);
-    VL[n] = V[1][n] + (P.e4km * f1 + P.e4kp * f2);
-    VR[n] = V[2][n] - (P.e4kp * f3 + P.e4km * f4);
+    const T v0 = n == 0 ? s[0].r : (n == 1 ? s[0].u : (n == 2 ? s[0].v : (n == 3 ? s[0].w : s[0].p)));
+    const T v1 = n == 0 ? s[1].r : (n == 1 ? s[1].u : (n == 2 ? s[1].v : (n == 3 ? s[1].w : s[1].p)));
+    const T v2 = n == 0 ? s[2].r : (n == 1 ? s[2].u : (n == 2 ? s[2].v : (n == 3 ? s[2].w : s[2].p)));
+    const T v3 = n == 0 ? s[3].r : (n == 1 ? s[3].u : (n == 2 ? s[3].v : (n == 3 ? s[3].w : s[3].p)));
+    const T dm = v1 - v0, d0 = v2 - v1, dp = v3 - v2;
+    T a1, b1, a2, b2, a3, b3, a4, b4;
+    const T f1 = lim_phi(P, d0, dm, a1, b1);
+    const T f2 = lim_phi(P, dm, d0, a2, b2);
+    const T f3 = lim_phi(P, dp, d0, a3, b3);
+    const T f4 = lim_phi(P, d0, dp, a4, b4);
+    VL[n] = v1 + (P.e4km * f1 + P.e4kp * f2);
+    VR[n] = v2 - (P.e4kp * f3 + P.e4km * f4);
+    jL0[n] = P.e4km * a1 + P.e4kp * b2;
+    jLm[n] = P.e4km * b1 + P.e4kp * a2;
+    jR0[n] = -(P.e4kp * b3 + P.e4km * a4);
+    jRp[n] = -(P.e4kp * a3 + P.e4km * b4);
   }
-  const double rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
-  const double rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
-  const double VnL = nx * uL + ny * vL + nz * wL, VnR = nx * uR + ny * vR + nz * wR;
-  const double riL = 1.0 / rL, riR = 1.0 / rR;
-  const double hL = P.g_gm1 * pL * riL + 0.5 * (uL * uL + vL * vL + wL * wL);
-  const double hR = P.g_gm1 * pR * riR + 0.5 * (uR * uR + vR * vR + wR * wR);
-  const double mL = rL * VnL, mR = rR * VnR;
-  const double z = rR * riL;
-  const double Rt = sqrt(z);
-  const double rt = rL * Rt;
-  const double w1 = 1.0 / (1.0 + Rt);
-  const double ut = (uL + Rt * uR) * w1, vt = (vL + Rt * vR) * w1, wt = (wL + Rt * wR) * w1;
-  const double ht = (hL + Rt * hR) * w1;
-  const double q2h = 0.5 * (ut * ut + vt * vt + wt * wt);
-  const double c2 = P.gm1 * (ht - q2h);
-  const double ct = sqrt(c2);
-  const double ic2 = 1.0 / c2;
-  const double Vnt = nx * ut + ny * vt + nz * wt;
-  const double dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dP = pR - pL, dVn = VnR - VnL;
-  const double x1 = Vnt - ct, x2 = Vnt, x5 = Vnt + ct;
-  const double la1 = fabs(x1), la2 = fabs(x2), la5 = fabs(x5);
-  const bool fix = P.harten > 0.0;
-  const double delta = P.harten * ct;
-  double d1l, d1d, d2l, d2d, d5l, d5d;
-  const double l1 = fix_fwd(la1, delta, fix, d1l, d1d);
-  const double l2 = fix_fwd(la2, delta, fix && P.fix_all, d2l, d2d);
-  const double l5 = fix_fwd(la5, delta, fix, d5l, d5d);
-  const double rcd = rt * ct * dVn;
-  const double hic2 = 0.5 * ic2;
-  const double a1 = l1 * (dP - rcd) * hic2;
-  const double a5 = l5 * (dP + rcd) * hic2;
-  const double a2 = l2 * (dr - dP * ic2);
-  const double a3 = l2 * rt;
-  const double a15 = a1 + a5, d51 = (a5 - a1) * ct;
-  const double D0 = a15 + a2;
-  const double D1 = a15 * ut + d51 * nx + a2 * ut + a3 * (du - nx * dVn);
-  const double D2 = a15 * vt + d51 * ny + a2 * vt + a3 * (dv - ny * dVn);
-  const double D3 = a15 * wt + d51 * nz + a2 * wt + a3 * (dw - nz * dVn);
-  const double E4 = ut * du + vt * dv + wt * dw - Vnt * dVn;
-  const double D4 = a15 * ht + d51 * Vnt + a2 * q2h + a3 * E4;
-  const double hA = 0.5 * A;
+  const T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
+  const T rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
+  const T VnL = nx * uL + ny * vL + nz * wL, VnR = nx * uR + ny * vR + nz * wR;
+  const T riL = S::rcp(rL), riR = S::rcp(rR);
+  const T hL = P.g_gm1 * pL * riL + S::halve(uL * uL + vL * vL + wL * wL);
+  const T hR = P.g_gm1 * pR * riR + S::halve(uR * uR + vR * vR + wR * wR);
+  const T mL = rL * VnL, mR = rR * VnR;
+  const T z = rR * riL;
+  const T Rt = S::sqrt(z);
+  const T rt = rL * Rt;
+  const T w1 = S::rcp(P.one + Rt);
+  const T ut = (uL + Rt * uR) * w1, vt = (vL + Rt * vR) * w1, wt = (wL + Rt * wR) * w1;
+  const T ht = (hL + Rt * hR) * w1;
+  const T q2h = S::halve(ut * ut + vt * vt + wt * wt);
+  const T c2 = P.gm1 * (ht - q2h);
+  const T ct = S::sqrt(c2);
+  const T ic2 = S::rcp(c2);
+  const T Vnt = nx * ut + ny * vt + nz * wt;
+  const T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dP = pR - pL, dVn = VnR - VnL;
+  const T x1 = Vnt - ct, x2 = Vnt, x5 = Vnt + ct;
+  const T la1 = S::abs(x1), la2 = S::abs(x2), la5 = S::abs(x5);
+  const bool fix = P.fix;
+  const T delta = P.harten * ct;
+  T d1l, d1d, d2l, d2d, d5l, d5d;
+  const T l1 = fix_fwd(P, la1, delta, fix, d1l, d1d);
+  const T l2 = fix_fwd(P, la2, delta, fix && P.fix_all, d2l, d2d);
+  const T l5 = fix_fwd(P, la5, delta, fix, d5l, d5d);
+  const T rcd = rt * ct * dVn;
+  const T hic2 = S::halve(ic2);
+  const T a1 = l1 * (dP - rcd) * hic2;
+  const T a5 = l5 * (dP + rcd) * hic2;
+  const T a2 = l2 * (dr - dP * ic2);
+  const T a3 = l2 * rt;
+  const T a15 = a1 + a5, d51 = (a5 - a1) * ct;
+  const T D0 = a15 + a2;
+  const T D1 = a15 * ut + d51 * nx + a2 * ut + a3 * (du - nx * dVn);
+  const T D2 = a15 * vt + d51 * ny + a2 * vt + a3 * (dv - ny * dVn);
+  const T D3 = a15 * wt + d51 * nz + a2 * wt + a3 * (dw - nz * dVn);
+  const T E4 = ut * du + vt * dv + wt * dw - Vnt * dVn;
+  const T D4 = a15 * ht + d51 * Vnt + a2 * q2h + a3 * E4;
+  const T hA = S::halve(A);
   F[0] = (mL + mR - D0) * hA;
   F[1] = (mL * uL + mR * uR + nx * (pL + pR) - D1) * hA;
   F[2] = (mL * vL + mR * vR + ny * (pL + pR) - D2) * hA;
@@ -160,49 +214,49 @@ FVA_HD void face_vjp(const AdjParams& P, const double q[4][5], double nx, double
   F[4] = (mL * hL + mR * hR - D4) * hA;
 
   // ---------------- reverse ----------------
-  const double G0 = Fb[0] * hA, G1 = Fb[1] * hA, G2 = Fb[2] * hA, G3 = Fb[3] * hA, G4 = Fb[4] * hA;
-  double rLb = 0, uLb = 0, vLb = 0, wLb = 0, pLb = 0, rRb = 0, uRb = 0, vRb = 0, wRb = 0, pRb = 0;
-  double hLb = 0, hRb = 0, VnLb = 0, VnRb = 0;
+  const T G0 = Fb[0] * hA, G1 = Fb[1] * hA, G2 = Fb[2] * hA, G3 = Fb[3] * hA, G4 = Fb[4] * hA;
+  T rLb = S::c(0.0), uLb = S::c(0.0), vLb = S::c(0.0), wLb = S::c(0.0), pLb = S::c(0.0), rRb = S::c(0.0), uRb = S::c(0.0), vRb = S::c(0.0), wRb = S::c(0.0), pRb = S::c(0.0);
+  T hLb = S::c(0.0), hRb = S::c(0.0), VnLb = S::c(0.0), VnRb = S::c(0.0);
   // central part
-  double mLb = G0 + G1 * uL + G2 * vL + G3 * wL + G4 * hL;
-  double mRb = G0 + G1 * uR + G2 * vR + G3 * wR + G4 * hR;
+  T mLb = G0 + G1 * uL + G2 * vL + G3 * wL + G4 * hL;
+  T mRb = G0 + G1 * uR + G2 * vR + G3 * wR + G4 * hR;
   uLb += G1 * mL; vLb += G2 * mL; wLb += G3 * mL; hLb += G4 * mL;
   uRb += G1 * mR; vRb += G2 * mR; wRb += G3 * mR; hRb += G4 * mR;
-  const double pnb = nx * G1 + ny * G2 + nz * G3;
+  const T pnb = nx * G1 + ny * G2 + nz * G3;
   pLb += pnb; pRb += pnb;
   // dissipation, Dn enters with -1
-  const double D0b = -G0, D1b = -G1, D2b = -G2, D3b = -G3, D4b = -G4;
-  const double a15b = D0b + D1b * ut + D2b * vt + D3b * wt + D4b * ht;
-  const double d51b = D1b * nx + D2b * ny + D3b * nz + D4b * Vnt;
-  const double a2b = D0b + D1b * ut + D2b * vt + D3b * wt + D4b * q2h;
-  const double a3b = D1b * (du - nx * dVn) + D2b * (dv - ny * dVn) + D3b * (dw - nz * dVn) + D4b * E4;
-  double utb = D1b * (a15 + a2) + D4b * a3 * du;
-  double vtb = D2b * (a15 + a2) + D4b * a3 * dv;
-  double wtb = D3b * (a15 + a2) + D4b * a3 * dw;
-  double htb = D4b * a15;
-  double Vntb = D4b * (d51 - a3 * dVn);
-  double q2hb = D4b * a2;
-  double dub = D1b * a3 + D4b * a3 * ut;
-  double dvb = D2b * a3 + D4b * a3 * vt;
-  double dwb = D3b * a3 + D4b * a3 * wt;
-  double dVnb = -a3 * (D1b * nx + D2b * ny + D3b * nz + D4b * Vnt);
-  double ctb = d51b * (a5 - a1);
-  const double a1b = a15b - d51b * ct;
-  const double a5b = a15b + d51b * ct;
-  double l1b = 0, l2b = 0, l5b = 0, rtb = 0, drb = 0, dPb = 0, ic2b = 0, hic2b = 0, rcdb = 0;
+  const T D0b = -G0, D1b = -G1, D2b = -G2, D3b = -G3, D4b = -G4;
+  const T a15b = D0b + D1b * ut + D2b * vt + D3b * wt + D4b * ht;
+  const T d51b = D1b * nx + D2b * ny + D3b * nz + D4b * Vnt;
+  const T a2b = D0b + D1b * ut + D2b * vt + D3b * wt + D4b * q2h;
+  const T a3b = D1b * (du - nx * dVn) + D2b * (dv - ny * dVn) + D3b * (dw - nz * dVn) + D4b * E4;
+  T utb = D1b * (a15 + a2) + D4b * a3 * du;
+  T vtb = D2b * (a15 + a2) + D4b * a3 * dv;
+  T wtb = D3b * (a15 + a2) + D4b * a3 * dw;
+  T htb = D4b * a15;
+  T Vntb = D4b * (d51 - a3 * dVn);
+  T q2hb = D4b * a2;
+  T dub = D1b * a3 + D4b * a3 * ut;
+  T dvb = D2b * a3 + D4b * a3 * vt;
+  T dwb = D3b * a3 + D4b * a3 * wt;
+  T dVnb = -a3 * (D1b * nx + D2b * ny + D3b * nz + D4b * Vnt);
+  T ctb = d51b * (a5 - a1);
+  const T a1b = a15b - d51b * ct;
+  const T a5b = a15b + d51b * ct;
+  T l1b = S::c(0.0), l2b = S::c(0.0), l5b = S::c(0.0), rtb = S::c(0.0), drb = S::c(0.0), dPb = S::c(0.0), ic2b = S::c(0.0), hic2b = S::c(0.0), rcdb = S::c(0.0);
   l2b += a3b * rt; rtb += a3b * l2;
   l2b += a2b * (dr - dP * ic2); drb += a2b * l2; dPb += -a2b * l2 * ic2; ic2b += -a2b * l2 * dP;
   l5b += a5b * (dP + rcd) * hic2; dPb += a5b * l5 * hic2; rcdb += a5b * l5 * hic2; hic2b += a5b * l5 * (dP + rcd);
   l1b += a1b * (dP - rcd) * hic2; dPb += a1b * l1 * hic2; rcdb += -a1b * l1 * hic2; hic2b += a1b * l1 * (dP - rcd);
-  ic2b += 0.5 * hic2b;
+  ic2b += S::halve(hic2b);
   rtb += rcdb * ct * dVn; ctb += rcdb * rt * dVn; dVnb += rcdb * rt * ct;
   // eigenvalue magnitudes with the entropy fix (delta = harten * ct)
-  double deltab = l1b * d1d + l2b * d2d + l5b * d5d;
-  const double la1b = l1b * d1l, la2b = l2b * d2l, la5b = l5b * d5l;
+  T deltab = l1b * d1d + l2b * d2d + l5b * d5d;
+  const T la1b = l1b * d1l, la2b = l2b * d2l, la5b = l5b * d5l;
   ctb += deltab * P.harten;
-  const double x1b = la1b * (x1 < 0 ? -1.0 : 1.0);
-  const double x2b = la2b * (x2 < 0 ? -1.0 : 1.0);
-  const double x5b = la5b * (x5 < 0 ? -1.0 : 1.0);
+  const T x1b = la1b * sgn(x1);
+  const T x2b = la2b * sgn(x2);
+  const T x5b = la5b * sgn(x5);
   Vntb += x1b + x2b + x5b;
   ctb += -x1b + x5b;
   // jumps
@@ -214,19 +268,19 @@ FVA_HD void face_vjp(const AdjParams& P, const double q[4][5], double nx, double
   VnRb += dVnb; VnLb -= dVnb;
   // Roe-averaged normal velocity and sound speed
   utb += nx * Vntb; vtb += ny * Vntb; wtb += nz * Vntb;
-  double c2b = -ic2b * ic2 * ic2 + ctb / (2.0 * ct);
+  T c2b = -ic2b * ic2 * ic2 + S::halve(ctb * S::rcp(ct));
   htb += P.gm1 * c2b;
   q2hb += -P.gm1 * c2b;
   utb += q2hb * ut; vtb += q2hb * vt; wtb += q2hb * wt;
-  double Rtb = 0, w1b = 0;
+  T Rtb = S::c(0.0), w1b = S::c(0.0);
   uLb += utb * w1; uRb += utb * Rt * w1; Rtb += utb * uR * w1; w1b += utb * (uL + Rt * uR);
   vLb += vtb * w1; vRb += vtb * Rt * w1; Rtb += vtb * vR * w1; w1b += vtb * (vL + Rt * vR);
   wLb += wtb * w1; wRb += wtb * Rt * w1; Rtb += wtb * wR * w1; w1b += wtb * (wL + Rt * wR);
   hLb += htb * w1; hRb += htb * Rt * w1; Rtb += htb * hR * w1; w1b += htb * (hL + Rt * hR);
   Rtb += -w1b * w1 * w1;
   rLb += rtb * Rt; Rtb += rtb * rL;
-  const double zb = Rtb / (2.0 * Rt);
-  double riLb = zb * rR, riRb = 0;
+  const T zb = S::halve(Rtb * S::rcp(Rt));
+  T riLb = zb * rR, riRb = S::c(0.0);
   rRb += zb * riL;
   // mass fluxes and enthalpies
   rLb += mLb * VnL; VnLb += mLb * rL;
@@ -240,22 +294,20 @@ FVA_HD void face_vjp(const AdjParams& P, const double q[4][5], double nx, double
   uLb += nx * VnLb; vLb += ny * VnLb; wLb += nz * VnLb;
   uRb += nx * VnRb; vRb += ny * VnRb; wRb += nz * VnRb;
   // MUSCL reverse
-  const double VLb[5] = {rLb, uLb, vLb, wLb, pLb};
-  const double VRb[5] = {rRb, uRb, vRb, wRb, pRb};
-  double Vb[4][5];
+  const T VLb[5] = {rLb, uLb, vLb, wLb, pLb};
+  const T VRb[5] = {rRb, uRb, vRb, wRb, pRb};
+  T Vb[4][5];
+#pragma unroll
   for (int n = 0; n < 5; ++n) {
-    double d0b = 0, dmb = 0, dpb = 0;
-    const double Lb = VLb[n], Rb = VRb[n];
-    // VL = V1 + e4km phi(d0, dm) + e4kp phi(dm, d0)
-    d0b += Lb * P.e4km * pa[n][0]; dmb += Lb * P.e4km * pb[n][0];
-    dmb += Lb * P.e4kp * pa[n][1]; d0b += Lb * P.e4kp * pb[n][1];
-    // VR = V2 - e4kp phi(dp, d0) - e4km phi(d0, dp)
-    dpb += -Rb * P.e4kp * pa[n][2]; d0b += -Rb * P.e4kp * pb[n][2];
-    d0b += -Rb * P.e4km * pa[n][3]; dpb += -Rb * P.e4km * pb[n][3];
+    const T Lb = VLb[n], Rb = VRb[n];
+    const T d0b = Lb * jL0[n] + Rb * jR0[n];
+    const T dmb = Lb * jLm[n];
+    const T dpb = Rb * jRp[n];
     Vb[0][n] = -dmb;
     Vb[1][n] = Lb + dmb - d0b;
     Vb[2][n] = Rb + d0b - dpb;
     Vb[3][n] = dpb;
   }
-  for (int c = 0; c < 4; ++c) prim_bwd(P, q[c], s[c], Vb[c], qb[c]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) prim_bwd(P, s[c], Vb[c], qb[c]);
 }

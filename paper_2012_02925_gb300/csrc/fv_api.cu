@@ -34,6 +34,8 @@ struct fv_ctx {
   FvLaunch launch{};
   FvConnDev* d_conns = nullptr;
   long long conn_items = 0;
+  FvXchTile* d_xtiles = nullptr;    // exchange kernel work units of d_conns
+  int nxtiles = 0;
   double* buf[3] = {nullptr, nullptr, nullptr};
   long long state_elems = 0;        // internal layout, doubles per buffer
   long long ext_state_elems = 0;    // packed ghosted layout
@@ -52,6 +54,7 @@ struct fv_ctx {
   double* adj_contrib = nullptr;    // adjoint: per-face input cotangents (20 per face)
   double* adj_lamg = nullptr;       // adjoint: ghosted cotangent of Q^(m-1)
   double* adj_qx = nullptr;         // adjoint: X(Q^(m-1)), the exchanged stage input
+  int adj_df64 = 0;                 // adjoint face VJPs in double-float arithmetic (fv_set_adjoint_arith)
   std::vector<FvConnDev> hconns;
   // cross-device halo slabs (fv_set_halo): send = this device's donor side,
   // recv = this device's ghost side; item offsets count slab items
@@ -59,6 +62,9 @@ struct fv_ctx {
   FvConnDev* d_hrecv = nullptr;
   int nhsend = 0, nhrecv = 0;
   long long hsend_items = 0, hrecv_items = 0;
+  FvXchTile* d_hstiles = nullptr;   // their exchange kernel work units
+  FvXchTile* d_hrtiles = nullptr;
+  int nhstiles = 0, nhrtiles = 0;
   std::vector<fv_bc_patch> bcs;     // physical boundary patches as set
   FvBcDev* d_bcs = nullptr;
   int nbc = 0;
@@ -231,72 +237,119 @@ __global__ void split_kernel(const double* in, float2* out, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// ghost exchange: work item = (connection, tangential a, b, depth d), a
-// fastest.  XCH_COPY: dst ghost <- src donor, both blocks on this device
-// (Section 2, Section 4).  Across devices (Section 7.2 V1, pack/unpack) the
-// same item order splits into halves: XCH_PACK writes the donor cells of
-// this device's src blocks into a contiguous slab buffer, XCH_UNPACK writes
-// a received slab buffer into this device's dst ghosts.  Connection c's slab
-// occupies buf[5*item_off, 5*(item_off + n_c)), variable-major (n_c = 2 L0 L1
-// items: the 5 values of item x at x, x + n_c, ...).
+// ghost exchange.  A connection's items are (tangential a, b, depth d), a
+// fastest; item (a, b, d) takes the ghost cell at depth d of the dst patch
+// position (a, b) from the src interior cell at depth d under the signed
+// tangential axis map.  XCH_COPY: dst ghost <- src donor, both blocks on
+// this device (Section 2, Section 4).  Across devices (Section 7.2 V1,
+// pack/unpack) the same items split into halves: XCH_PACK writes the donor
+// cells of this device's src blocks into a contiguous slab buffer,
+// XCH_UNPACK writes a received slab buffer into this device's dst ghosts.
+// Connection c's slab occupies buf[5*item_off, 5*(item_off + n_c)),
+// variable-major (n_c = 2 L0 L1 items: the 5 values of item x at x,
+// x + n_c, ...).
+//
+// One CTA per tile of FV_XCH_TA x FV_XCH_TB positions and both depths
+// (FvXchTile): it reads the tile's donor cells in the src block's memory
+// order into shared memory and writes the ghosts in the dst block's order,
+// so both sides run along i: the tangential axis that maps to i (a or b,
+// through the axis map), or, on a face normal to i, the depth pair (two
+// adjacent cells).  Slab buffers are read and written in item order.
 // ---------------------------------------------------------------------------
 enum { XCH_COPY = 0, XCH_PACK = 1, XCH_UNPACK = 2 };
 
+// memory-contiguous index of a side: 0 = a, 1 = b, 2 = depth
+__device__ __forceinline__ int xch_fast_dst(const FvConnDev& c) { return (c.dst_face >> 1) == 0 ? 2 : 0; }
+__device__ __forceinline__ int xch_fast_src(const FvConnDev& c) {
+  if ((c.src_face >> 1) == 0) return 2;
+  return ((c.t0 < 0 ? -c.t0 : c.t0) == 1) ? 0 : 1;   // the item axis that maps to src tangential axis 0 = i
+}
+
+// t -> (a, b, d - 1) of a TA x TB x 2 tile with index `fast` fastest, then
+// the others in (a, b, depth) order
+__device__ __forceinline__ void xch_order(int t, int fast, int& a, int& b, int& d) {
+  constexpr int TA = FV_XCH_TA, TB = FV_XCH_TB;
+  if (fast == 0) { a = t % TA; b = (t / TA) % TB; d = t / (TA * TB); }
+  else if (fast == 1) { b = t % TB; a = (t / TB) % TA; d = t / (TA * TB); }
+  else { d = t & 1; a = (t >> 1) % TA; b = (t >> 1) / TA; }
+}
+
+__device__ __forceinline__ long long xch_dst_index(const FvBlockDev& D, const FvConnDev& c, int a, int b, int d) {
+  const int da = c.dst_face >> 1;
+  const int dext[3] = {D.ni, D.nj, D.nk};
+  int dc[3];
+  const int dt0 = da == 0 ? 1 : 0, dt1 = da == 2 ? 1 : 2;
+  dc[dt0] = c.dlo0 + a;
+  dc[dt1] = c.dlo1 + b;
+  dc[da] = (c.dst_face & 1) ? dext[da] - 1 + d : -d;
+  return D.qoff + (long long)(dc[2] + 2) * D.kstride + (long long)(dc[1] + 2) * D.jstride + (dc[0] + 2);
+}
+
+__device__ __forceinline__ long long xch_src_index(const FvBlockDev& S, const FvConnDev& c, int a, int b, int d) {
+  const int sa = c.src_face >> 1;
+  const int sext[3] = {S.ni, S.nj, S.nk};
+  int sc[3];
+  const int st0 = sa == 0 ? 1 : 0, st1 = sa == 2 ? 1 : 2;
+  int st[2] = {c.slo0, c.slo1};
+  const int u0 = (c.t0 < 0 ? -c.t0 : c.t0) - 1, u1 = (c.t1 < 0 ? -c.t1 : c.t1) - 1;
+  st[u0] += c.t0 > 0 ? a : -a;
+  st[u1] += c.t1 > 0 ? b : -b;
+  sc[st0] = st[0];
+  sc[st1] = st[1];
+  sc[sa] = (c.src_face & 1) ? sext[sa] - d : d - 1;
+  return S.qoff + (long long)(sc[2] + 2) * S.kstride + (long long)(sc[1] + 2) * S.jstride + (sc[0] + 2);
+}
+
 template <int MODE>
-__global__ void exchange_kernel(const FvBlockDev* __restrict__ blocks, const FvConnDev* __restrict__ conns, int nconn,
-                                long long nitems, double* q, double* buf) {
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nitems;
-       it += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nconn - 1;
-    while (lo < hi) {               // last connection with item_off <= it
-      const int mid = (lo + hi + 1) >> 1;
-      if (conns[mid].item_off <= it) lo = mid; else hi = mid - 1;
+__global__ void __launch_bounds__(256) exchange_kernel(const FvBlockDev* __restrict__ blocks,
+                                                       const FvConnDev* __restrict__ conns,
+                                                       const FvXchTile* __restrict__ tiles, double* q, double* buf) {
+  constexpr int TA = FV_XCH_TA, TB = FV_XCH_TB, N = 2 * TA * TB;
+  // [b][a][depth], a row padded by one position against bank conflicts
+  __shared__ double tile_v[TB * (TA + 1) * 2];
+  const FvXchTile T = tiles[blockIdx.x];
+  const FvConnDev c = conns[T.conn];
+  const long long nc = 2LL * c.L0 * c.L1;
+  const int fs = MODE == XCH_UNPACK ? 0 : xch_fast_src(c);
+  const int fd = MODE == XCH_PACK ? 0 : xch_fast_dst(c);
+  const FvBlockDev* S = MODE == XCH_UNPACK ? nullptr : &blocks[c.src_block];
+  const FvBlockDev* D = MODE == XCH_PACK ? nullptr : &blocks[c.dst_block];
+  for (int v = 0; v < 5; ++v) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      int a, b, d;
+      xch_order(t, fs, a, b, d);
+      const int ga = T.a0 + a, gb = T.b0 + b;
+      if (ga >= c.L0 || gb >= c.L1) continue;
+      double x;
+      if (MODE == XCH_UNPACK)
+        x = buf[5 * c.item_off + v * nc + ga + (long long)c.L0 * (gb + (long long)c.L1 * d)];
+      else
+        x = q[xch_src_index(*S, c, ga, gb, d + 1) + v * S->plane];
+      tile_v[(b * (TA + 1) + a) * 2 + d] = x;
     }
-    const FvConnDev c = conns[lo];
-    long long local = it - c.item_off;
-    const long long li = local;
-    const int a = (int)(local % c.L0);
-    local /= c.L0;
-    const int b = (int)(local % c.L1);
-    const int d = (int)(local / c.L1) + 1;
-    long long di = 0, si = 0, dplane = 0, splane = 0;
-    if (MODE != XCH_PACK) {
-      const FvBlockDev& D = blocks[c.dst_block];
-      const int da = c.dst_face >> 1;
-      const int dext[3] = {D.ni, D.nj, D.nk};
-      int dc[3];
-      const int dt0 = da == 0 ? 1 : 0, dt1 = da == 2 ? 1 : 2;
-      dc[dt0] = c.dlo0 + a;
-      dc[dt1] = c.dlo1 + b;
-      dc[da] = (c.dst_face & 1) ? dext[da] - 1 + d : -d;
-      di = D.qoff + (long long)(dc[2] + 2) * D.kstride + (long long)(dc[1] + 2) * D.jstride + (dc[0] + 2);
-      dplane = D.plane;
+    __syncthreads();
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      int a, b, d;
+      xch_order(t, fd, a, b, d);
+      const int ga = T.a0 + a, gb = T.b0 + b;
+      if (ga >= c.L0 || gb >= c.L1) continue;
+      const double x = tile_v[(b * (TA + 1) + a) * 2 + d];
+      if (MODE == XCH_PACK)
+        buf[5 * c.item_off + v * nc + ga + (long long)c.L0 * (gb + (long long)c.L1 * d)] = x;
+      else
+        q[xch_dst_index(*D, c, ga, gb, d + 1) + v * D->plane] = x;
     }
-    if (MODE != XCH_UNPACK) {
-      const FvBlockDev& S = blocks[c.src_block];
-      const int sa = c.src_face >> 1;
-      const int sext[3] = {S.ni, S.nj, S.nk};
-      int sc[3];
-      const int st0 = sa == 0 ? 1 : 0, st1 = sa == 2 ? 1 : 2;
-      int st[2] = {c.slo0, c.slo1};
-      const int u0 = (c.t0 < 0 ? -c.t0 : c.t0) - 1, u1 = (c.t1 < 0 ? -c.t1 : c.t1) - 1;
-      st[u0] += c.t0 > 0 ? a : -a;
-      st[u1] += c.t1 > 0 ? b : -b;
-      sc[st0] = st[0];
-      sc[st1] = st[1];
-      sc[sa] = (c.src_face & 1) ? sext[sa] - d : d - 1;
-      si = S.qoff + (long long)(sc[2] + 2) * S.kstride + (long long)(sc[1] + 2) * S.jstride + (sc[0] + 2);
-      splane = S.plane;
-    }
-    const long long nc = 2LL * c.L0 * c.L1;
-    double* slab = buf + 5 * c.item_off + li;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      if (MODE == XCH_COPY) q[di + v * dplane] = q[si + v * splane];
-      if (MODE == XCH_PACK) slab[v * nc] = q[si + v * splane];
-      if (MODE == XCH_UNPACK) q[di + v * dplane] = slab[v * nc];
-    }
+    __syncthreads();
   }
+}
+
+// the tiles of a connection table, connection by connection
+std::vector<FvXchTile> xch_tiles(const std::vector<FvConnDev>& cd) {
+  std::vector<FvXchTile> out;
+  for (int c = 0; c < (int)cd.size(); ++c)
+    for (int b0 = 0; b0 < cd[c].L1; b0 += FV_XCH_TB)
+      for (int a0 = 0; a0 < cd[c].L0; a0 += FV_XCH_TA) out.push_back(FvXchTile{c, a0, b0, 0});
+  return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -621,16 +674,12 @@ struct StageVariant {
 };
 StageVariant stage_variant(const fv_ctx* h) {
 #define FV_VARIANT_ENTRY(NAME) {fv_launch_stage_##NAME, fv_stage_occupancy_##NAME},
-  // in FV_STAGE_VARIANTS order: [form][fast][visc][bc], binary64 without fast
+  // in FV_STAGE_VARIANTS order: [form][fast][visc][bc]
   static const StageVariant table[] = {FV_STAGE_VARIANTS(FV_VARIANT_ENTRY)};
 #undef FV_VARIANT_ENTRY
   const FvLaunch& l = h->launch;
-  const int tail = (l.visc ? 2 : 0) + (l.bc ? 1 : 0);
-  switch (h->cfg.precision) {
-    case FV_PREC_FP64: return table[tail];
-    case FV_PREC_DF64: return table[4 + (l.fast ? 4 : 0) + tail];
-    default: return table[12 + (l.fast ? 4 : 0) + tail];
-  }
+  const int form = h->cfg.precision == FV_PREC_FP64 ? 0 : (h->cfg.precision == FV_PREC_DF64 ? 1 : 2);
+  return table[8 * form + (l.fast ? 4 : 0) + (l.visc ? 2 : 0) + (l.bc ? 1 : 0)];
 }
 
 int launch_stage(fv_ctx* h, const FvStageArgs& a, cudaStream_t s) {
@@ -697,9 +746,8 @@ int stage_out(const fv_ctx* h, int m) {
 // connections first, then the physical boundaries
 int do_exchange(fv_ctx* h, double* q, cudaStream_t s) {
   const int threads = 256;
-  if (h->conn_items) {
-    exchange_kernel<XCH_COPY><<<grid_for(h->conn_items, threads, h->nsm), threads, 0, s>>>(
-        h->d_blocks, h->d_conns, h->nconn, h->conn_items, q, nullptr);
+  if (h->nxtiles) {
+    exchange_kernel<XCH_COPY><<<h->nxtiles, threads, 0, s>>>(h->d_blocks, h->d_conns, h->d_xtiles, q, nullptr);
     CK(h, cudaGetLastError());
   }
   if (h->bc_items) {
@@ -810,7 +858,7 @@ void choose_launch(fv_ctx* h) {
   l.tx = FV_SHAPE_TABLE[shape - 1][0];
   l.ty = FV_SHAPE_TABLE[shape - 1][1];
   l.threads = FV_SHAPE_TABLE[shape - 1][2];
-  l.fast = c.precision != FV_PREC_FP64 && fv_default_scheme(c.flux, c.limiter, c.eps, c.kappa, c.harten, c.fix_all);
+  l.fast = fv_default_scheme(c.flux, c.limiter, c.eps, c.kappa, c.harten, c.fix_all);
   // viscous kernels: the binary32 form fuses the viscous faces into the
   // stage kernel (its T on the fly costs a MUFU reciprocal); for binary64
   // and double-float a separate kernel measured faster, and their _visc
@@ -1261,6 +1309,10 @@ int fv_create_blocks(const fv_block_desc* blocks, int nblocks, const fv_connecti
     h->hconns = cd;
     CK(hp, cudaMalloc(&h->d_conns, sizeof(FvConnDev) * nconn));
     CK(hp, cudaMemcpy(h->d_conns, cd.data(), sizeof(FvConnDev) * nconn, cudaMemcpyHostToDevice));
+    const std::vector<FvXchTile> xt = xch_tiles(cd);
+    h->nxtiles = (int)xt.size();
+    CK(hp, cudaMalloc(&h->d_xtiles, sizeof(FvXchTile) * xt.size()));
+    CK(hp, cudaMemcpy(h->d_xtiles, xt.data(), sizeof(FvXchTile) * xt.size(), cudaMemcpyHostToDevice));
   }
   // ---- viscous-term tables ----
   if (cfg->visc) {
@@ -1323,7 +1375,7 @@ int fv_destroy(fv_handle hh) {
   cudaFree(h->scratch_r); cudaFree(h->partials); cudaFree(h->d_norm); cudaFree(h->stage_buf);
   cudaFree(h->adj_contrib); cudaFree(h->adj_lamg); cudaFree(h->adj_qx);
   cudaFree(h->d_bcs); cudaFree(h->d_bcmap);
-  cudaFree(h->d_hsend); cudaFree(h->d_hrecv);
+  cudaFree(h->d_hsend); cudaFree(h->d_hrecv); cudaFree(h->d_hstiles); cudaFree(h->d_hrtiles); cudaFree(h->d_xtiles);
   cudaFree(h->geo_t);
   cudaFree(h->geo); cudaFree(h->d_vtiles); cudaFree(h->d_edges);
   cudaFree(h->rmon); cudaFree(h->mon_partials); cudaFree(h->mon_norm);
@@ -1776,9 +1828,10 @@ int fv_set_halo(fv_handle hh, const fv_connection* send, int nsend, const fv_con
     }
   }
   CK(h, cudaDeviceSynchronize());
-  cudaFree(h->d_hsend); cudaFree(h->d_hrecv);
+  cudaFree(h->d_hsend); cudaFree(h->d_hrecv); cudaFree(h->d_hstiles); cudaFree(h->d_hrtiles);
   h->d_hsend = h->d_hrecv = nullptr;
-  h->nhsend = h->nhrecv = 0;
+  h->d_hstiles = h->d_hrtiles = nullptr;
+  h->nhsend = h->nhrecv = h->nhstiles = h->nhrtiles = 0;
   h->hsend_items = h->hrecv_items = 0;
   for (int side = 0; side < 2; ++side) {
     const fv_connection* tab = side ? recv : send;
@@ -1803,6 +1856,11 @@ int fv_set_halo(fv_handle hh, const fv_connection* send, int nsend, const fv_con
     CK(h, cudaMemcpy(*dst, cd.data(), sizeof(FvConnDev) * n, cudaMemcpyHostToDevice));
     (side ? h->nhrecv : h->nhsend) = n;
     (side ? h->hrecv_items : h->hsend_items) = items;
+    const std::vector<FvXchTile> xt = xch_tiles(cd);
+    FvXchTile** tdst = side ? &h->d_hrtiles : &h->d_hstiles;
+    CK(h, cudaMalloc(tdst, sizeof(FvXchTile) * xt.size()));
+    CK(h, cudaMemcpy(*tdst, xt.data(), sizeof(FvXchTile) * xt.size(), cudaMemcpyHostToDevice));
+    (side ? h->nhrtiles : h->nhstiles) = (int)xt.size();
   }
   return FV_OK;
 }
@@ -1819,8 +1877,8 @@ int fv_halo_pack(fv_handle hh, int buffer, double* send_dev, void* stream) {
   if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
   if (!h->hsend_items) return FV_OK;
   if (!send_dev) return fail(h, FV_ERR_INVALID_ARG, "send_dev is NULL");
-  exchange_kernel<XCH_PACK><<<grid_for(h->hsend_items, 256, h->nsm), 256, 0, (cudaStream_t)stream>>>(
-      h->d_blocks, h->d_hsend, h->nhsend, h->hsend_items, h->buf[buffer], send_dev);
+  exchange_kernel<XCH_PACK><<<h->nhstiles, 256, 0, (cudaStream_t)stream>>>(h->d_blocks, h->d_hsend, h->d_hstiles,
+                                                                             h->buf[buffer], send_dev);
   CK(h, cudaGetLastError());
   return FV_OK;
 }
@@ -1831,8 +1889,8 @@ int fv_halo_unpack(fv_handle hh, int buffer, const double* recv_dev, void* strea
   if (buffer < 0 || buffer > 2) return fail(h, FV_ERR_INVALID_ARG, "buffer must be 0, 1 or 2");
   if (!h->hrecv_items) return FV_OK;
   if (!recv_dev) return fail(h, FV_ERR_INVALID_ARG, "recv_dev is NULL");
-  exchange_kernel<XCH_UNPACK><<<grid_for(h->hrecv_items, 256, h->nsm), 256, 0, (cudaStream_t)stream>>>(
-      h->d_blocks, h->d_hrecv, h->nhrecv, h->hrecv_items, h->buf[buffer], const_cast<double*>(recv_dev));
+  exchange_kernel<XCH_UNPACK><<<h->nhrtiles, 256, 0, (cudaStream_t)stream>>>(
+      h->d_blocks, h->d_hrecv, h->d_hrtiles, h->buf[buffer], const_cast<double*>(recv_dev));
   CK(h, cudaGetLastError());
   return FV_OK;
 }
@@ -1849,6 +1907,15 @@ int fv_get_launch(fv_handle hh, int* out4) {
   out4[1] = h->cfg.kchunk;
   out4[2] = h->ntiles;
   out4[3] = h->launch.grid;
+  return FV_OK;
+}
+
+int fv_set_adjoint_arith(fv_handle hh, int precision) {
+  if (!hh) return FV_ERR_INVALID_ARG;
+  fv_ctx* h = H(hh);
+  if (precision != FV_PREC_FP64 && precision != FV_PREC_DF64)
+    return fail(h, FV_ERR_INVALID_ARG, "adjoint arithmetic must be FV_PREC_FP64 or FV_PREC_DF64");
+  h->adj_df64 = precision == FV_PREC_DF64;
   return FV_OK;
 }
 
@@ -1895,7 +1962,7 @@ int fv_adjoint_vjp(fv_handle hh, int stage, double dt, const double* qin_dev, co
     const FvBlockDev& B = h->hb[b];
     for (int d = 0; d < nd; ++d)
       if (fv_adjoint_faces(B, d, qx, lam_out_dev, h->invvol, alpha_dt, (const double*)h->metric[d], h->nfaces[d],
-                           a.fp, cdir[d] + 20 * coff[3 * b + d], s))
+                           a.fp, h->adj_df64, cdir[d] + 20 * coff[3 * b + d], s))
         return cuda_fail(h, cudaGetLastError(), "adjoint face kernel");
   }
   for (size_t b = 0; b < h->hb.size(); ++b) {

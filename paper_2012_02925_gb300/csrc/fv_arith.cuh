@@ -122,6 +122,8 @@ FV_HD df64 operator*(df64 a, float b) {
   return quick_two_sum(p.hi, e);
 }
 FV_HD df64 operator*(float b, df64 a) { return a * b; }
+FV_HD df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+FV_HD df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
 
 // sum_i a_i b_i with one renormalisation at the end (a compensated dot
 // product after Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM
@@ -265,6 +267,10 @@ template <> struct Sc<double> {
   static __device__ __forceinline__ bool lt_nonneg(double a, double b) {
     return __double_as_longlong(a) < __double_as_longlong(b);
   }
+  static __device__ __forceinline__ bool neg(double a) {
+    const long long b = __double_as_longlong(a);
+    return b < 0 && (b & 0x7fffffffffffffffLL) != 0;   // below zero (not -0)
+  }
   using mask = bool;
   static __device__ __forceinline__ double sel(bool m, double a, double b) { return m ? a : b; }
   static __device__ __forceinline__ bool ge(double a, float t) { return a >= (double)t; }
@@ -298,6 +304,7 @@ template <> struct Sc<float> {
   static __device__ __forceinline__ float hi(float x) { return x; }
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ bool lt_nonneg(float a, float b) { return a < b; }
+  static __device__ __forceinline__ bool neg(float a) { return a < 0.0f; }
   static __device__ __forceinline__ bool pos(float a) { return a > 0.0f; }
   static __device__ __forceinline__ bool above(float a, float t) { return a > t; }
   using mask = bool;
@@ -337,6 +344,7 @@ template <> struct Sc<df64> {
   static __device__ __forceinline__ float hi(df64 x) { return x.hi; }
   static __device__ __forceinline__ bool lt(df64 a, df64 b) { return a < b; }
   static __device__ __forceinline__ bool lt_nonneg(df64 a, df64 b) { return a < b; }
+  static __device__ __forceinline__ bool neg(df64 a) { return a.hi < 0.0f; }
   static __device__ __forceinline__ bool pos(df64 a) { return a.hi > 0.0f; }
   static __device__ __forceinline__ bool above(df64 a, float t) { return a.hi > t; }
   using mask = bool;

@@ -42,6 +42,13 @@ struct FvConnDev {
   long long item_off;           // first work item (a, b, depth) of this connection
 };
 
+// One unit of work of the exchange kernel: items a0..a0+FV_XCH_TA-1 x
+// b0..b0+FV_XCH_TB-1 (both depths) of connection `conn`, clipped to its patch.
+struct FvXchTile {
+  int conn, a0, b0, pad_;
+};
+constexpr int FV_XCH_TA = 32, FV_XCH_TB = 16;
+
 // Physical boundary kinds as the kernels see them (the values of fv_bc_kind).
 constexpr int FV_BCK_FIXED = 0, FV_BCK_SUPERSONIC_INFLOW = 1, FV_BCK_EXTRAPOLATE = 2, FV_BCK_SLIP_WALL = 3,
               FV_BCK_FARFIELD = 4, FV_BCK_NOSLIP_WALL = 5;
@@ -118,14 +125,15 @@ inline bool fv_default_scheme(int flux, int limiter, double eps, double kappa, d
 }
 
 // Stage kernel variants, fv_stage_<name>.cu each: the form (fp64, df64,
-// fp32 = binary32 flux), _fast = default scheme compiled in (not binary64),
+// fp32 = binary32 flux), _fast = default scheme compiled in,
 // _visc = laminar viscous terms, _bc = boundary-face flux overwrites.
 // launch: enqueue on a stream; occupancy: CTAs per SM for the launch's tile
 // shape (0 = shape not compiled) and its dynamic shared memory.
 #define FV_STAGE_VARIANTS(X)                                                                  \
-  X(fp64) X(fp64_bc) X(fp64_visc) X(fp64_visc_bc) X(df64) X(df64_bc) X(df64_visc) X(df64_visc_bc) \
-  X(df64_fast) X(df64_fast_bc) X(df64_fast_visc) X(df64_fast_visc_bc) X(fp32) X(fp32_bc)      \
-  X(fp32_visc) X(fp32_visc_bc) X(fp32_fast) X(fp32_fast_bc) X(fp32_fast_visc) X(fp32_fast_visc_bc)
+  X(fp64) X(fp64_bc) X(fp64_visc) X(fp64_visc_bc) X(fp64_fast) X(fp64_fast_bc) X(fp64_fast_visc)  \
+  X(fp64_fast_visc_bc) X(df64) X(df64_bc) X(df64_visc) X(df64_visc_bc) X(df64_fast) X(df64_fast_bc) \
+  X(df64_fast_visc) X(df64_fast_visc_bc) X(fp32) X(fp32_bc) X(fp32_visc) X(fp32_visc_bc) X(fp32_fast) \
+  X(fp32_fast_bc) X(fp32_fast_visc) X(fp32_fast_visc_bc)
 #define FV_DECLARE_STAGE_VARIANT(NAME)                                                       \
   int fv_launch_stage_##NAME(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s);     \
   int fv_stage_occupancy_##NAME(const FvLaunch& l, size_t* smem_bytes);
@@ -138,10 +146,11 @@ constexpr int FV_SHAPE_TABLE[FV_NUM_SHAPES][4] = {{32, 8, 256, 0}, {32, 4, 128, 
                                                   {30, 8, 256, 0}, {32, 8, 288, 0}, {32, 8, 256, 1},
                                                   {32, 4, 128, 1}, {32, 7, 256, 0}};
 
-// Discrete-adjoint kernels (fv_adjoint.cu), binary64 only.
+// Discrete-adjoint kernels (fv_adjoint.cu): binary64 data; the face VJPs in
+// binary64 (double_float = 0) or double-float arithmetic.
 int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const double* lam_out, const double* invvol,
                      double alpha_dt, const double* metric, long long mstride, const FvFaceParams& fp,
-                     double* contrib, cudaStream_t s);
+                     int double_float, double* contrib, cudaStream_t s);
 int fv_adjoint_gather(const FvBlockDev& B, const double* cx, const double* cy, const double* cz, int three_d,
                       double* lamg, cudaStream_t s);
 int fv_adjoint_transpose(const FvBlockDev* d_blocks, const FvConnDev& c, double* lamg, cudaStream_t s);
