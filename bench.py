@@ -135,16 +135,18 @@ def workload_ns(base: str):
     return pb
 
 
-def algorithmic_bytes(pb, stage: int, curvilinear: bool) -> float:
+def algorithmic_bytes(pb, stage: int, curvilinear: bool, precision: str = "fp64") -> float:
     """Bytes a cell-update must move at least: read Q^(m-1) (40 B), read Q^(0)
-    for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics 24 B per
-    face family (3 in 3D, 2 in 2D) + 8 B of 1/Omega; a source term 40 B;
-    exchanged ghost cells read and write 80 B each; a physical boundary
-    position writes its two ghost layers and reads one interior cell (120 B)."""
+    for stages > 1 (40 B), write Q^(m) (40 B); curvilinear metrics - the face
+    vector of each face family (3 in 3D, 2 in 2D) in the form's storage, 24 B
+    (binary64, or a pair of binary32 per value) or 12 B (the binary32-flux
+    form) - and 8 B of 1/Omega; a source term 40 B; exchanged ghost cells
+    read and write 80 B each; a physical boundary position writes its two
+    ghost layers and reads one interior cell (120 B)."""
     n = pb.ncells
     per = 80.0 + (40.0 if stage > 1 else 0.0)
     if curvilinear:
-        per += 24.0 * pb.dim + 8.0
+        per += (12.0 if precision == "fp32flux" else 24.0) * pb.dim + 8.0
     if pb.source is not None:
         per += 40.0
     if pb.params.get("visc", 0):
@@ -330,7 +332,7 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
     bandwidth.  The HBM fraction is reported for every form."""
     M = len(stage_times)
     kt = [max(t - ex_time, 1e-12) for t in stage_times]
-    byts = [algorithmic_bytes(pb, m + 1, curvilinear) for m in range(M)]
+    byts = [algorithmic_bytes(pb, m + 1, curvilinear, precision) for m in range(M)]
     gbs = sum(byts) / sum(kt) / 1e9
     hbm = pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     r = {"kernel": "fv_stage_kernel<%s>" % precision, "bytes_per_launch": sum(byts) / M,
@@ -789,11 +791,18 @@ def main():
     ap.add_argument("--variant-precisions", default="fp64,df64,fp32flux")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--peaks", action="store_true")
+    ap.add_argument("--adjoint", action="store_true", help="the adjoint workload's line only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.peaks:
         run_peaks()
+    elif args.adjoint:
+        import torch
+        import paper_2012_02925_gb300 as fv
+        torch.cuda.set_device(0)
+        pk, kind = peaks()
+        print(json.dumps({"adjoint": sig(run_adjoint(rates=fv.probe_alu_rates(), pk=pk, peak_kind=kind))}))
     elif args.impl == "reference":
         run_reference(args)
     else:
