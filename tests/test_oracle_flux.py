@@ -225,11 +225,30 @@ def test_muscl_extremum_is_first_order():
 
 
 def test_primitive_recovery():
-    q = np.array([1.2, 0.36, -0.24, 0.3, 2.5])
-    V = oracle.cons_to_prim(q)
-    u = q[1:4] / q[0]
-    assert np.allclose(V[:4], [1.2, *u], rtol=1e-15)
-    assert V[4] == pytest.approx(0.4 * (2.5 - 0.5 * 1.2 * (u @ u)), rel=1e-15)
+    """Primitive recovery (Section 2: V from Q) against facts fixed outside
+    the oracle: it inverts the seeded generators' own conserved map
+    (cases.prim_to_cons, rho E = p/(gamma-1) + rho |u|^2/2) on random states;
+    a gas at rest has p = (gamma - 1) rho E; and for the inflow of
+    the paper's inlet table (Mach 4, 12270 Pa, 217 K, air with R = 287) the
+    recovered state gives the textbook sound speed sqrt(gamma R T) = 295.3 m/s
+    and the Mach number 4."""
+    import cases
+    rng = np.random.default_rng(31)
+    for _ in range(200):
+        V = rand_state(rng)
+        q = cases.prim_to_cons(V.reshape(5, 1)).ravel()
+        W = oracle.cons_to_prim(q)
+        assert np.allclose(W, V, rtol=1e-13, atol=1e-15 * np.abs(V).max())
+    W = oracle.cons_to_prim(np.array([1.3, 0.0, 0.0, 0.0, 2.5]))
+    assert W[4] == pytest.approx((1.4 - 1.0) * 2.5, rel=1e-15) and (W[1:4] == 0.0).all()
+    R, T, p = 287.0, 217.0, 12270.0
+    rho = p / (R * T)
+    c = np.sqrt(1.4 * R * T)
+    assert c == pytest.approx(295.3, abs=0.05)
+    V = np.array([rho, 4.0 * c, 0.0, 0.0, p])
+    W = oracle.cons_to_prim(cases.prim_to_cons(V.reshape(5, 1)).ravel())
+    assert np.sqrt(1.4 * W[4] / W[0]) == pytest.approx(c, rel=1e-13)
+    assert W[1] / np.sqrt(1.4 * W[4] / W[0]) == pytest.approx(4.0, rel=1e-13)
 
 
 # ------------------------------------------------- flux-vector splittings ---
