@@ -20,8 +20,8 @@ __device__ __forceinline__ long long ghost_index(const FvBlockDev& B, int i, int
 
 // faces of direction `dir` in block B: index f over (n_dir + 1) x (other two
 // extents); the face's VJP in arithmetic T, inputs and outputs binary64
-template <class T>
-__global__ void __launch_bounds__(128) adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
+template <class T, int MINB>
+__global__ void __launch_bounds__(128, MINB) adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
                                                        const double* __restrict__ lam_out,
                                                        const double* __restrict__ invvol, double alpha_dt,
                                                        const double* __restrict__ metric, long long mstride,
@@ -195,12 +195,17 @@ int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const doub
   P.limiter = fp.limiter;
   P.fix_all = fp.fix_all;
   const long long nf = (long long)(B.ni + (dir == 0)) * (B.nj + (dir == 1)) * (B.nk + (dir == 2));
+  // The double-float sweep's registers are capped for 3 CTAs of 128 threads
+  // per SM (168 registers; it spills ~430 bytes): 3.08 -> 2.52 ms per 96^3
+  // VJP stage on GB300 against the uncapped 255 registers and 2 CTAs (a cap
+  // for 4 CTAs spilled more and measured 2.65 ms).  The binary64 sweep is
+  // bound by the FP64 unit and keeps its registers.
   if (double_float)
-    adj_face_kernel<df64><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride, P,
-                                                           contrib);
+    adj_face_kernel<df64, 3><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride, P,
+                                                              contrib);
   else
-    adj_face_kernel<double><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride,
-                                                             P, contrib);
+    adj_face_kernel<double, 1><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric,
+                                                                mstride, P, contrib);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
