@@ -411,6 +411,11 @@ class RankSolver:
     def __init__(self, pb, part: Partition, rank: int, precision: str = "fp64", **kw):
         import torch
         from ._binding import Solver
+        if pb.params.get("visc", 0):
+            # a halo slab carries state values only: the viscous terms' ghost
+            # geometry and depth-1 edge ghosts at a cross-rank cut would not
+            # be the donor's, so the partitioned form is inviscid
+            raise ValueError("the partitioned form covers the inviscid residual (visc = 0)")
         self.rank = rank
         self.problem = part.local_problem(pb, rank)
         self.solver = Solver.from_problem(self.problem, precision=precision, **kw)

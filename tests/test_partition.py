@@ -247,3 +247,13 @@ def test_two_gloo_ranks_reproduce_the_serial_run(name):
     ref_i = [cases.interior_view(b, x) for b, x in zip(pb.blocks, cases.unpack_state(pb.blocks, ref))]
     for a, b in zip(out["interior"], ref_i):
         assert np.array_equal(a, b)
+
+
+def test_rank_solver_refuses_viscous_problems():
+    """A halo slab carries state values only, not the viscous terms' ghost
+    geometry or edge ghosts, so the partitioned form refuses visc = 1
+    before touching a GPU."""
+    pb = cases.mms_3d(12, curvilinear=True, visc=1, mu=0.05)
+    part = P.partition(pb, 2)
+    with pytest.raises(ValueError):
+        P.RankSolver(pb, part, 0)
