@@ -630,9 +630,11 @@ int grid_for(long long n, int threads, int nsm) {
 
 fv_ctx* H(fv_handle h) { return reinterpret_cast<fv_ctx*>(h); }
 
-// destroy the cached RK-step graphs (one still running is freed when it
-// completes; cudaFree waits for the device, so no dt slot is freed in use)
+// destroy the cached RK-step graphs after the device is idle, so that no
+// graph that may still run reads a dt slot being freed
 void drop_graphs(fv_ctx* h) {
+  if (h->graphs.empty()) return;
+  cudaDeviceSynchronize();
   for (auto& g : h->graphs) {
     cudaGraphExecDestroy(g.second.exec);
     cudaFree(g.second.dt_dev);
