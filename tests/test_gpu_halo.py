@@ -137,3 +137,23 @@ def test_pack_then_unpack_is_the_exchange():
         (g,) = part.rank_children(rs.rank)
         assert np.array_equal(got.reshape(ref[g].shape), ref[g])
         rs.close()
+
+
+def test_partitioned_full_size_batch():
+    """The benchmark's 64-block batch (10.9 M cells, random orientations)
+    on four ranks with over-decomposition: one RK step bit-equal to the
+    single handle."""
+    pb = cases.multiblock_batched()
+    part, ranks = _ranks(pb, 4, "fp64", over=2.0)
+    assert part.imbalance() < 1.05
+    tr = P.LoopbackTransport()
+    P.rk_step(ranks, pb.dt, tr)
+    got = _gather(pb, part, ranks)
+    for rs in ranks:
+        rs.close()
+    one = solver(pb, "fp64")
+    one.rk_step(pb.dt, use_graph=False)
+    ref = _interior(pb, one.get_state(0).cpu().numpy())
+    one.close()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
