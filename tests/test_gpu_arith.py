@@ -24,3 +24,19 @@ def test_reciprocal_within_one_ulp_of_ieee():
     ulps = np.abs(mine.view(np.int64) - ieee.view(np.int64))
     assert ulps.max() <= 1, int(ulps.max())
     assert (ulps == 0).mean() > 0.9
+
+
+def test_probe_rates_are_ordered():
+    """The measured rates the roofline is graded against: positive, binary32
+    FMA far above binary64 FMA (GB300 runs binary64 at 1/64 of the binary32
+    rate), add = multiply = FMA in binary64, the face code's reciprocal
+    faster than the compiler's IEEE one, double-float operations between
+    the two precisions' FMA rates."""
+    import paper_2012_02925_gb300 as fv
+    r = fv.probe_alu_rates()
+    assert all(v > 0 for v in r.values())
+    assert r["fp32_fma"] > 30 * r["fp64_fma"]
+    assert abs(r["fp64_add"] / r["fp64_fma"] - 1) < 0.1 and abs(r["fp64_mul"] / r["fp64_fma"] - 1) < 0.1
+    assert r["fp64_rcp_refined"] > r["fp64_rcp"]
+    for k in ("df64_add", "df64_mul", "df64_div", "df64_sqrt"):
+        assert r["fp64_fma"] < r[k] < r["fp32_fma"], k
