@@ -166,7 +166,8 @@ typedef struct {
  *   tile: 0 = automatic; else an index into the compiled tile shapes
  *     (1: 32x8 cells / 256 threads, 2: 32x4 / 128, 3: 16x8 / 128, 4: 30x8 / 256,
  *     5: 32x8 / 288, 6: 32x8 / 256 and 7: 32x4 / 128 with the next k-plane
- *     prefetched by cp.async - 6 and 7 for FV_PREC_FP32FLUX only -, 8: 32x7 / 256).
+ *     prefetched by cp.async - 6 and 7 for FV_PREC_FP32FLUX only -, 8: 32x7 / 256,
+ *     9: 32x6 / 256, 10: 16x12 / 192).
  *   kchunk: k-planes per tile; 0 = automatic (about three tiles per resident
  *     CTA slot); -w = about w tiles per resident CTA slot.  Tiles are handed
  *     to persistent CTAs largest first through a device counter.
@@ -432,13 +433,14 @@ int fv_halo_unpack(fv_handle h, int buffer, const double* recv_dev, void* stream
  * second of: [0] binary64 FMA, [1] add, [2] multiply, [3] the compiler's IEEE
  * reciprocal 1.0/x, [4] IEEE square root, [5] binary32 FMA, and the
  * double-float operations of the stage kernel's other form: [6] add,
- * [7] multiply, [8] quotient, [9] square root, [10] absolute value, and
- * [11] the binary64 face code's reciprocal (see fv_check_rcp64).
+ * [7] multiply, [8] quotient, [9] square root, [10] absolute value,
+ * [11] the binary64 face code's reciprocal (see fv_check_rcp64) and [12] its
+ * square root (see fv_check_sqrt64).
  * Allocates and frees 2 KB, synchronises `stream`, takes ~50 ms.
  * FV_ERR_INVALID_ARG for a NULL pointer or short array, FV_ERR_CUDA if a
  * launch fails.
  * ------------------------------------------------------------------------- */
-#define FV_PROBE_NRATES 12
+#define FV_PROBE_NRATES 13
 
 int fv_probe_alu_rates(double* out_host, int n_out, void* stream);
 
@@ -450,6 +452,13 @@ int fv_probe_alu_rates(double* out_host, int n_out, void* stream);
  * FV_ERR_INVALID_ARG for NULL pointers or n <= 0, FV_ERR_CUDA if the launch
  * fails. */
 int fv_check_rcp64(const double* x_dev, int64_t n, double* out_dev, void* stream);
+
+/* Test support for the binary64 face code's square root (the hardware's
+ * approximate reciprocal square root corrected by the binomial series of
+ * (1 - e)^(-1/2), within one unit in the last place of sqrt(x) for positive
+ * normal x): out_dev[2i] = that square root, out_dev[2i+1] = the compiler's
+ * IEEE sqrt(x[i]).  Arguments, stream and errors as fv_check_rcp64. */
+int fv_check_sqrt64(const double* x_dev, int64_t n, double* out_dev, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free residual norms.  The paper has no counterpart: this entry

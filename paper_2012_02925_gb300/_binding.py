@@ -25,7 +25,7 @@ EXPORTS = ("fv_config_default", "fv_create_blocks", "fv_destroy", "fv_last_error
            "fv_adjoint_vjp", "fv_autotune", "fv_get_launch", "fv_set_boundaries", "fv_set_monitor",
            "fv_monitor_norms", "fv_stage_state", "fv_set_state_staged", "fv_graph_count",
            "fv_probe_alu_rates", "fv_set_halo", "fv_halo_size", "fv_halo_pack", "fv_halo_unpack",
-           "fv_check_rcp64", "fv_set_adjoint_arith")
+           "fv_check_rcp64", "fv_check_sqrt64", "fv_set_adjoint_arith")
 
 
 class FvError(RuntimeError):
@@ -113,6 +113,8 @@ def load_library(path: Optional[str] = None):
     L.fv_set_adjoint_arith.restype = i32
     L.fv_check_rcp64.argtypes = [vp, i64, vp, vp]
     L.fv_check_rcp64.restype = i32
+    L.fv_check_sqrt64.argtypes = [vp, i64, vp, vp]
+    L.fv_check_sqrt64.restype = i32
     L.fv_set_halo.argtypes = [vp, ctypes.POINTER(fv_connection), i32, ctypes.POINTER(fv_connection), i32]
     L.fv_set_halo.restype = i32
     L.fv_halo_size.argtypes = [vp, i32]
@@ -151,7 +153,8 @@ def _stream(stream) -> int:
 
 
 PROBE_RATES = ("fp64_fma", "fp64_add", "fp64_mul", "fp64_rcp", "fp64_sqrt", "fp32_fma",
-               "df64_add", "df64_mul", "df64_div", "df64_sqrt", "df64_abs", "fp64_rcp_refined")
+               "df64_add", "df64_mul", "df64_div", "df64_sqrt", "df64_abs", "fp64_rcp_refined",
+               "fp64_sqrt_refined")
 
 
 def probe_alu_rates(stream=None) -> dict:
@@ -180,16 +183,26 @@ def _conn_table(conns: Sequence):
     return cs
 
 
-def check_rcp64(x):
-    """(face-code reciprocal, IEEE 1.0 / x) of a float64 CUDA tensor x, as a
-    (n, 2) tensor (fv_check_rcp64)."""
+def _check_arith(name, x):
     import torch
     L = load_library()
     out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
-    rc = L.fv_check_rcp64(_ptr(x), x.numel(), out.data_ptr(), _stream(None))
+    rc = getattr(L, name)(_ptr(x), x.numel(), out.data_ptr(), _stream(None))
     if rc != FV_OK:
-        raise FvError(rc, "fv_check_rcp64 failed")
+        raise FvError(rc, name + " failed")
     return out
+
+
+def check_rcp64(x):
+    """(face-code reciprocal, IEEE 1.0 / x) of a float64 CUDA tensor x, as a
+    (n, 2) tensor (fv_check_rcp64)."""
+    return _check_arith("fv_check_rcp64", x)
+
+
+def check_sqrt64(x):
+    """(face-code square root, IEEE sqrt(x)) of a float64 CUDA tensor x, as a
+    (n, 2) tensor (fv_check_sqrt64)."""
+    return _check_arith("fv_check_sqrt64", x)
 
 
 class Solver:

@@ -227,6 +227,25 @@ __device__ __forceinline__ double fv_rcp64(double x) {
 }
 
 // ---------------------------------------------------------------------------
+// binary64 square root within one unit in the last place: the hardware's
+// approximate reciprocal square root y0 of x (PTX rsqrt.approx.ftz.f64),
+// s = x y0 and e = 1 - s y0, so that x / s^2 = 1 / (1 - e) up to the
+// rounding of s, and sqrt(x) = s (1 - e)^(-1/2) = s (1 + e/2 + 3 e^2/8 + ...)
+// by the binomial series, here truncated after its e^2 term: five FP64
+// instructions where the compiler's IEEE square root costs about 7.5 FMA
+// issue slots on GB300.  For finite, positive, normal x (0, infinities,
+// negative and subnormal x give NaN): the face code takes it of density
+// ratios and squared sound speeds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fv_sqrt64(double x) {
+  double y0;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+  const double s = x * y0;
+  const double e = fma(-s, y0, 1.0);
+  return fma(s * e, fma(e, 0.375, 0.5), s);
+}
+
+// ---------------------------------------------------------------------------
 // uniform scalar interface used by the face code
 // ---------------------------------------------------------------------------
 template <class T> struct Sc;
@@ -235,7 +254,7 @@ template <> struct Sc<double> {
   static __device__ __forceinline__ double from_d(double x) { return x; }
   static __device__ __forceinline__ double to_d(double x) { return x; }
   static __device__ __forceinline__ double c(double x) { return x; }     // constant
-  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double sqrt(double x) { return fv_sqrt64(x); }
   static __device__ __forceinline__ double abs(double x) { return ::fabs(x); }
   // reciprocal within one unit in the last place (fv_rcp64); a quotient is
   // that reciprocal times the numerator

@@ -21,7 +21,8 @@ constexpr int CHAINS = 8;
 constexpr int THREADS = 256;
 
 enum ProbeOp {
-  P_DFMA, P_DADD, P_DMUL, P_DRCP, P_DSQRT, P_FFMA, P_DF_ADD, P_DF_MUL, P_DF_DIV, P_DF_SQRT, P_DF_ABS, P_DRCPN
+  P_DFMA, P_DADD, P_DMUL, P_DRCP, P_DSQRT, P_FFMA, P_DF_ADD, P_DF_MUL, P_DF_DIV, P_DF_SQRT, P_DF_ABS, P_DRCPN,
+  P_DSQRTN
 };
 
 template <int OP>
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(THREADS) probe_fp64(int iters, double seed, do
       if (OP == P_DRCP) x[c] = 1.0 / x[c];
       if (OP == P_DSQRT) x[c] = sqrt(x[c]);
       if (OP == P_DRCPN) x[c] = fv_rcp64(x[c]);
+      if (OP == P_DSQRTN) x[c] = fv_sqrt64(x[c]);
     }
   }
   double s = 0.0;
@@ -140,6 +142,7 @@ extern "C" int fv_probe_alu_rates(double* out_host, int n_out, void* stream) {
   out_host[9] = FV_PROBE_DF(P_DF_SQRT, it_dfs);
   out_host[10] = FV_PROBE_DF(P_DF_ABS, it_df);
   out_host[11] = FV_PROBE_D(P_DRCPN, it_slow);
+  out_host[12] = FV_PROBE_D(P_DSQRTN, it_slow);
 #undef FV_PROBE_D
 #undef FV_PROBE_DF
   cudaEventDestroy(e0);
@@ -149,25 +152,34 @@ extern "C" int fv_probe_alu_rates(double* out_host, int n_out, void* stream) {
 }
 
 // ---------------------------------------------------------------------------
-// binary64 reciprocal check: the face code's reciprocal next to the
-// compiler's IEEE 1.0 / x, for a test on the host
+// binary64 reciprocal and square-root checks: the face code's reciprocal
+// and square root next to the compiler's IEEE 1.0 / x and sqrt(x), for a
+// test on the host
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void rcp_check_kernel(const double* __restrict__ x, long long n, double* __restrict__ out) {
+template <bool SQRT>
+__global__ void arith_check_kernel(const double* __restrict__ x, long long n, double* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    out[2 * i] = fv_rcp64(x[i]);
-    out[2 * i + 1] = 1.0 / x[i];
+    out[2 * i] = SQRT ? fv_sqrt64(x[i]) : fv_rcp64(x[i]);
+    out[2 * i + 1] = SQRT ? sqrt(x[i]) : 1.0 / x[i];
   }
 }
-}  // namespace
 
-extern "C" int fv_check_rcp64(const double* x_dev, int64_t n, double* out_dev, void* stream) {
+int arith_check(const void* kernel, const double* x_dev, int64_t n, double* out_dev, void* stream) {
   if (!x_dev || !out_dev || n <= 0) return FV_ERR_INVALID_ARG;
   const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
   long long nn = n;
   void* args[] = {&x_dev, &nn, &out_dev};
-  if (cudaLaunchKernel((const void*)rcp_check_kernel, dim3((unsigned)blocks), dim3(256), args, 0,
-                       (cudaStream_t)stream) != cudaSuccess)
+  if (cudaLaunchKernel(kernel, dim3((unsigned)blocks), dim3(256), args, 0, (cudaStream_t)stream) != cudaSuccess)
     return FV_ERR_CUDA;
   return FV_OK;
+}
+}  // namespace
+
+extern "C" int fv_check_rcp64(const double* x_dev, int64_t n, double* out_dev, void* stream) {
+  return arith_check((const void*)arith_check_kernel<false>, x_dev, n, out_dev, stream);
+}
+
+extern "C" int fv_check_sqrt64(const double* x_dev, int64_t n, double* out_dev, void* stream) {
+  return arith_check((const void*)arith_check_kernel<true>, x_dev, n, out_dev, stream);
 }

@@ -77,13 +77,16 @@ __device__ __forceinline__ double rk_apply(double q0, df64 fac, df64 R) {
 }
 
 // NV: variables per ring cell (the primitives, and with the fused viscous
-// terms a sixth: T - tref)
-template <class T, int TX, int TY, int NV = 5>
+// terms a sixth: T - tref); SHARE: the per-cell slope planes (below);
+// NSLOT3: planes in the 3-D ring
+template <class T, int TX, int TY, int NV = 5, bool SHARE = false, int NSLOT3 = 4>
 struct StageSmem {
   static constexpr int W = TX + 4, H = TY + 4, PL = W * H;
   static constexpr int NXI = (TX + 1) * TY, NETA = TX * (TY + 1), NZETA = TX * TY;
+  static constexpr int NHX = (TX + 2) * TY, NHY = TX * (TY + 2);
   static constexpr __host__ __device__ size_t typed(bool three_d) {
-    return sizeof(T) * (size_t)((three_d ? 4 : 1) * NV * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0));
+    return sizeof(T) * (size_t)((three_d ? NSLOT3 : 1) * NV * PL + 5 * NXI + 5 * NETA + (three_d ? 2 * 5 * NZETA : 0) +
+                                (SHARE ? 5 * NHX + 5 * NHY + (three_d ? 2 * 5 * NZETA : 0) : 0));
   }
   // with prefetch: + a binary64 staging plane that cp.async fills while the
   // faces of the previous plane are computed
@@ -91,6 +94,31 @@ struct StageSmem {
     return ((typed(three_d) + 15) / 16) * 16 + (prefetch && three_d ? sizeof(double) * 5 * PL : 0);
   }
 };
+
+// The default scheme (kappa = -1, eps = 1, van Leer) puts V_i + h_i on cell
+// i's upper face and V_i - h_i on its lower face, h_i = Psi(a/b) b / 2 of the
+// cell's forward difference a and backward difference b: van Leer's Psi
+// makes h symmetric in a and b, so the two faces share one limiter
+// evaluation, done once per cell and direction in a slope pass before the
+// faces (about 0.56 of the per-face stencil's limiter work with the tile
+// halo).  Built for the binary64 form, which the FP64 unit bounds (128^3
+// block: 0.625 -> 0.716 Gcell/s); the double-float and binary32 forms are
+// bound by issue and latency at their occupancy, and the slope planes, the
+// third barrier per plane and the lost resident CTA made them slower
+// (2.75 -> 2.62 and 9.84 -> 8.26 Gcell/s), so they keep the per-face stencil.
+template <class T, bool FAST, bool VISC>
+__host__ __device__ constexpr bool stage_share() {
+  return FAST && std::is_same<T, double>::value;
+}
+// planes in the 3-D ring: with shared slopes a pass reads planes k .. k+2
+// only, unless a slip-wall zeta face on a block's upper side reads k - 1
+template <class T, bool FAST, bool VISC, bool BC>
+__host__ __device__ constexpr int stage_slots() {
+  return stage_share<T, FAST, VISC>() && !BC ? 3 : 4;
+}
+template <class T, int TX, int TY, bool FAST, bool VISC, bool BC>
+using StageSmemOf = StageSmem<T, TX, TY, (VISC && std::is_same<T, float>::value) ? 6 : 5,
+                              stage_share<T, FAST, VISC>(), stage_slots<T, FAST, VISC, BC>()>;
 
 // resident CTAs per SM the register allocation must allow (shared memory
 // permits this many for the compiled shapes)
@@ -117,18 +145,28 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
   using AT = typename Acc<T>::type;
   using MT = typename MetricStore<T>::type;
   constexpr int NV = FUSED_VISC ? 6 : 5;
-  using SM = StageSmem<T, TX, TY, NV>;
+  constexpr bool SHARE = stage_share<T, FAST, VISC>();
+  using SM = StageSmemOf<T, TX, TY, FAST, VISC, BC>;
   constexpr int W = SM::W, PL = SM::PL;
   constexpr int NXI = SM::NXI, NETA = SM::NETA, NZETA = SM::NZETA;
-  constexpr int NSLOT = DIM3 ? 4 : 1;
+  constexpr int NHX = SM::NHX, NHY = SM::NHY;
+  constexpr int NSLOT = DIM3 ? stage_slots<T, FAST, VISC, BC>() : 1;
   constexpr int NFACE = NXI + NETA + (DIM3 ? NZETA : 0);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);        // [NSLOT][NV][H][W]
   T* Fx = Vs + NSLOT * NV * PL;                   // [5][TY][TX+1]
   T* Fy = Fx + 5 * NXI;                           // [5][TY+1][TX]
-  T* Fz = Fy + 5 * NETA;                          // [2][5][TY][TX]
+  T* Fz = Fy + 5 * NETA;                          // [2][5][TY][TX] (3-D)
+  T* Hx = Fz + (DIM3 ? 2 * 5 * NZETA : 0);        // SHARE: [5][TY][TX+2], cells x = -1 .. TX
+  T* Hy = Hx + 5 * NHX;                           // SHARE: [5][TY+2][TX], rows y = -1 .. TY
+  T* Hz = Hy + 5 * NHY;                           // SHARE: [2][5][TY][TX] (3-D), planes by parity
   double* stg = reinterpret_cast<double*>(smem_raw + ((SM::typed(DIM3) + 15) / 16) * 16);  // [5][H][W] (PF)
+  // ring slot of plane kk (kk >= -2)
+  auto ring = [&](int kk) -> T* {
+    const int sl = NSLOT == 4 ? (kk & 3) : (NSLOT == 3 ? (kk + 6) % 3 : 0);
+    return Vs + sl * NV * PL;
+  };
 
   const int tid = threadIdx.x;
   const CC C = CC::from(make_face_consts<T>(args.fp));
@@ -188,9 +226,9 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
       const float ri = __fdividef(1.0f, rho);
       return FADD(num.hi, num.lo) * ri * ri * iR_f;
     };
-    // stage plane kk (ghosted index kk + 2 in memory) into ring slot `slot`
-    auto load_plane = [&](int kk, int slot) {
-      T* dst = Vs + slot * NV * PL;
+    // stage plane kk (ghosted index kk + 2 in memory) into its ring slot
+    auto load_plane = [&](int kk) {
+      T* dst = ring(kk);
       const double* base = qin + (long long)(kk + 2) * ks;
 #pragma unroll
       for (int r = 0; r < LROUNDS; ++r) {
@@ -223,9 +261,9 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
       }
       __pipeline_commit();
     };
-    auto convert_staged = [&](int slot) {
+    auto convert_staged = [&](int kk) {
       __pipeline_wait_prior(0);
-      T* dst = Vs + slot * NV * PL;
+      T* dst = ring(kk);
 #pragma unroll
       for (int r = 0; r < LROUNDS; ++r) {
         if (loff[r] < 0) continue;
@@ -254,8 +292,9 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
       const T *Lbm, *Lbp, *Rbm, *Rbp, *Lcm, *Lcp, *Rcm, *Rcp;
       long long gR, gstep;
     };
-    auto do_face = [&](const T* s0, const T* s1, const T* s2, const T* s3, int dir, long long f, T* dst,
-                       int dstr, int code, int side, const VisArgs& vis) {
+    // hL, hR, hs (SHARE): the half-slopes of s1 and s2, components hs apart
+    auto do_face = [&](const T* s0, const T* s1, const T* s2, const T* s3, const T* hL, const T* hR, int hs,
+                       int dir, long long f, T* dst, int dstr, int code, int side, const VisArgs& vis) {
       T nx, ny, nz, A;
       if (cart) {
         nx = S::from_d(B.cart_n[dir][0]); ny = S::from_d(B.cart_n[dir][1]);
@@ -274,6 +313,14 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
 #pragma unroll
         for (int n = 0; n < 5; ++n) Vb[n] = gc[n * PL];
         normal_face_flux(C, Vb, nx, ny, nz, A, out);
+      } else if constexpr (SHARE) {
+        T VL[5], VR[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+          VL[n] = s1[n * PL] + hL[n * hs];
+          VR[n] = s2[n * PL] - hR[n * hs];
+        }
+        face_riemann(C, VL, VR, nx, ny, nz, A, out);
       } else {
         face_flux(C, s0, s1, s2, s3, PL, nx, ny, nz, A, out);
       }
@@ -307,7 +354,8 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
     // (zeta), metric index without its k term and destination slot
     // (dir < 0: unused or outside).  Decoded on the fly: holding these in
     // registers for the whole tile costs more occupancy than the decode.
-    auto face_item = [&](int it, int& dir, int& off, int& dst, long long& met) {
+    // and (SHARE) the index of the face's lower cell in its direction's slope plane
+    auto face_item = [&](int it, int& dir, int& off, int& dst, int& hoff, long long& met) {
       dir = -1;
       if (it < NXI) {
         // the TX faces x < TX of every row first, row by row, then the last
@@ -321,7 +369,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         }
         const int i = i0 + x, j = j0 + y;
         if (i <= ni && j < nj) {
-          dir = 0; off = (y + 2) * W + x; dst = y * (TX + 1) + x;
+          dir = 0; off = (y + 2) * W + x; dst = y * (TX + 1) + x; hoff = y * (TX + 2) + x;
           met = B.face_off[0] + (long long)j * (ni + 1) + i;
         }
       } else if (it < NXI + NETA) {
@@ -329,15 +377,62 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
         const int y = e / TX, x = e - y * TX;                   // face between rows y-1 and y
         const int i = i0 + x, j = j0 + y;
         if (i < ni && j <= nj) {
-          dir = 1; off = y * W + (x + 2); dst = e;
+          dir = 1; off = y * W + (x + 2); dst = e; hoff = e;
           met = B.face_off[1] + (long long)j * ni + i;
         }
       } else if (DIM3 && it < NFACE) {
         const int e = it - NXI - NETA;
         const int y = e / TX, x = e - y * TX;
         if (i0 + x < ni && j0 + y < nj) {
-          dir = 2; off = (y + 2) * W + (x + 2); dst = e;
+          dir = 2; off = (y + 2) * W + (x + 2); dst = e; hoff = e;
           met = B.face_off[2] + (long long)(j0 + y) * ni + (i0 + x);
+        }
+      }
+    };
+    // SHARE: the half-slopes h = vanleer_half(forward, backward difference)
+    // of the cells the faces read - in xi and eta those of plane kp (cells
+    // x = -1 .. TX, rows y = -1 .. TY, inside the ghosted block), in zeta
+    // that of plane kz (from planes kz-1 .. kz+1, into the slot of kz's
+    // parity); inplane = false: zeta only
+    auto slopes = [&](int kp, int kz, bool inplane) {
+      constexpr int NH = NHX + NHY + (DIM3 ? NZETA : 0);
+      const T* Pk = ring(kp);
+      for (int it = inplane ? tid : NHX + NHY + tid; it < NH; it += NT) {
+        const T *cm, *c0, *cp;
+        T* hd;
+        int hs;
+        if (it < NHX) {
+          const int y = it / (TX + 2), x = it - y * (TX + 2);   // cell x - 1 of row y
+          if (j0 + y >= nj || i0 + x > ni + 1) continue;
+          c0 = Pk + (y + 2) * W + (x + 1);
+          cm = c0 - 1;
+          cp = c0 + 1;
+          hd = Hx + it;
+          hs = NHX;
+        } else if (it < NHX + NHY) {
+          const int e = it - NHX;
+          const int y = e / TX, x = e - y * TX;                 // cell x of row y - 1
+          if (j0 + y > nj + 1 || i0 + x >= ni) continue;
+          c0 = Pk + (y + 1) * W + (x + 2);
+          cm = c0 - W;
+          cp = c0 + W;
+          hd = Hy + e;
+          hs = NHY;
+        } else {
+          const int e = it - NHX - NHY;
+          const int y = e / TX, x = e - y * TX;
+          if (j0 + y >= nj || i0 + x >= ni) continue;
+          const int off = (y + 2) * W + (x + 2);
+          cm = ring(kz - 1) + off;
+          c0 = ring(kz) + off;
+          cp = ring(kz + 1) + off;
+          hd = Hz + (kz & 1) * 5 * NZETA + e;
+          hs = NZETA;
+        }
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+          const T v0 = c0[n * PL];
+          hd[n * hs] = vanleer_half(cp[n * PL] - v0, v0 - cm[n * PL]);
         }
       }
     };
@@ -345,48 +440,63 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
     // zeta face between planes kf-1 and kf (stencil kf-2 .. kf+1) at column offset c
     if (DIM3) {
       // planes k0-2 .. k0 now; plane k0+1 arrives in the first pass below
-      for (int s = -2; s <= 0; ++s) load_plane(k0 + s, (k0 + s) & 3);
+      for (int s = -2; s <= 0; ++s) load_plane(k0 + s);
       if (PF) prefetch_plane(k0 + 1);
+      if constexpr (SHARE) {
+        // the zeta slope of plane k0-1; the first pass overwrites k0-2
+        __syncthreads();
+        slopes(k0 - 1, k0 - 1, false);
+        __syncthreads();
+      }
     } else {
-      load_plane(0, 0);
+      load_plane(0);
       __syncthreads();
     }
 
     // In 3D the first pass (k = k0 - 1) evaluates only the zeta faces below
     // plane k0; every later pass is one plane.
     for (int k = DIM3 ? k0 - 1 : k0; k < k1; ++k) {
-      const int slot = DIM3 ? (k & 3) : 0;
       if (DIM3) {
         if (PF) {
-          convert_staged((k + 2) & 3);
+          convert_staged(k + 2);
           __syncthreads();
           if (k + 1 < k1) prefetch_plane(k + 3);   // overlaps the faces below
         } else {
-          load_plane(k + 2, (k + 2) & 3);
+          load_plane(k + 2);
           __syncthreads();
         }
       }
-      const T* P = Vs + slot * NV * PL;
+      const T* P = ring(k);
+      if constexpr (SHARE) {
+        slopes(k, k + 1, !DIM3 || k >= k0);
+        __syncthreads();
+      }
       // ---- every face of this plane (and the zeta faces above it), once;
       // one call site of the face code for all three directions ----
       for (int it = tid; it < NFACE; it += NT) {
-        int d, off, dst;
+        int d, off, dst, hoff;
         long long met;
-        face_item(it, d, off, dst, met);
+        face_item(it, d, off, dst, hoff, met);
         if (d < 0 || (DIM3 && k < k0 && d != 2)) continue;
-        const T *s0, *s1, *s2, *s3;
+        const T *s0, *s1, *s2, *s3, *hL, *hR;
+        int hs;
         T* dp;
         int dstr;
         long long f;
         if (DIM3 && d == 2) {
           // zeta face between planes k and k+1: stencil k-1 .. k+2 from the ring
-          s0 = Vs + ((k - 1) & 3) * NV * PL + off;
-          s1 = Vs + (k & 3) * NV * PL + off;
-          s2 = Vs + ((k + 1) & 3) * NV * PL + off;
-          s3 = Vs + ((k + 2) & 3) * NV * PL + off;
+          // (with a 3-plane ring s0 aliases plane k+2; only the
+          // per-face stencil and the wall flux, which keep 4 planes, read it)
+          s0 = ring(k - 1) + off;
+          s1 = ring(k) + off;
+          s2 = ring(k + 1) + off;
+          s3 = ring(k + 2) + off;
           dp = Fz + ((k + 1) & 1) * 5 * NZETA + dst;
           dstr = NZETA;
           f = met + (k + 1) * kfz;
+          hL = Hz + (k & 1) * 5 * NZETA + hoff;
+          hR = Hz + ((k + 1) & 1) * 5 * NZETA + hoff;
+          hs = NZETA;
         } else {
           const int st = d == 0 ? 1 : W;
           s0 = P + off;
@@ -396,6 +506,9 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
           dp = (d == 0 ? Fx : Fy) + dst;
           dstr = d == 0 ? NXI : NETA;
           f = met + k * (d == 0 ? kfx : kfy);
+          hL = (d == 0 ? Hx : Hy) + hoff;
+          hR = hL + (d == 0 ? 1 : TX);
+          hs = d == 0 ? NHX : NHY;
         }
         // physical boundary face with an overwritten flux?
         int code = 0, side = 0;
@@ -443,12 +556,12 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
             vis.Lcm = s1 - W; vis.Lcp = s1 + W; vis.Rcm = s2 - W; vis.Rcp = s2 + W;
           } else {
             const long long oL = s1 - P, oR = s2 - P;
-            const T* Pm = Vs + ((k - 1) & 3) * NV * PL;
-            const T* Pp = Vs + ((k + 1) & 3) * NV * PL;
+            const T* Pm = ring(k - 1);
+            const T* Pp = ring(k + 1);
             vis.Lcm = Pm + oL; vis.Lcp = Pp + oL; vis.Rcm = Pm + oR; vis.Rcp = Pp + oR;
           }
         }
-        do_face(s0, s1, s2, s3, d, f, dp, dstr, code, side, vis);
+        do_face(s0, s1, s2, s3, hL, hR, hs, d, f, dp, dstr, code, side, vis);
       }
       __syncthreads();
       if (DIM3 && k < k0) continue;
@@ -567,7 +680,7 @@ __global__ void __launch_bounds__(NT, (stage_min_ctas<T, NT, VISC>())) fv_stage_
 // creation), so a launch is a plain enqueue that stream capture accepts.
 template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC, bool BC>
 static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t s) {
-  const size_t smem = StageSmem<T, TX, TY, (VISC && std::is_same<T, float>::value) ? 6 : 5>::bytes(l.three_d != 0, PF);
+  const size_t smem = StageSmemOf<T, TX, TY, FAST, VISC, BC>::bytes(l.three_d != 0, PF);
   if (l.three_d) {
     fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC, BC><<<l.grid, NT, smem, s>>>(a);
   } else {
@@ -578,7 +691,7 @@ static int launch_stage_t(const FvStageArgs& a, const FvLaunch& l, cudaStream_t 
 
 template <class T, int TX, int TY, int NT, bool PF, bool FAST, bool VISC, bool BC>
 static int occupancy_t(bool three_d, size_t* smem_out) {
-  const size_t smem = StageSmem<T, TX, TY, (VISC && std::is_same<T, float>::value) ? 6 : 5>::bytes(three_d, PF);
+  const size_t smem = StageSmemOf<T, TX, TY, FAST, VISC, BC>::bytes(three_d, PF);
   int n = 0;
   if (three_d) {
     auto k = fv_stage_kernel<T, TX, TY, NT, true, PF, FAST, VISC, BC>;
@@ -605,7 +718,9 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
   X(5, 32, 8, 288, false) \
   X(6, 32, 8, 256, true)  \
   X(7, 32, 4, 128, true)  \
-  X(8, 32, 7, 256, false)
+  X(8, 32, 7, 256, false) \
+  X(9, 32, 6, 256, false) \
+  X(10, 16, 12, 192, false)
 
 // FAST selects the compile-time default scheme (FaceCFast); each
 // translation unit instantiates one combination of FAST, VISC and BC.

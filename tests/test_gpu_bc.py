@@ -80,7 +80,8 @@ def test_rk_steps_with_boundaries(prec, case):
     assert rel_err_states(got, ref, o) <= TOL_STEPS[prec]
 
 
-@pytest.mark.parametrize("prec,tile", [("fp64", 3), ("df64", 1), ("df64", 8), ("fp32flux", 5), ("fp32flux", 6)])
+@pytest.mark.parametrize("prec,tile", [("fp64", 3), ("fp64", 9), ("df64", 1), ("df64", 8), ("df64", 10),
+                                       ("fp32flux", 5), ("fp32flux", 6)])
 def test_boundary_faces_in_every_tile_position(prec, tile):
     """Ragged tiles and k-chunks so that boundary faces fall on tile edges,
     chunk starts and chunk ends."""
