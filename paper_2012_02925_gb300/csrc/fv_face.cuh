@@ -83,7 +83,8 @@ __device__ __forceinline__ FaceC<T> make_face_consts(const FvFaceParams& p) {
   return c;
 }
 
-// Q = (rho, rho u, rho v, rho w, rho e_t) -> V = (rho, u, v, w, p)
+// Q = (rho, rho u, rho v, rho w, rho e_t) -> V = (rho, u, v, w, p), the
+// kinetic energy rho |u|^2 / 2 as (rho u) . u / 2
 template <class T, class CC>
 __device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]) {
   T rinv = Sc<T>::rcp(q[0]);
@@ -92,7 +93,7 @@ __device__ __forceinline__ void prim_from_cons(const CC& C, const T q[5], T V[5]
   V[1] = u;
   V[2] = v;
   V[3] = w;
-  V[4] = C.gm1 * (q[4] - Sc<T>::halve(q[0]) * Sc<T>::dot3(u, u, v, v, w, w));
+  V[4] = C.gm1 * (q[4] - Sc<T>::halve(Sc<T>::dot3(q[1], u, q[2], v, q[3], w)));
 }
 
 // Half the van Leer limited slope, Psi(a/b) b / 2 with Psi(r) = (r + |r|)/(1 + |r|).
@@ -165,22 +166,24 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   const T hR = C.g_gm1 * pR * riR + S::halve(S::dot3(uR, uR, vR, vR, wR, wR));
   const T mL = rL * VnL, mR = rR * VnR;
 
-  // Roe averages: R = sqrt(rho_R/rho_L), rho~ = rho_L R
+  // Roe averages: R = sqrt(rho_R/rho_L), rho~ = rho_L R, and
+  // phi~ = (phi_L + R phi_R)/(1 + R) = phi_L + beta (phi_R - phi_L) with
+  // beta = R/(1 + R): one multiply-add per velocity from the jumps below
+  const T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
   const T Rt = S::sqrt(rR * riL);
   const T rt = rL * Rt;
-  const T w1 = S::rcp(C.one + Rt);
-  const T ut = (uL + Rt * uR) * w1;
-  const T vt = (vL + Rt * vR) * w1;
-  const T wt = (wL + Rt * wR) * w1;
-  const T ht = (hL + Rt * hR) * w1;
+  const T beta = Rt * S::rcp(C.one + Rt);
+  const T ut = uL + beta * du;
+  const T vt = vL + beta * dv;
+  const T wt = wL + beta * dw;
+  const T ht = hL + beta * (hR - hL);
   const T q2h = S::halve(S::dot3(ut, ut, vt, vt, wt, wt));
   const T c2 = C.gm1 * (ht - q2h);
   const T ct = S::sqrt(c2);
   const T ic2 = S::rcp(c2);
-  const T Vnt = S::dot3(nx, ut, ny, vt, nz, wt);
-
-  const T dr = rR - rL, du = uR - uL, dv = vR - vL, dw = wR - wL, dp = pR - pL;
+  // the averaged normal velocity by the same weights: n . u~ = VnL + beta dVn
   const T dVn = VnR - VnL;
+  const T Vnt = VnL + beta * dVn;
 
   T l1 = S::abs(Vnt - ct), l2 = S::abs(Vnt), l5 = S::abs(Vnt + ct);
   if (C.k_fix()) {
@@ -197,11 +200,12 @@ __device__ __forceinline__ void roe_flux(const CC& C, const T VL[5], const T VR[
   const T a3 = l2 * rt;
   const T a15 = a1 + a5, d51 = (a5 - a1) * ct;
 
-  // dissipation |dF1| + |dF234| + |dF5|
+  // dissipation |dF1| + |dF234| + |dF5| (the velocity components take
+  // a15 + a2 = D0 times the averaged velocity)
   T D0 = a15 + a2;
-  T D1 = S::dot4(a15, ut, d51, nx, a2, ut, a3, du - nx * dVn);
-  T D2 = S::dot4(a15, vt, d51, ny, a2, vt, a3, dv - ny * dVn);
-  T D3 = S::dot4(a15, wt, d51, nz, a2, wt, a3, dw - nz * dVn);
+  T D1 = S::dot3(D0, ut, d51, nx, a3, du - nx * dVn);
+  T D2 = S::dot3(D0, vt, d51, ny, a3, dv - ny * dVn);
+  T D3 = S::dot3(D0, wt, d51, nz, a3, dw - nz * dVn);
   T D4 = S::dot4(a15, ht, d51, Vnt, a2, q2h, a3, S::dot4(ut, du, vt, dv, wt, dw, -Vnt, dVn));
 
   const T hA = S::halve(A);
