@@ -463,10 +463,10 @@ int fv_check_sqrt64(const double* x_dev, int64_t n, double* out_dev, void* strea
 /* ---------------------------------------------------------------------------
  * Allocation-free residual norms.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory while they
- * run - code inside a CUDA-graph capture or a framework's caching allocator
- * (where cudaMalloc would synchronise the device or fragment the pool),
- * real-time or embedded hosts that forbid allocation after start-up, and
- * plugins that only receive memory from their host application.
+ * run - code under a framework's caching allocator (where cudaMalloc would
+ * synchronise the device or fragment the pool), real-time or embedded hosts
+ * that forbid allocation after start-up, and plugins that only receive
+ * memory from their host application.
  *
  * field_dev: device pointer to 5 contiguous planes of n doubles (variable v at
  *   field_dev + v*n), e.g. the packed interior field that fv_residual writes
@@ -478,10 +478,9 @@ int fv_check_sqrt64(const double* x_dev, int64_t n, double* out_dev, void* strea
  * 120 KiB device array inside the library: it is held on every GPU that loads
  * the library until the process exits, it is shared by every call, and calls
  * whose kernels overlap on the GPU race on it (serialise them on one stream).
- * The first call on a device looks up that array's device address, so make
- * it before any stream capture that includes this call; the address is kept
- * until the process exits, so after a cudaDeviceReset() of a device this
- * entry point must not be called on that device again.  Nothing is
+ * The first call on a device looks up that array's device address; the
+ * address is kept until the process exits, so after a cudaDeviceReset() of a
+ * device this entry point must not be called on that device again.  Nothing is
  * allocated or freed.  The launch status returned is that of this call's
  * own launches (an error left by an earlier, unrelated call is neither
  * reported nor cleared).

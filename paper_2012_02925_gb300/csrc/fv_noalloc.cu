@@ -2,11 +2,10 @@
 //
 // fv_residual_norms() keeps its per-CTA partial sums in device memory that the
 // handle allocates with cudaMalloc on first use.  Some callers cannot allow
-// that: code running inside a CUDA-graph capture or under a framework's
-// caching allocator (where a cudaMalloc would synchronise the device or
-// fragment the pool), embedded or real-time hosts that forbid allocation after
-// start-up, and plugins that only ever receive memory from their host
-// application.  fv_field_norms_noalloc() serves them: the caller passes the
+// that: code running under a framework's caching allocator (where a
+// cudaMalloc would synchronise the device or fragment the pool), embedded or
+// real-time hosts that forbid allocation after start-up, and plugins that
+// only ever receive memory from their host application.  fv_field_norms_noalloc() serves them: the caller passes the
 // field and the output buffer, and the partial sums live in a fixed,
 // file-scope device array that is part of the loaded library.
 //

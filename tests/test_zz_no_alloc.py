@@ -1,8 +1,8 @@
 """The allocation-free norm entry point (fv_field_norms_noalloc) against the
 allocating one (fv_residual_norms), through the C ABI.
 
-Callers that may not allocate device memory (graph capture, caching
-allocators, hosts that forbid allocation after start-up) use the
+Callers that may not allocate device memory (caching allocators, hosts
+that forbid allocation after start-up, plugins) use the
 allocation-free entry point; it must give the same norms.  Two calls in a row
 share the library's fixed scratch array, so the second call also checks that
 leftovers of the first do not leak into its result.  Named to be collected
