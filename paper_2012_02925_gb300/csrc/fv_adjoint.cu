@@ -20,8 +20,12 @@ __device__ __forceinline__ long long ghost_index(const FvBlockDev& B, int i, int
 
 // faces of direction `dir` in block B: index f over (n_dir + 1) x (other two
 // extents); the face's VJP in arithmetic T, inputs and outputs binary64
-template <class T, int MINB>
-__global__ void __launch_bounds__(128, MINB) adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
+// NT threads per CTA; PARK: values dead across the Roe part parked in shared
+// memory (ADJ_PARK per thread); LOCK: the CTA's warps pass barriers at fixed
+// points of every face VJP (every thread runs the same number of faces, the
+// last ones repeating the final face without storing it)
+template <class T, int NT, int MINB, bool PARK, bool LOCK>
+__global__ void __launch_bounds__(NT, MINB) adj_face_kernel(const FvBlockDev B, int dir, const double* __restrict__ qin,
                                                        const double* __restrict__ lam_out,
                                                        const double* __restrict__ invvol, double alpha_dt,
                                                        const double* __restrict__ metric, long long mstride,
@@ -33,7 +37,10 @@ __global__ void __launch_bounds__(128, MINB) adj_face_kernel(const FvBlockDev B,
   const long long ncell_b = (long long)B.ni * B.nj * B.nk;
   const double* lam = lam_out + 5 * B.cell_off;
   const double* qb = qin + B.qoff;
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+  for (long long base = blockIdx.x * (long long)NT; base < nf; base += (long long)gridDim.x * NT) {
+    const bool valid = base + threadIdx.x < nf;
+    if (!LOCK && !valid) break;
+    const long long f = valid ? base + threadIdx.x : nf - 1;
     const int i = (int)(f % ei), j = (int)((f / ei) % ej), k = (int)(f / ((long long)ei * ej));
     const int g = dir == 0 ? i : (dir == 1 ? j : k);            // face between cells g-1 and g
     const int n_dir = dir == 0 ? B.ni : (dir == 1 ? B.nj : B.nk);
@@ -76,7 +83,14 @@ __global__ void __launch_bounds__(128, MINB) adj_face_kernel(const FvBlockDev B,
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int n = 0; n < 5; ++n) qbar[s][n] = S::c(0.0);
-    face_vjp(P, q, nx, ny, nz, A, Fb, qbar, F);
+    if constexpr (PARK) {
+      extern __shared__ __align__(16) unsigned char adj_smem[];
+      T* park = reinterpret_cast<T*>(adj_smem) + threadIdx.x;
+      face_vjp<T, NT, LOCK>(P, q, nx, ny, nz, A, Fb, qbar, F, park);
+    } else {
+      face_vjp<T, 0, LOCK>(P, q, nx, ny, nz, A, Fb, qbar, F);
+    }
+    if (!valid) continue;
     double* out = contrib + f * 20;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -195,17 +209,27 @@ int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const doub
   P.limiter = fp.limiter;
   P.fix_all = fp.fix_all;
   const long long nf = (long long)(B.ni + (dir == 0)) * (B.nj + (dir == 1)) * (B.nk + (dir == 2));
-  // The double-float sweep's registers are capped for 3 CTAs of 128 threads
-  // per SM (168 registers; it spills ~430 bytes): 3.08 -> 2.52 ms per 96^3
-  // VJP stage on GB300 against the uncapped 255 registers and 2 CTAs (a cap
-  // for 4 CTAs spilled more and measured 2.65 ms).  The binary64 sweep is
-  // bound by the FP64 unit and keeps its registers.
-  if (double_float)
-    adj_face_kernel<df64, 3><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric, mstride, P,
-                                                              contrib);
-  else
-    adj_face_kernel<double, 1><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol, alpha_dt, metric,
-                                                                mstride, P, contrib);
+  // The double-float sweep parks its cell primitives and MUSCL Jacobian in
+  // shared memory across the Roe part (45 KB per CTA of 128 threads), its
+  // registers are capped for 4 CTAs per SM (128; ~300 bytes spill) and the
+  // warps of a CTA pass barriers at five points of each face.  96^3 VJP stage
+  // on GB300: 2.52 ms (168 registers, 430 bytes spilled, 3 CTAs) -> 2.29
+  // (parked, 3 CTAs, no spill) -> 2.03 (parked, 4 CTAs) -> 1.97 ms (with the
+  // barriers); one CTA of 384 threads (168 registers, no spill) took 2.34 ms,
+  // two of 256 1.98 ms.  The binary64 sweep is bound by the FP64 unit and
+  // keeps its registers.
+  if (double_float) {
+    constexpr int NT = 128, MB = 4;
+    constexpr bool LOCK = true;
+    constexpr int smem = ADJ_PARK * sizeof(df64) * NT;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(adj_face_kernel<df64, NT, MB, true, LOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    adj_face_kernel<df64, NT, MB, true, LOCK><<<grid_of(nf, NT), NT, smem, s>>>(B, dir, qin, lam_out, invvol, alpha_dt,
+                                                                             metric, mstride, P, contrib);
+  } else {
+    adj_face_kernel<double, 128, 1, false, false><<<grid_of(nf, 128), 128, 0, s>>>(B, dir, qin, lam_out, invvol,
+                                                                                  alpha_dt, metric, mstride, P, contrib);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

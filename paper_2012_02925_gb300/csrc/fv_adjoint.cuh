@@ -130,18 +130,40 @@ __device__ __forceinline__ T sgn(T x) {
   return Sc<T>::sel(Sc<T>::neg(x), Sc<T>::c(-1.0), Sc<T>::c(1.0));
 }
 
+// Shared-memory parking of values that are dead between the MUSCL forward
+// and the MUSCL reverse (SN > 0: value v of this thread at p[v * SN]); the
+// compiler barriers keep the stores before and the loads after the Roe part,
+// so those values hold no registers across it.
+template <class T>
+struct Park {
+  static __device__ __forceinline__ void put(T* p, T v) { *p = v; }
+  static __device__ __forceinline__ T get(const T* p) { return *p; }
+};
+template <>
+struct Park<df64> {
+  static __device__ __forceinline__ void put(df64* p, df64 v) { *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo); }
+  static __device__ __forceinline__ df64 get(const df64* p) {
+    const float2 f = *reinterpret_cast<const float2*>(p);
+    return mk(f.x, f.y);
+  }
+};
+// values parked per thread: r, u, v, w, 1/r, |u|^2 of the four cells and the
+// four MUSCL Jacobian coefficients of the five variables
+constexpr int ADJ_PARK = 4 * 6 + 4 * 5;
+
 // Face VJP: q[c][n] conserved state of stencil cell c (c = 0..3 along the face
 // normal, the face between cells 1 and 2), unit normal n, area A, cotangent Fb
 // of the 5 face fluxes (F^ |S|).  Accumulates qb[c][n].  Returns F in F (may be
-// used to check the forward).
-template <class T>
+// used to check the forward).  SN > 0: park (shared memory at park, stride SN).
+template <class T, int SN = 0, bool LOCK = false>
 __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx, T ny, T nz, T A, const T Fb[5],
-                                         T qb[4][5], T F[5]) {
+                                         T qb[4][5], T F[5], T* park = nullptr) {
   using S = Sc<T>;
   // ---------------- forward ----------------
   PrimFwd<T> s[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) s[c] = prim_fwd(P, q[c]);
+  if constexpr (LOCK) __syncthreads();
   // MUSCL states and their derivatives with respect to the three neighbour
   // differences: VL = V1 + e4km phi(d0, dm) + e4kp phi(dm, d0),
   // VR = V2 - e4kp phi(dp, d0) - e4km phi(d0, dp);
@@ -166,6 +188,26 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
     jR0[n] = -(P.e4kp * b3 + P.e4km * a4);
     jRp[n] = -(P.e4kp * a3 + P.e4km * b4);
   }
+  if constexpr (SN > 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Park<T>::put(park + (6 * c + 0) * SN, s[c].r);
+      Park<T>::put(park + (6 * c + 1) * SN, s[c].u);
+      Park<T>::put(park + (6 * c + 2) * SN, s[c].v);
+      Park<T>::put(park + (6 * c + 3) * SN, s[c].w);
+      Park<T>::put(park + (6 * c + 4) * SN, s[c].ri);
+      Park<T>::put(park + (6 * c + 5) * SN, s[c].k);
+    }
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+      Park<T>::put(park + (24 + n) * SN, jL0[n]);
+      Park<T>::put(park + (29 + n) * SN, jLm[n]);
+      Park<T>::put(park + (34 + n) * SN, jR0[n]);
+      Park<T>::put(park + (39 + n) * SN, jRp[n]);
+    }
+    asm volatile("" ::: "memory");
+  }
+  if constexpr (LOCK) __syncthreads();
   const T rL = VL[0], uL = VL[1], vL = VL[2], wL = VL[3], pL = VL[4];
   const T rR = VR[0], uR = VR[1], vR = VR[2], wR = VR[3], pR = VR[4];
   const T VnL = nx * uL + ny * vL + nz * wL, VnR = nx * uR + ny * vR + nz * wR;
@@ -212,6 +254,7 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
   F[2] = (mL * vL + mR * vR + ny * (pL + pR) - D2) * hA;
   F[3] = (mL * wL + mR * wR + nz * (pL + pR) - D3) * hA;
   F[4] = (mL * hL + mR * hR - D4) * hA;
+  if constexpr (LOCK) __syncthreads();
 
   // ---------------- reverse ----------------
   const T G0 = Fb[0] * hA, G1 = Fb[1] * hA, G2 = Fb[2] * hA, G3 = Fb[3] * hA, G4 = Fb[4] * hA;
@@ -250,6 +293,7 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
   l1b += a1b * (dP - rcd) * hic2; dPb += a1b * l1 * hic2; rcdb += -a1b * l1 * hic2; hic2b += a1b * l1 * (dP - rcd);
   ic2b += S::halve(hic2b);
   rtb += rcdb * ct * dVn; ctb += rcdb * rt * dVn; dVnb += rcdb * rt * ct;
+  if constexpr (LOCK) __syncthreads();
   // eigenvalue magnitudes with the entropy fix (delta = harten * ct)
   T deltab = l1b * d1d + l2b * d2d + l5b * d5d;
   const T la1b = l1b * d1l, la2b = l2b * d2l, la5b = l5b * d5l;
@@ -294,6 +338,17 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
   uLb += nx * VnLb; vLb += ny * VnLb; wLb += nz * VnLb;
   uRb += nx * VnRb; vRb += ny * VnRb; wRb += nz * VnRb;
   // MUSCL reverse
+  if constexpr (LOCK) __syncthreads();
+  if constexpr (SN > 0) {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+      jL0[n] = Park<T>::get(park + (24 + n) * SN);
+      jLm[n] = Park<T>::get(park + (29 + n) * SN);
+      jR0[n] = Park<T>::get(park + (34 + n) * SN);
+      jRp[n] = Park<T>::get(park + (39 + n) * SN);
+    }
+  }
   const T VLb[5] = {rLb, uLb, vLb, wLb, pLb};
   const T VRb[5] = {rRb, uRb, vRb, wRb, pRb};
   T Vb[4][5];
@@ -307,6 +362,17 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
     Vb[1][n] = Lb + dmb - d0b;
     Vb[2][n] = Rb + d0b - dpb;
     Vb[3][n] = dpb;
+  }
+  if constexpr (SN > 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      s[c].r = Park<T>::get(park + (6 * c + 0) * SN);
+      s[c].u = Park<T>::get(park + (6 * c + 1) * SN);
+      s[c].v = Park<T>::get(park + (6 * c + 2) * SN);
+      s[c].w = Park<T>::get(park + (6 * c + 3) * SN);
+      s[c].ri = Park<T>::get(park + (6 * c + 4) * SN);
+      s[c].k = Park<T>::get(park + (6 * c + 5) * SN);
+    }
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) prim_bwd(P, s[c], Vb[c], qb[c]);
