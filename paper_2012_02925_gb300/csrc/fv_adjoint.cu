@@ -209,13 +209,14 @@ int fv_adjoint_faces(const FvBlockDev& B, int dir, const double* qin, const doub
   P.limiter = fp.limiter;
   P.fix_all = fp.fix_all;
   const long long nf = (long long)(B.ni + (dir == 0)) * (B.nj + (dir == 1)) * (B.nk + (dir == 2));
-  // The double-float sweep parks its cell primitives and MUSCL Jacobian in
-  // shared memory across the Roe part (45 KB per CTA of 128 threads), its
-  // registers are capped for 4 CTAs per SM (128; ~300 bytes spill) and the
-  // warps of a CTA pass barriers at five points of each face.  96^3 VJP stage
-  // on GB300: 2.52 ms (168 registers, 430 bytes spilled, 3 CTAs) -> 2.29
-  // (parked, 3 CTAs, no spill) -> 2.03 (parked, 4 CTAs) -> 1.97 ms (with the
-  // barriers); one CTA of 384 threads (168 registers, no spill) took 2.34 ms,
+  // The double-float sweep parks its cell primitives, MUSCL states and
+  // Jacobian in shared memory across the Roe part (55 KB per CTA of 128
+  // threads), runs the MUSCL forward as a loop, is capped at 128 registers
+  // for 4 CTAs per SM (~200 bytes spill) and the warps of a CTA pass
+  // barriers at five points of each face.  96^3 VJP stage on GB300: 2.52 ms
+  // (168 registers, 430 bytes spilled, 3 CTAs) -> 2.29 (parked, 3 CTAs, no
+  // spill) -> 2.03 (parked, 4 CTAs) -> 1.97 (barriers) -> 1.80 ms (MUSCL
+  // loop); one CTA of 384 threads (168 registers, no spill) took 2.34 ms,
   // two of 256 1.98 ms.  The binary64 sweep is bound by the FP64 unit and
   // keeps its registers.
   if (double_float) {

@@ -147,9 +147,10 @@ struct Park<df64> {
     return mk(f.x, f.y);
   }
 };
-// values parked per thread: r, u, v, w, 1/r, |u|^2 of the four cells and the
-// four MUSCL Jacobian coefficients of the five variables
-constexpr int ADJ_PARK = 4 * 6 + 4 * 5;
+// values parked per thread: r, u, v, w, 1/r, |u|^2 of the four cells, the
+// four MUSCL Jacobian coefficients of the five variables and the two MUSCL
+// states of the five variables
+constexpr int ADJ_PARK = 4 * 6 + 4 * 5 + 2 * 5;
 
 // Face VJP: q[c][n] conserved state of stencil cell c (c = 0..3 along the face
 // normal, the face between cells 1 and 2), unit normal n, area A, cotangent Fb
@@ -169,8 +170,7 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
   // VR = V2 - e4kp phi(dp, d0) - e4km phi(d0, dp);
   // jL0 = dVL/dd0, jLm = dVL/ddm, jR0 = dVR/dd0 (sign included), jRp = dVR/ddp
   T VL[5], VR[5], jL0[5], jLm[5], jR0[5], jRp[5];
-#pragma unroll
-  for (int n = 0; n < 5; ++n) {
+  auto muscl_n = [&](int n, T& L, T& R, T& j0, T& j1, T& j2, T& j3) {
     const T v0 = n == 0 ? s[0].r : (n == 1 ? s[0].u : (n == 2 ? s[0].v : (n == 3 ? s[0].w : s[0].p)));
     const T v1 = n == 0 ? s[1].r : (n == 1 ? s[1].u : (n == 2 ? s[1].v : (n == 3 ? s[1].w : s[1].p)));
     const T v2 = n == 0 ? s[2].r : (n == 1 ? s[2].u : (n == 2 ? s[2].v : (n == 3 ? s[2].w : s[2].p)));
@@ -181,12 +181,36 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
     const T f2 = lim_phi(P, dm, d0, a2, b2);
     const T f3 = lim_phi(P, dp, d0, a3, b3);
     const T f4 = lim_phi(P, d0, dp, a4, b4);
-    VL[n] = v1 + (P.e4km * f1 + P.e4kp * f2);
-    VR[n] = v2 - (P.e4kp * f3 + P.e4km * f4);
-    jL0[n] = P.e4km * a1 + P.e4kp * b2;
-    jLm[n] = P.e4km * b1 + P.e4kp * a2;
-    jR0[n] = -(P.e4kp * b3 + P.e4km * a4);
-    jRp[n] = -(P.e4kp * a3 + P.e4km * b4);
+    L = v1 + (P.e4km * f1 + P.e4kp * f2);
+    R = v2 - (P.e4kp * f3 + P.e4km * f4);
+    j0 = P.e4km * a1 + P.e4kp * b2;
+    j1 = P.e4km * b1 + P.e4kp * a2;
+    j2 = -(P.e4kp * b3 + P.e4km * a4);
+    j3 = -(P.e4kp * a3 + P.e4km * b4);
+  };
+  if constexpr (SN > 0) {
+    // one copy of the variable's code, run five times (the unrolled
+    // straight-line sweep waits on instruction fetch); its results go to
+    // the parked shared memory, the states come back to registers
+#pragma unroll 1
+    for (int n = 0; n < 5; ++n) {
+      T L, R, j0, j1, j2, j3;
+      muscl_n(n, L, R, j0, j1, j2, j3);
+      Park<T>::put(park + (24 + n) * SN, j0);
+      Park<T>::put(park + (29 + n) * SN, j1);
+      Park<T>::put(park + (34 + n) * SN, j2);
+      Park<T>::put(park + (39 + n) * SN, j3);
+      Park<T>::put(park + (44 + n) * SN, L);
+      Park<T>::put(park + (49 + n) * SN, R);
+    }
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+      VL[n] = Park<T>::get(park + (44 + n) * SN);
+      VR[n] = Park<T>::get(park + (49 + n) * SN);
+    }
+  } else {
+#pragma unroll
+    for (int n = 0; n < 5; ++n) muscl_n(n, VL[n], VR[n], jL0[n], jLm[n], jR0[n], jRp[n]);
   }
   if constexpr (SN > 0) {
 #pragma unroll
@@ -197,13 +221,6 @@ __device__ __forceinline__ void face_vjp(const AdjC<T>& P, const T q[4][5], T nx
       Park<T>::put(park + (6 * c + 3) * SN, s[c].w);
       Park<T>::put(park + (6 * c + 4) * SN, s[c].ri);
       Park<T>::put(park + (6 * c + 5) * SN, s[c].k);
-    }
-#pragma unroll
-    for (int n = 0; n < 5; ++n) {
-      Park<T>::put(park + (24 + n) * SN, jL0[n]);
-      Park<T>::put(park + (29 + n) * SN, jLm[n]);
-      Park<T>::put(park + (34 + n) * SN, jR0[n]);
-      Park<T>::put(park + (39 + n) * SN, jRp[n]);
     }
     asm volatile("" ::: "memory");
   }
