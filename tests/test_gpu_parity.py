@@ -172,6 +172,26 @@ def test_every_tile_shape_residual_and_step(prec, tile):
     assert rel_err_states(got, ref_q, o) <= (1e-6 if prec == "fp32flux" else 1e-12)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 2, 1), (1, 7, 5), (17, 1, 3), (2, 9, 2), (33, 9, 2)])
+def test_thin_blocks_every_shape(prec, dims):
+    """Blocks thinner than a tile and than the two-cell halo, one k-plane per
+    tile (the binary64 slope pass then recomputes the zeta slopes below and
+    above every plane): residual and one RK step against the oracle in the
+    tile shapes with and without the shared slopes' two-CTA layouts."""
+    pb = cases.mms_3d(dims, curvilinear=True)
+    o = oracle.Oracle(pb)
+    ref_q = o.run(pb.q.copy(), pb.dt, 4)
+    for tile, kchunk in ((3, 1), (8, 2), (9, 1), (10, 3)):
+        r, ref, _ = residual_pair(pb, prec, exchange=False, tile=tile, kchunk=kchunk)
+        assert rel_err_fields(r, ref, o) <= TOL_RES[prec], (tile, kchunk)
+        s = solver(pb, prec, tile=tile, kchunk=kchunk)
+        s.rk_step(pb.dt, use_graph=False)
+        got = s.get_state(0).cpu().numpy()
+        s.close()
+        assert rel_err_states(got, ref_q, o) <= (1e-6 if prec == "fp32flux" else 1e-12), (tile, kchunk)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
 def test_autotuned_launch_keeps_parity(prec):
     pb = cases.multiblock_batched(nblocks=8, lo=6, hi=40, seed=6)
