@@ -349,8 +349,17 @@ def roofline(pb, precision, stage_times, ex_time, curvilinear, pk, peak_kind, tr
                   "frac": achieved / (peak / 1e9), "ops_per_launch": ops, "peak_source": how,
                   "nominal_peak": nominal_alu_peak(precision) / 1e9})
     # measured DRAM bytes of one launch, for the workload they were captured on
-    r["traffic"] = traffic.get(precision) if traffic.get("workload") == pb.name else None
+    r["traffic"] = traffic_of(traffic, pb.name, precision)
     return r
+
+
+def traffic_of(traffic, workload, precision):
+    """DRAM bytes per stage launch captured for this workload and form (the
+    headline workload at the top level of the summary, others under
+    "workloads"), else None."""
+    if traffic.get("workload") == workload:
+        return traffic.get(precision)
+    return traffic.get("workloads", {}).get(workload, {}).get(precision)
 
 
 def max_over_ranks(x: float, dist, device: str) -> float:

@@ -67,3 +67,9 @@ def test_traffic_applies_to_its_own_workload_and_sources_only():
     assert r["traffic"] == t[prec]
     r = bench.roofline(other, prec, [1e-3] * 4, 0.0, True, peaks, "test", t, RATES)
     assert r["traffic"] is None
+    for name, forms in t.get("workloads", {}).items():
+        other.name = name
+        for prec, v in forms.items():
+            if prec in ("fp64", "df64", "fp32flux"):
+                r = bench.roofline(other, prec, [1e-3] * 4, 0.0, True, peaks, "test", t, RATES)
+                assert r["traffic"] == v
