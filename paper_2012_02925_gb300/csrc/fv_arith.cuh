@@ -271,6 +271,13 @@ template <> struct Sc<double> {
                                                 double h) {
     return a * b + c * d + e * f + g * h;
   }
+  // a b + c d (+ e f) - z as a chain of fused multiply-adds from -z
+  static __device__ __forceinline__ double dot2m(double a, double b, double c, double d, double z) {
+    return fma(a, b, fma(c, d, -z));
+  }
+  static __device__ __forceinline__ double dot3m(double a, double b, double c, double d, double e, double f, double z) {
+    return fma(a, b, fma(c, d, fma(e, f, -z)));
+  }
   static __device__ __forceinline__ float hi(double x) { return (float)x; }
   static __device__ __forceinline__ bool lt(double a, double b) { return a < b; }
   // Sign and magnitude tests of the limiter and the entropy fix as integer
@@ -320,6 +327,12 @@ template <> struct Sc<float> {
                                                float h) {
     return a * b + c * d + e * f + g * h;
   }
+  static __device__ __forceinline__ float dot2m(float a, float b, float c, float d, float z) {
+    return fmaf(a, b, fmaf(c, d, -z));
+  }
+  static __device__ __forceinline__ float dot3m(float a, float b, float c, float d, float e, float f, float z) {
+    return fmaf(a, b, fmaf(c, d, fmaf(e, f, -z)));
+  }
   static __device__ __forceinline__ float hi(float x) { return x; }
   static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
   static __device__ __forceinline__ bool lt_nonneg(float a, float b) { return a < b; }
@@ -358,6 +371,16 @@ template <> struct Sc<df64> {
   }
   static __device__ __forceinline__ df64 dot4(df64 a, df64 b, df64 c, df64 d, df64 e, df64 f, df64 g, df64 h) {
     const df64 x[4] = {a, c, e, g}, y[4] = {b, d, f, h};
+    return df_dot<4>(x, y);
+  }
+  // the subtracted term as one more product with -1 (exact) in the
+  // compensated dot product
+  static __device__ __forceinline__ df64 dot2m(df64 a, df64 b, df64 c, df64 d, df64 z) {
+    const df64 x[3] = {a, c, z}, y[3] = {b, d, mk(-1.0f, 0.0f)};
+    return df_dot<3>(x, y);
+  }
+  static __device__ __forceinline__ df64 dot3m(df64 a, df64 b, df64 c, df64 d, df64 e, df64 f, df64 z) {
+    const df64 x[4] = {a, c, e, z}, y[4] = {b, d, f, mk(-1.0f, 0.0f)};
     return df_dot<4>(x, y);
   }
   static __device__ __forceinline__ float hi(df64 x) { return x.hi; }
