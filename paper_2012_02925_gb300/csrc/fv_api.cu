@@ -304,9 +304,11 @@ template <int MODE>
 __global__ void __launch_bounds__(256) exchange_kernel(const FvBlockDev* __restrict__ blocks,
                                                        const FvConnDev* __restrict__ conns,
                                                        const FvXchTile* __restrict__ tiles, double* q, double* buf) {
-  constexpr int TA = FV_XCH_TA, TB = FV_XCH_TB, N = 2 * TA * TB;
-  // [b][a][depth], a row padded by one position against bank conflicts
-  __shared__ double tile_v[TB * (TA + 1) * 2];
+  constexpr int TA = FV_XCH_TA, TB = FV_XCH_TB, N = 2 * TA * TB, P = TB * (TA + 1) * 2;
+  // [variable][b][a][depth], a row padded by one position against bank
+  // conflicts; all five variables are read before the one barrier, so each
+  // thread has its items' five loads in flight together (42 KB)
+  __shared__ double tile_v[5 * P];
   const FvXchTile T = tiles[blockIdx.x];
   const FvConnDev c = conns[T.conn];
   const long long nc = 2LL * c.L0 * c.L1;
@@ -314,32 +316,40 @@ __global__ void __launch_bounds__(256) exchange_kernel(const FvBlockDev* __restr
   const int fd = MODE == XCH_PACK ? 0 : xch_fast_dst(c);
   const FvBlockDev* S = MODE == XCH_UNPACK ? nullptr : &blocks[c.src_block];
   const FvBlockDev* D = MODE == XCH_PACK ? nullptr : &blocks[c.dst_block];
-  for (int v = 0; v < 5; ++v) {
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      int a, b, d;
-      xch_order(t, fs, a, b, d);
-      const int ga = T.a0 + a, gb = T.b0 + b;
-      if (ga >= c.L0 || gb >= c.L1) continue;
-      double x;
-      if (MODE == XCH_UNPACK)
-        x = buf[5 * c.item_off + v * nc + ga + (long long)c.L0 * (gb + (long long)c.L1 * d)];
-      else
-        x = q[xch_src_index(*S, c, ga, gb, d + 1) + v * S->plane];
-      tile_v[(b * (TA + 1) + a) * 2 + d] = x;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    int a, b, d;
+    xch_order(t, fs, a, b, d);
+    const int ga = T.a0 + a, gb = T.b0 + b;
+    if (ga >= c.L0 || gb >= c.L1) continue;
+    const int o = (b * (TA + 1) + a) * 2 + d;
+    if (MODE == XCH_UNPACK) {
+      const double* src = buf + 5 * c.item_off + ga + (long long)c.L0 * (gb + (long long)c.L1 * d);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) tile_v[v * P + o] = src[v * nc];
+    } else {
+      const double* src = q + xch_src_index(*S, c, ga, gb, d + 1);
+      const long long pl = S->plane;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) tile_v[v * P + o] = src[v * pl];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      int a, b, d;
-      xch_order(t, fd, a, b, d);
-      const int ga = T.a0 + a, gb = T.b0 + b;
-      if (ga >= c.L0 || gb >= c.L1) continue;
-      const double x = tile_v[(b * (TA + 1) + a) * 2 + d];
-      if (MODE == XCH_PACK)
-        buf[5 * c.item_off + v * nc + ga + (long long)c.L0 * (gb + (long long)c.L1 * d)] = x;
-      else
-        q[xch_dst_index(*D, c, ga, gb, d + 1) + v * D->plane] = x;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    int a, b, d;
+    xch_order(t, fd, a, b, d);
+    const int ga = T.a0 + a, gb = T.b0 + b;
+    if (ga >= c.L0 || gb >= c.L1) continue;
+    const int o = (b * (TA + 1) + a) * 2 + d;
+    if (MODE == XCH_PACK) {
+      double* dst = buf + 5 * c.item_off + ga + (long long)c.L0 * (gb + (long long)c.L1 * d);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dst[v * nc] = tile_v[v * P + o];
+    } else {
+      double* dst = q + xch_dst_index(*D, c, ga, gb, d + 1);
+      const long long pl = D->plane;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dst[v * pl] = tile_v[v * P + o];
     }
-    __syncthreads();
   }
 }
 
