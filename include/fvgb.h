@@ -167,7 +167,7 @@ typedef struct {
  *     (1: 32x8 cells / 256 threads, 2: 32x4 / 128, 3: 16x8 / 128, 4: 30x8 / 256,
  *     5: 32x8 / 288, 6: 32x8 / 256 and 7: 32x4 / 128 with the next k-plane
  *     prefetched by cp.async - 6 and 7 for FV_PREC_FP32FLUX only -, 8: 32x7 / 256,
- *     9: 32x6 / 256, 10: 16x12 / 192).
+ *     9: 32x6 / 256, 10: 16x12 / 192, 11: 16x4 / 128).
  *   kchunk: k-planes per tile; 0 = automatic (about three tiles per resident
  *     CTA slot); -w = about w tiles per resident CTA slot.  Tiles are handed
  *     to persistent CTAs largest first through a device counter.

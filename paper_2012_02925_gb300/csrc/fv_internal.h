@@ -141,11 +141,11 @@ FV_STAGE_VARIANTS(FV_DECLARE_STAGE_VARIANT)
 #undef FV_DECLARE_STAGE_VARIANT
 
 // tile shapes compiled into fv_stage_kernel: {TX, TY, threads, prefetch}
-constexpr int FV_NUM_SHAPES = 10;
+constexpr int FV_NUM_SHAPES = 11;
 constexpr int FV_SHAPE_TABLE[FV_NUM_SHAPES][4] = {{32, 8, 256, 0}, {32, 4, 128, 0}, {16, 8, 128, 0},
                                                   {30, 8, 256, 0}, {32, 8, 288, 0}, {32, 8, 256, 1},
                                                   {32, 4, 128, 1}, {32, 7, 256, 0}, {32, 6, 256, 0},
-                                                  {16, 12, 192, 0}};
+                                                  {16, 12, 192, 0}, {16, 4, 128, 0}};
 
 // Discrete-adjoint kernels (fv_adjoint.cu): binary64 data; the face VJPs in
 // binary64 (double_float = 0) or double-float arithmetic.

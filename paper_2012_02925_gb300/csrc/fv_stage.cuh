@@ -720,7 +720,8 @@ static int occupancy_t(bool three_d, size_t* smem_out) {
   X(7, 32, 4, 128, true)  \
   X(8, 32, 7, 256, false) \
   X(9, 32, 6, 256, false) \
-  X(10, 16, 12, 192, false)
+  X(10, 16, 12, 192, false) \
+  X(11, 16, 4, 128, false)
 
 // FAST selects the compile-time default scheme (FaceCFast); each
 // translation unit instantiates one combination of FAST, VISC and BC.

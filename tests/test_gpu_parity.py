@@ -156,7 +156,7 @@ def test_residual_method_options(prec, opts):
     assert rel_err_fields(r, ref, o) <= TOL_RES[prec]
 
 
-SHAPES = [(p, t) for p in PRECS for t in range(1, 11) if t not in (6, 7) or p == "fp32flux"]
+SHAPES = [(p, t) for p in PRECS for t in range(1, 12) if t not in (6, 7) or p == "fp32flux"]
 
 
 @pytest.mark.parametrize("prec,tile", SHAPES)
